@@ -1,0 +1,240 @@
+/*
+ * mnemonic.h -- C ABI of a B300-native incremental subgraph matcher for
+ * streaming multigraphs (Mnemonic, arXiv 2206.09983).
+ *
+ * Problem (Sec. II-B, "Problem Definition"): given a data graph G, a query
+ * graph G_Q and a batch dG of edge insertions (or deletions), report the
+ * embeddings dS that appear (or disappear), so that S(G + dG) = S(G) + dS.
+ * The driver loop of Alg. 1 applies each snapshot's insertions first and its
+ * deletions second; one call of mn_insert_batch is one such snapshot for a
+ * count window (window_edges > 0): insert the batch, then expire the oldest
+ * edges beyond the window.
+ *
+ * Data edges keep their own identity (Sec. I, Sec. II-A: every edge has an
+ * id, so parallel edges with distinct timestamps are distinct).  Here the id
+ * of an edge is its arrival sequence number `seq` (0, 1, 2, ... over the life
+ * of the graph).  Timestamps must be strictly increasing in arrival order.
+ *
+ * Embedding (Sec. II-B): a vertex map f and an edge map g with
+ * src(g(e)) = f(s(e)), dst(g(e)) = f(t(e)); query vertex label mask a subset
+ * of the data vertex's mask (0 = any); query edge label -1 (any) or equal;
+ * edge attribute and timestamp inside the query edge's half-open ranges;
+ * MN_ISO requires f injective, MN_HOMO does not (Sec. III); temporal
+ * constraints require ts(g(a)) < ts(g(b)) for precedence pairs (Sec. VI-D).
+ *
+ * Result records (one per embedding) are, per query, nv uint32 vertex ids
+ * (f(u_0) ... f(u_{nv-1})), zero padding to an 8-byte boundary, then ne
+ * uint64 edge seqs (seq(g(e_0)) ... seq(g(e_{ne-1}))); mn_record_layout
+ * gives the size.  Records come in no particular order.
+ *
+ * Errors: every call returns MN_OK (0) or a negative mn_status; the message
+ * of the last failing call on a graph is in mn_last_error.  On a validation
+ * error nothing is applied.  Handles are not thread-safe: one thread per
+ * graph handle; distinct handles are independent.
+ *
+ * Ownership: every input pointer is read before the call returns; the
+ * library copies what it keeps.  Count arrays in mn_batch_result are owned by
+ * the library and stay valid until the next call on the same graph.
+ * Embedding lists stay on the device until the next insert/delete call.
+ */
+#ifndef MNEMONIC_H
+#define MNEMONIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mn_status;
+
+#define MN_OK                    0
+#define MN_ERR_INVALID_ARG      -1  /* bad pointer, size, flag or query */
+#define MN_ERR_INVALID_VERTEX   -2  /* vertex id >= num_vertices or label >= num_edge_labels */
+#define MN_ERR_TS_ORDER         -3  /* timestamps not strictly increasing */
+#define MN_ERR_OOM              -4  /* device allocation failed or over mem_budget_bytes */
+#define MN_ERR_ADMISSION        -5  /* batch larger than max_batch or the ring is full */
+#define MN_ERR_OUTPUT_OVERFLOW  -6  /* result lists beyond mem_budget_bytes; counts exact */
+#define MN_ERR_TIMEOUT          -7  /* a bounded device wait gave up */
+#define MN_ERR_DEVICE           -8  /* a CUDA call failed */
+#define MN_ERR_STATE            -9  /* call not valid in the graph's current state */
+
+#define MN_MAX_QV 16           /* query vertices */
+#define MN_MAX_QE 16           /* query edges */
+#define MN_LABEL_ANY (-1)
+
+#define MN_ISO  0
+#define MN_HOMO 1
+
+#define MN_TEMPORAL_NONE  0    /* no ordering */
+#define MN_TEMPORAL_CHAIN 1    /* ts(g(e_0)) < ts(g(e_1)) < ... in declaration order */
+#define MN_TEMPORAL_PAIRS 2    /* ts(g(a)) < ts(g(b)) for each listed pair (a, b) */
+
+/* insert/delete flags */
+#define MN_DEVICE_PTR 0x1u     /* the edge (or seq) array is device memory */
+#define MN_COUNT_ONLY 0x2u     /* count embeddings, keep no lists */
+
+/* fetch destination flags */
+#define MN_DST_HOST   0x0u
+#define MN_DST_DEVICE 0x1u
+
+typedef struct mn_graph mn_graph;
+
+/* One data edge as the caller hands it in (24 bytes, ts 8-byte aligned). */
+typedef struct {
+    uint32_t src, dst;      /* vertex ids < num_vertices */
+    uint32_t label;         /* edge label < num_edge_labels */
+    int32_t  attr;          /* edge attribute */
+    int64_t  ts;            /* timestamp, strictly increasing over the stream */
+} mn_edge;
+
+typedef struct {
+    uint32_t num_vertices;
+    uint32_t num_edge_labels;            /* 1..256 */
+    const uint32_t *vertex_label_mask;   /* host, num_vertices entries, copied; NULL = all 0 */
+    uint64_t window_edges;               /* count window W; 0 = insert-only */
+    uint64_t max_batch;                  /* largest insert or delete batch */
+    uint64_t edge_capacity;              /* insert-only: most edges ever held; ignored with a window */
+    uint64_t out_capacity;               /* initial records per (query, sign) list; 0 = 1M */
+    uint64_t mem_budget_bytes;           /* cap on device memory the graph may hold; 0 = none */
+    uint32_t max_queries;                /* 1..64 */
+    int32_t  device;                     /* CUDA device ordinal */
+    void    *cuda_stream;                /* cudaStream_t to run on; NULL = the graph makes one */
+} mn_graph_config;
+
+typedef struct {
+    uint32_t src, dst;                   /* query vertex ids < nv; src != dst */
+    int32_t  label;                      /* edge label or MN_LABEL_ANY */
+    int32_t  attr_lo, attr_hi;           /* attr in [attr_lo, attr_hi) */
+    int32_t  pad_;
+    int64_t  ts_lo, ts_hi;               /* ts in [ts_lo, ts_hi) */
+} mn_qedge;
+
+typedef struct {
+    uint32_t nv, ne;                     /* 2..MN_MAX_QV vertices, 1..MN_MAX_QE edges, connected */
+    const uint32_t *vlabel_mask;         /* nv entries; NULL = all 0 (any) */
+    const mn_qedge *edges;               /* ne entries; no two with the same (src, dst) */
+    uint32_t semantics;                  /* MN_ISO or MN_HOMO */
+    uint32_t temporal;                   /* MN_TEMPORAL_* */
+    uint32_t n_prec;                     /* MN_TEMPORAL_PAIRS: number of pairs */
+    const uint32_t *prec;                /* 2 * n_prec query-edge indices (a, b) */
+} mn_query_desc;
+
+typedef struct {
+    uint64_t batch_id;                   /* 1, 2, ... per insert/delete call */
+    uint64_t seq_lo, seq_hi;             /* seqs given to the inserted edges */
+    uint64_t expired_lo, expired_hi;     /* seqs that left the window in this call */
+    uint32_t num_queries;
+    const uint64_t *count_pos;           /* per query |dS+| (library-owned) */
+    const uint64_t *count_neg;           /* per query |dS-| (library-owned) */
+} mn_batch_result;
+
+/* Create an empty graph on `device` (Sec. III, InitializeStream: window size
+ * and batch size are the snapshot generator's parameters).  Allocates the
+ * edge ring, the label-partitioned adjacency and its delta buffers on the
+ * device.  *out is NULL on error. */
+mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out);
+
+/* Free every device and host resource of the graph; NULL is ignored. */
+void mn_destroy_graph(mn_graph *g);
+
+/* Register a query (Sec. III, InitializeIndex: root, query tree and one
+ * matching order per starting query edge, Sec. V "Matching order
+ * computation"; masks of Table I) and build its DEBI words over the live
+ * edges (Sec. IV-A).  No embeddings are reported for edges already live.
+ * *query_id receives 0, 1, ... in registration order. */
+mn_status mn_register_query(mn_graph *g, const mn_query_desc *q, uint32_t *query_id);
+
+/* One snapshot (Alg. 1; Alg. 2 batchInserts then batchDeletes): append n
+ * edges (host array, or device array with MN_DEVICE_PTR), report dS+ for
+ * every query, then, with a window, expire the oldest edges beyond
+ * window_edges and report dS- computed before their removal.  n may be 0.
+ * `out` may be NULL. */
+mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags,
+                          mn_batch_result *out);
+
+/* Explicit deletion of live edges by seq (Alg. 2 batchDeletes): report dS-
+ * on the graph before removal, then remove them.  Every seq must be live and
+ * listed once. */
+mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_t flags,
+                          mn_batch_result *out);
+
+/* Copy records [offset, offset + max_records) of the last batch's list for
+ * (query_id, sign: +1 new, -1 removed) to dst (host, or device with
+ * MN_DST_DEVICE).  *n_written gets the number copied.  batch_id must be the
+ * last batch's id. */
+mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id, int32_t sign,
+                              uint64_t offset, uint64_t max_records, void *dst,
+                              uint32_t dst_flags, uint64_t *n_written);
+
+/* Record layout of a query's results: vertex count, edge count, bytes. */
+mn_status mn_record_layout(const mn_graph *g, uint32_t query_id, uint32_t *nv, uint32_t *ne,
+                           uint32_t *record_bytes);
+
+/* |S(G)| for a query over the live window (Sec. II-B), by seeding every live
+ * edge at query edge 0. */
+mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
+
+/* Copy the DEBI words (Sec. IV-A; bit e = the edge matches query edge e) of
+ * the edges with seq in [seq_lo, seq_hi) to host memory `words` (uint32
+ * each); edges not live read 0. */
+mn_status mn_read_debi(mn_graph *g, uint32_t query_id, uint64_t seq_lo, uint64_t seq_hi,
+                       uint32_t *words);
+
+/* Copy the adjacency of direction dir (0 = out, 1 = in) to host memory:
+ * entry i is (key[i] = v * num_edge_labels + label, nbr[i], seq[i]), sorted
+ * by (key, nbr, seq), live edges only.  *n gets the entry count; arrays must
+ * hold `cap` entries (MN_ERR_INVALID_ARG with *n set when they do not). */
+mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *key,
+                            uint32_t *nbr, uint64_t *seq, uint64_t *n);
+
+/* Live window [lo, hi) of seqs and the number of registered queries. */
+mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi,
+                        uint32_t *num_queries);
+
+/* Bound the enumerator's work: each device warp gives up after max_iters
+ * backtracking steps, sets a status word and returns (no spin, no trap).  The
+ * batch is still applied to the graph, its counts are partial and the call
+ * returns MN_ERR_TIMEOUT; later calls work normally.  0 = no limit (the
+ * default).  Lets tests drive the bounded-wait path without faulting. */
+mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters);
+
+/* Counters of one graph since creation (or the last mn_reset_stats).  Stage
+ * times are device time measured with CUDA events on the graph's stream
+ * around each stage when timing is enabled (mn_set_timing), else 0.  The
+ * enumerator counters are summed on the device: seeds taken, adjacency
+ * entries tested, candidates bound (search-tree nodes) and embeddings
+ * emitted (Sec. VI-A counts traversed edges per update the same way). */
+typedef struct {
+    uint64_t kernel_launches;      /* kernels launched by the library */
+    uint64_t batches;              /* insert/delete calls */
+    uint64_t enumerate_launches;   /* launches of the enumerator */
+    double   ms_ingest;            /* ingest + edgeMatcher */
+    double   ms_adjacency;         /* delta sort, compaction, merge, offsets */
+    double   ms_seeds;             /* work-unit compaction */
+    double   ms_enumerate;         /* backtracking enumerator */
+    double   ms_expire;            /* DEBI clear of expired edges */
+    uint64_t seeds;
+    uint64_t entries_scanned;
+    uint64_t binds;
+    uint64_t records;
+} mn_stats;
+
+/* Turn per-stage event timing on (1) or off (0, the default). */
+mn_status mn_set_timing(mn_graph *g, int enable);
+
+/* Copy the counters to *out. */
+mn_status mn_get_stats(const mn_graph *g, mn_stats *out);
+
+/* Zero the counters. */
+mn_status mn_reset_stats(mn_graph *g);
+
+/* Message of the last failing call on g (or of the last failing create when
+ * g is NULL); never NULL. */
+const char *mn_last_error(const mn_graph *g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MNEMONIC_H */

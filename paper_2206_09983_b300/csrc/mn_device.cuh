@@ -1,0 +1,882 @@
+// mn_device.cuh -- device data structures and kernels of the incremental
+// matcher (Mnemonic, arXiv 2206.09983) for sm_103a.
+//
+// Hot path per edge batch (Alg. 2, batchInserts then batchDeletes):
+//   k_ingest          validate, append to the edge ring, edgeMatcher -> DEBI
+//                     words (Sec. IV-A "Updating"), delta sort keys
+//   k_sort_tiles /    sort the batch's adjacency entries by (vertex, label,
+//   k_merge_pass      neighbour), ties by arrival
+//   k_delta_finalize  delta entries + per-(vertex,label) degree counts
+//   k_live_count /    drop entries that left the window from the base
+//   k_compact         adjacency (memory recycling, Sec. IV-A)
+//   k_merge_csr       merge base and delta into the new sorted adjacency
+//   k_scan_*          offsets of every (vertex, label) segment
+//   k_seeds_*         work units: one per (batch edge, query, query edge)
+//                     whose DEBI bit is set (Sec. V "Work decomposition")
+//   k_enumerate       warp-per-seed backtracking (Sec. III enumerator) with
+//                     the masks of Table I and the per-seed matching orders
+//                     of Sec. V
+//   k_expire          clear DEBI words of expired edges (Sec. IV-A)
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "mnemonic.h"
+
+namespace mn {
+
+constexpr uint32_t FULL = 0xffffffffu;
+
+// device status bits (host maps them to mn_status)
+constexpr uint32_t ST_BAD_VERTEX = 1u;
+constexpr uint32_t ST_TS_ORDER   = 2u;
+constexpr uint32_t ST_BAD_DELETE = 4u;
+constexpr uint32_t ST_TIMEOUT    = 8u;
+
+// One query edge's edgeMatcher predicate (Sec. III: labels of the edge and
+// both endpoints; Sec. I: vertex and edge attributes).
+struct QPred {
+    int32_t label;          // -1 = any
+    uint32_t vmask_src;     // query vertex label masks (subset test)
+    uint32_t vmask_dst;
+    int32_t attr_lo, attr_hi;
+    int32_t pad_;
+    int64_t ts_lo, ts_hi;
+};
+
+struct QueryDev {
+    uint32_t ne, pad_[3];
+    QPred e[MN_MAX_QE];
+};
+
+// One step of a per-seed matching order: binds query edge `qe`.
+//   EXTEND: `from` is bound, `to` is not; scan the adjacency of f(from) in
+//           direction `dir` (0 = out: edge from->to, 1 = in: edge to->from).
+//   CLOSE : both bound; find the parallel instances between them.
+constexpr uint8_t K_EXTEND = 0, K_CLOSE = 1;
+struct Step {
+    uint8_t qe, kind, from, to;
+    uint8_t dir, avoid;     // avoid: qe precedes the seed edge -> no batch edge (Table I)
+    int16_t label;
+    uint16_t pred, succ;    // bound query edges that must be older / newer
+    uint16_t bound_v, pad_; // query vertices bound before this step
+};
+static_assert(sizeof(Step) == 16, "Step is 16 bytes");
+
+// 16-byte aligned: lanes load their step with one 16-byte vector load.
+struct alignas(16) Plan {
+    Step step[MN_MAX_QE];   // step[0] is the seed edge
+    uint8_t nsteps, nv, ne, iso;
+    uint8_t seed_src, seed_dst, pad_[2];
+    uint32_t rec_bytes, goff;
+};
+static_assert(sizeof(Plan) % 16 == 0, "Plan rows must keep 16-byte alignment");
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ uint32_t lanemask_lt()
+{
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t match_word(const QueryDev *q, uint32_t label, int32_t attr,
+                                               int64_t ts, uint32_t ms, uint32_t md)
+{
+    uint32_t w = 0;
+    const uint32_t ne = q->ne;
+    for (uint32_t e = 0; e < ne; e++) {
+        const QPred &P = q->e[e];
+        bool ok = (P.label < 0 || (uint32_t)P.label == label) &&
+                  ((ms & P.vmask_src) == P.vmask_src) && ((md & P.vmask_dst) == P.vmask_dst) &&
+                  attr >= P.attr_lo && attr < P.attr_hi && ts >= P.ts_lo && ts < P.ts_hi;
+        w |= (uint32_t)ok << e;
+    }
+    return w;
+}
+
+// First i in [lo, hi) with a[i] >= t (hi if none); all 32 lanes cooperate,
+// each round probing 32 evenly spaced positions.
+__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t *__restrict__ a, uint32_t lo,
+                                                     uint32_t hi, uint32_t t, int lane)
+{
+    while (hi - lo > 32) {
+        uint32_t stride = (hi - lo + 31) >> 5;
+        uint32_t pos = lo + (uint32_t)lane * stride;
+        bool less = pos < hi && a[pos] < t;
+        uint32_t k = __popc(__ballot_sync(FULL, less));
+        if (k == 0) return lo;
+        uint32_t nlo = lo + (k - 1) * stride + 1;
+        uint32_t nhi = lo + k * stride;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    uint32_t pos = lo + (uint32_t)lane;
+    bool less = pos < hi && a[pos] < t;
+    return lo + __popc(__ballot_sync(FULL, less));
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim multiple of 32,
+// at most 1024).  Returns the exclusive prefix; *total gets the block sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            uint32_t y = __shfl_up_sync(FULL, s, d);
+            if (lane >= d) s += y;
+        }
+        warp_sums[lane] = s;   // inclusive over warps
+    }
+    __syncthreads();
+    uint32_t warp_off = wid ? warp_sums[wid - 1] : 0;
+    *total = warp_sums[nw - 1];
+    uint32_t r = warp_off + x - v;
+    __syncthreads();
+    return r;
+}
+
+// ------------------------------------------------------------------ ingest
+
+struct IngestParams {
+    const mn_edge *edges;
+    uint32_t n, n_pad;
+    uint64_t seq0;
+    int64_t last_ts;
+    uint32_t V, L, cap_mask;
+    uint32_t *r_src, *r_dst;
+    uint8_t *r_label, *r_dead;
+    int32_t *r_attr;
+    int64_t *r_ts;
+    const uint32_t *vmask;
+    uint32_t nq;
+    const QueryDev *queries;
+    uint32_t *const *debi;
+    unsigned long long *dkey[2];
+    uint32_t *dval[2];
+    uint32_t *status;
+    long long *last_ts_out;
+};
+
+// Append the batch to the ring, compute its DEBI words for every query
+// (edgeMatcher, Sec. III / IV-A) and emit the sort keys of its adjacency
+// entries.  Invalid batches are flagged in *status; every later kernel of the
+// batch checks the flag, and ring slots written here were free.
+__global__ void k_ingest(IngestParams p)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.n_pad) return;
+    if (i >= p.n) {
+        p.dkey[0][i] = ~0ull; p.dval[0][i] = ~0u;
+        p.dkey[1][i] = ~0ull; p.dval[1][i] = ~0u;
+        return;
+    }
+    const mn_edge e = p.edges[i];
+    const int64_t prev = i == 0 ? p.last_ts : p.edges[i - 1].ts;
+    uint32_t err = 0;
+    if (e.src >= p.V || e.dst >= p.V || e.label >= p.L) err |= ST_BAD_VERTEX;
+    if (e.ts <= prev) err |= ST_TS_ORDER;
+    if (err) atomicOr(p.status, err);
+    if (i == p.n - 1) *p.last_ts_out = e.ts;
+    const uint32_t slot = (uint32_t)(p.seq0 + i) & p.cap_mask;
+    p.r_src[slot] = e.src;
+    p.r_dst[slot] = e.dst;
+    p.r_label[slot] = (uint8_t)e.label;
+    p.r_attr[slot] = e.attr;
+    p.r_ts[slot] = e.ts;
+    p.r_dead[slot] = 0;
+    const uint32_t ms = err ? 0u : p.vmask[e.src];
+    const uint32_t md = err ? 0u : p.vmask[e.dst];
+    for (uint32_t q = 0; q < p.nq; q++)
+        p.debi[q][slot] = err ? 0u : match_word(&p.queries[q], e.label, e.attr, e.ts, ms, md);
+    const uint32_t L = p.L;
+    const uint32_t ks = err ? 0u : e.src * L + e.label;
+    const uint32_t kd = err ? 0u : e.dst * L + e.label;
+    p.dkey[0][i] = ((unsigned long long)ks << 32) | e.dst;
+    p.dkey[1][i] = ((unsigned long long)kd << 32) | e.src;
+    p.dval[0][i] = i;
+    p.dval[1][i] = i;
+}
+
+// Bulk edgeMatcher over live slots [seq_lo, seq_hi) for one query
+// (query registration and periodic reset, Sec. VI-E).
+__global__ void k_match_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask,
+                              const uint32_t *r_src, const uint32_t *r_dst, const uint8_t *r_label,
+                              const int32_t *r_attr, const int64_t *r_ts, const uint8_t *r_dead,
+                              const uint32_t *vmask, const QueryDev *q, uint32_t *debi)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t slot = (uint32_t)(seq_lo + i) & cap_mask;
+    uint32_t w = 0;
+    if (!r_dead[slot])
+        w = match_word(q, r_label[slot], r_attr[slot], r_ts[slot], vmask[r_src[slot]],
+                       vmask[r_dst[slot]]);
+    debi[slot] = w;
+}
+
+// ------------------------------------------------------------------ delta sort
+
+constexpr int SORT_TILE = 2048;
+
+__device__ __forceinline__ bool kv_greater(unsigned long long ka, uint32_t va,
+                                           unsigned long long kb, uint32_t vb)
+{
+    return ka > kb || (ka == kb && va > vb);
+}
+
+// Bitonic sort of SORT_TILE (key, index) pairs per block; blockIdx.y = direction.
+__global__ void __launch_bounds__(1024) k_sort_tiles(unsigned long long *key0, uint32_t *val0,
+                                                     unsigned long long *key1, uint32_t *val1,
+                                                     const uint32_t *status)
+{
+    if (*status) return;
+    __shared__ unsigned long long sk[SORT_TILE];
+    __shared__ uint32_t sv[SORT_TILE];
+    unsigned long long *key = blockIdx.y ? key1 : key0;
+    uint32_t *val = blockIdx.y ? val1 : val0;
+    const uint32_t base = blockIdx.x * SORT_TILE;
+    for (int i = threadIdx.x; i < SORT_TILE; i += blockDim.x) {
+        sk[i] = key[base + i];
+        sv[i] = val[base + i];
+    }
+    __syncthreads();
+    for (int k = 2; k <= SORT_TILE; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < SORT_TILE; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool asc = (i & k) == 0;
+                    bool gt = kv_greater(sk[i], sv[i], sk[ixj], sv[ixj]);
+                    if (gt == asc) {
+                        unsigned long long tk = sk[i]; sk[i] = sk[ixj]; sk[ixj] = tk;
+                        uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < SORT_TILE; i += blockDim.x) {
+        key[base + i] = sk[i];
+        val[base + i] = sv[i];
+    }
+}
+
+constexpr int MERGE_ITEMS = 8;
+
+// One pass of a bottom-up merge sort: merge neighbouring sorted runs of
+// length R into runs of 2R (merge path per thread).  blockIdx.y = direction.
+__global__ void k_merge_pass(const unsigned long long *ks0, const uint32_t *vs0,
+                             unsigned long long *kd0, uint32_t *vd0,
+                             const unsigned long long *ks1, const uint32_t *vs1,
+                             unsigned long long *kd1, uint32_t *vd1,
+                             uint32_t n, uint32_t R, const uint32_t *status)
+{
+    if (*status) return;
+    const unsigned long long *ks = blockIdx.y ? ks1 : ks0;
+    const uint32_t *vs = blockIdx.y ? vs1 : vs0;
+    unsigned long long *kd = blockIdx.y ? kd1 : kd0;
+    uint32_t *vd = blockIdx.y ? vd1 : vd0;
+    const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
+    if (o >= n) return;
+    const uint32_t pbase = o / (2 * R) * (2 * R);
+    const uint32_t nA = min(R, n - pbase);
+    const uint32_t nB = min(R, n - pbase - nA);
+    const unsigned long long *KA = ks + pbase, *KB = KA + nA;
+    const uint32_t *VA = vs + pbase, *VB = VA + nA;
+    const uint32_t d = o - pbase;
+    uint32_t lo = d > nB ? d - nB : 0, hi = min(d, nA);
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (!kv_greater(KA[mid], VA[mid], KB[d - 1 - mid], VB[d - 1 - mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t i = lo, j = d - lo;
+    for (int t = 0; t < MERGE_ITEMS && o + t < pbase + nA + nB; t++) {
+        bool takeA = j >= nB || (i < nA && !kv_greater(KA[i], VA[i], KB[j], VB[j]));
+        if (takeA) { kd[o + t] = KA[i]; vd[o + t] = VA[i]; i++; }
+        else       { kd[o + t] = KB[j]; vd[o + t] = VB[j]; j++; }
+    }
+}
+
+// Sorted (key, index) pairs -> delta adjacency entries, and +1 on the
+// (vertex, label) degree counters.  blockIdx.y = direction.
+__global__ void k_delta_finalize(const unsigned long long *k0, const uint32_t *v0,
+                                 const unsigned long long *k1, const uint32_t *v1,
+                                 uint32_t *dk0, uint32_t *dn0, uint32_t *ds0,
+                                 uint32_t *dk1, uint32_t *dn1, uint32_t *ds1,
+                                 uint32_t *cnt0, uint32_t *cnt1,
+                                 uint32_t n, uint64_t seq0, const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long k = blockIdx.y ? k1[i] : k0[i];
+    const uint32_t v = blockIdx.y ? v1[i] : v0[i];
+    uint32_t *dk = blockIdx.y ? dk1 : dk0, *dn = blockIdx.y ? dn1 : dn0, *ds = blockIdx.y ? ds1 : ds0;
+    const uint32_t key = (uint32_t)(k >> 32);
+    dk[i] = key;
+    dn[i] = (uint32_t)k;
+    ds[i] = (uint32_t)(seq0 + v);
+    atomicAdd(blockIdx.y ? &cnt1[key] : &cnt0[key], 1u);
+}
+
+// ------------------------------------------------------------------ base compaction
+
+constexpr int CBLK = 256, CITEMS = 8, CTILE = CBLK * CITEMS;
+
+// Live entries (seq >= lo) per tile of the base adjacency.
+__global__ void __launch_bounds__(CBLK) k_live_count(const uint32_t *s0, const uint32_t *s1,
+                                                     uint32_t n, uint32_t lo32, uint32_t live_span,
+                                                     uint32_t *bc0, uint32_t *bc1,
+                                                     const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t *s = blockIdx.y ? s1 : s0;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    uint32_t c = 0;
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) {
+        uint32_t i = base + t;
+        c += (i < n && (uint32_t)(s[i] - lo32) < live_span) ? 1u : 0u;
+    }
+    uint32_t total;
+    block_excl_scan(c, &total);
+    if (threadIdx.x == 0) (blockIdx.y ? bc1 : bc0)[blockIdx.x] = total;
+}
+
+// In-place exclusive scan of nb values per direction (one block per
+// direction); writes the grand total to tot[dir].
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *b0, uint32_t *b1, uint32_t nb,
+                                                      uint32_t *tot0, uint32_t *tot1,
+                                                      const uint32_t *status)
+{
+    if (*status) return;
+    uint32_t *b = blockIdx.x ? b1 : b0;
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < nb; base += blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t v = i < nb ? b[i] : 0;
+        uint32_t total;
+        uint32_t ex = block_excl_scan(v, &total);
+        if (i < nb) b[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        uint32_t *tot = blockIdx.x ? tot1 : tot0;
+        if (tot) *tot = carry;
+    }
+}
+
+// Stable compaction of the live base entries into the merge input.
+__global__ void __launch_bounds__(CBLK) k_compact(
+    const uint32_t *k0, const uint32_t *n0, const uint32_t *s0,
+    const uint32_t *k1, const uint32_t *n1, const uint32_t *s1,
+    uint32_t *tk0, uint32_t *tn0, uint32_t *ts0,
+    uint32_t *tk1, uint32_t *tn1, uint32_t *ts1,
+    uint32_t n, uint32_t lo32, uint32_t live_span,
+    const uint32_t *bc0, const uint32_t *bc1, const uint32_t *status)
+{
+    if (*status) return;
+    const bool d1 = blockIdx.y != 0;
+    const uint32_t *K = d1 ? k1 : k0, *N = d1 ? n1 : n0, *S = d1 ? s1 : s0;
+    uint32_t *TK = d1 ? tk1 : tk0, *TN = d1 ? tn1 : tn0, *TS = d1 ? ts1 : ts0;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    uint32_t sv[CITEMS];
+    uint32_t c = 0;
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) {
+        uint32_t i = base + t;
+        sv[t] = i < n ? S[i] : 0;
+        c += (i < n && (uint32_t)(sv[t] - lo32) < live_span) ? 1u : 0u;
+    }
+    uint32_t total;
+    uint32_t pos = block_excl_scan(c, &total) + (d1 ? bc1 : bc0)[blockIdx.x];
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) {
+        uint32_t i = base + t;
+        if (i < n && (uint32_t)(sv[t] - lo32) < live_span) {
+            TK[pos] = K[i];
+            TN[pos] = N[i];
+            TS[pos] = sv[t];
+            pos++;
+        }
+    }
+}
+
+// Merge the compacted base A (nA entries) with the sorted delta B (nB) into
+// the new adjacency; order (key, nbr), base first on ties (older seqs).
+__global__ void k_merge_csr(
+    const uint32_t *ak0, const uint32_t *an0, const uint32_t *as0,
+    const uint32_t *ak1, const uint32_t *an1, const uint32_t *as1,
+    const uint32_t *bk0, const uint32_t *bn0, const uint32_t *bs0,
+    const uint32_t *bk1, const uint32_t *bn1, const uint32_t *bs1,
+    uint32_t *ok0, uint32_t *on0, uint32_t *os0,
+    uint32_t *ok1, uint32_t *on1, uint32_t *os1,
+    uint32_t nA, uint32_t nB, const uint32_t *status)
+{
+    if (*status) return;
+    const bool d1 = blockIdx.y != 0;
+    const uint32_t *AK = d1 ? ak1 : ak0, *AN = d1 ? an1 : an0, *AS = d1 ? as1 : as0;
+    const uint32_t *BK = d1 ? bk1 : bk0, *BN = d1 ? bn1 : bn0, *BS = d1 ? bs1 : bs0;
+    uint32_t *OK = d1 ? ok1 : ok0, *ON = d1 ? on1 : on0, *OS = d1 ? os1 : os0;
+    const uint32_t n = nA + nB;
+    const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
+    if (o >= n) return;
+    auto keyA = [&](uint32_t i) { return ((unsigned long long)AK[i] << 32) | AN[i]; };
+    auto keyB = [&](uint32_t i) { return ((unsigned long long)BK[i] << 32) | BN[i]; };
+    uint32_t lo = o > nB ? o - nB : 0, hi = min(o, nA);
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (keyA(mid) <= keyB(o - 1 - mid)) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t i = lo, j = o - lo;
+    for (int t = 0; t < MERGE_ITEMS && o + t < n; t++) {
+        bool takeA = j >= nB || (i < nA && keyA(i) <= keyB(j));
+        if (takeA) { OK[o + t] = AK[i]; ON[o + t] = AN[i]; OS[o + t] = AS[i]; i++; }
+        else       { OK[o + t] = BK[j]; ON[o + t] = BN[j]; OS[o + t] = BS[j]; j++; }
+    }
+}
+
+// ------------------------------------------------------------------ offsets scan
+
+// Block sums of the (vertex, label) degree counters.
+__global__ void __launch_bounds__(CBLK) k_scan_reduce(const uint32_t *c0, const uint32_t *c1,
+                                                      uint32_t n, uint32_t *bs0, uint32_t *bs1,
+                                                      const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t *c = blockIdx.y ? c1 : c0;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) s += base + t < n ? c[base + t] : 0u;
+    uint32_t total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) (blockIdx.y ? bs1 : bs0)[blockIdx.x] = total;
+}
+
+// offs[i] = sum of counts before i; offs[n] = total (written by the last block).
+__global__ void __launch_bounds__(CBLK) k_scan_apply(const uint32_t *c0, const uint32_t *c1,
+                                                     uint32_t n, const uint32_t *bs0,
+                                                     const uint32_t *bs1, uint32_t *o0,
+                                                     uint32_t *o1, const uint32_t *status)
+{
+    if (*status) return;
+    const bool d1 = blockIdx.y != 0;
+    const uint32_t *c = d1 ? c1 : c0;
+    uint32_t *o = d1 ? o1 : o0;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    uint32_t v[CITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) {
+        v[t] = base + t < n ? c[base + t] : 0u;
+        s += v[t];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_scan(s, &total) + (d1 ? bs1 : bs0)[blockIdx.x];
+#pragma unroll
+    for (int t = 0; t < CITEMS; t++) {
+        if (base + t < n) o[base + t] = run;
+        run += v[t];
+    }
+    if (base < n && base + CITEMS >= n) o[n] = run;   // the thread holding item n-1
+}
+
+// ------------------------------------------------------------------ seeds
+
+// Work units (Sec. V "Work decomposition"): one seed per (edge, query,
+// query edge) with the DEBI bit set, for edges with seq in [seq_lo, seq_lo+n).
+// Packed as (seq32 << 32) | (query << 8) | query edge.
+__global__ void k_seeds_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, uint32_t nq,
+                              uint32_t *const *debi, uint32_t qsel, uint32_t jmask,
+                              unsigned long long *seeds, uint32_t *nseeds, uint32_t seed_cap,
+                              const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t nql = qsel == 0xffffffffu ? nq : 1u;
+    const uint32_t i = t / nql;
+    const uint32_t q = qsel == 0xffffffffu ? t % nql : qsel;
+    uint32_t w = 0;
+    uint32_t s32 = 0;
+    if (i < n) {
+        s32 = (uint32_t)(seq_lo + i);
+        w = debi[q][s32 & cap_mask] & jmask;
+    }
+    const uint32_t c = __popc(w);
+    const int lane = threadIdx.x & 31;
+    uint32_t x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    uint32_t tot = __shfl_sync(FULL, x, 31);
+    uint32_t base = 0;
+    if (lane == 31 && tot) base = atomicAdd(nseeds, tot);
+    base = __shfl_sync(FULL, base, 31);
+    uint32_t pos = base + x - c;
+    while (w) {
+        uint32_t j = __ffs(w) - 1;
+        w &= w - 1;
+        if (pos < seed_cap)
+            seeds[pos] = ((unsigned long long)s32 << 32) | ((unsigned long long)q << 8) | j;
+        pos++;
+    }
+}
+
+// Seeds for an explicit deletion list (seqs given as u64).
+__global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_t cap_mask,
+                             uint32_t nq, uint32_t *const *debi, unsigned long long *seeds,
+                             uint32_t *nseeds, uint32_t seed_cap, const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = t / nq, q = t % nq;
+    uint32_t w = 0, s32 = 0;
+    if (i < n) {
+        s32 = (uint32_t)seqs[i];
+        w = debi[q][s32 & cap_mask];
+    }
+    const uint32_t c = __popc(w);
+    const int lane = threadIdx.x & 31;
+    uint32_t x = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    uint32_t tot = __shfl_sync(FULL, x, 31);
+    uint32_t base = 0;
+    if (lane == 31 && tot) base = atomicAdd(nseeds, tot);
+    base = __shfl_sync(FULL, base, 31);
+    uint32_t pos = base + x - c;
+    while (w) {
+        uint32_t j = __ffs(w) - 1;
+        w &= w - 1;
+        if (pos < seed_cap)
+            seeds[pos] = ((unsigned long long)s32 << 32) | ((unsigned long long)q << 8) | j;
+        pos++;
+    }
+}
+
+// ------------------------------------------------------------------ enumerator
+
+struct EnumParams {
+    const uint32_t *nbr[2];
+    const uint32_t *s32[2];
+    const uint32_t *offs[2];
+    uint32_t L, cap_mask;
+    const uint32_t *ring_src, *ring_dst;
+    uint32_t *const *debi;              // [query] -> word per slot
+    const Plan *plans;                  // [query * MN_MAX_QE + seed edge]
+    const unsigned long long *seeds;
+    const uint32_t *nseeds;
+    uint32_t seed_cap;
+    uint32_t *next_seed;
+    uint32_t lo32, vis_len;             // visible seqs: rel = seq32 - lo32 < vis_len
+    unsigned long long lo;
+    uint32_t brel_lo, brel_len;         // batch seqs, relative to lo
+    const uint8_t *batch_flag;          // optional per-slot batch flags
+    uint32_t sign;                      // 0 new, 1 removed, 2 static count
+    unsigned long long *counts;         // [query * 3 + sign]
+    uint8_t *const *out;                // [query * 2 + sign]
+    const unsigned long long *out_cap;  // [query * 2 + sign]
+    uint32_t count_only;
+    unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
+    uint32_t *status;
+    unsigned long long *work;           // [seeds, entries tested, binds, records]
+};
+
+// Emit the embeddings completed by the valid lanes of one chunk: f/g are
+// lane-distributed (lane u holds f(u), lane e holds rel seq of g(e)); the
+// lane's own candidate supplies vertex `to_new` (if < 16) and edge `qe_new`.
+__device__ __forceinline__ void emit_chunk(const EnumParams &p, int lane, bool ok, uint32_t q,
+                                           uint32_t nv, uint32_t ne, uint32_t rec_bytes,
+                                           uint32_t goff, uint32_t f, uint32_t g,
+                                           uint32_t to_new, uint32_t nb, uint32_t qe_new,
+                                           uint32_t rel, unsigned long long *warp_count)
+{
+    const uint32_t m = __ballot_sync(FULL, ok);
+    if (!m) return;
+    const uint32_t cnt = __popc(m);
+    if (p.count_only) {
+        *warp_count += cnt;
+        return;
+    }
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(&p.counts[q * 3 + p.sign], (unsigned long long)cnt);
+    base = __shfl_sync(FULL, base, 0);
+    const unsigned long long idx = base + __popc(m & lanemask_lt());
+    const bool wr = ok && idx < p.out_cap[q * 2 + p.sign];
+    uint8_t *rec = p.out[q * 2 + p.sign] + idx * rec_bytes;
+    for (uint32_t u = 0; u < nv; u++) {
+        uint32_t fu = __shfl_sync(FULL, f, u);
+        if (u == to_new) fu = nb;
+        if (wr) reinterpret_cast<uint32_t *>(rec)[u] = fu;
+    }
+    if ((nv & 1) && wr) reinterpret_cast<uint32_t *>(rec)[nv] = 0;
+    for (uint32_t e = 0; e < ne; e++) {
+        uint32_t ge = __shfl_sync(FULL, g, e);
+        if (e == qe_new) ge = rel;
+        if (wr) reinterpret_cast<unsigned long long *>(rec + goff)[e] = p.lo + ge;
+    }
+}
+
+// Warp-per-seed backtracking enumerator (Sec. III enumerator, Sec. V work
+// units, matching orders and masks).  Persistent: warps pull seeds from a
+// global counter (pull-based distribution of work units).  Per warp, lane s
+// holds the state of depth s; candidates of a depth are tested 32 at a time,
+// one per lane, against DEBI, liveness, the batch mask, the temporal bounds
+// and injectivity.
+__global__ void __launch_bounds__(256) k_enumerate(EnumParams p)
+{
+    if (*p.status) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nseeds = min(*p.nseeds, p.seed_cap);
+    unsigned long long iters = 0;
+    unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0;
+    for (;;) {
+        uint32_t sid = 0;
+        if (lane == 0) sid = atomicAdd(p.next_seed, 1u);
+        sid = __shfl_sync(FULL, sid, 0);
+        if (sid >= nseeds) break;
+        w_seeds++;
+        const unsigned long long sd = p.seeds[sid];
+        const uint32_t seed32 = (uint32_t)(sd >> 32);
+        const uint32_t q = (uint32_t)(sd >> 8) & 0xffffu;
+        const uint32_t j = (uint32_t)sd & 0xffu;
+        const Plan *pl = &p.plans[q * MN_MAX_QE + j];
+        const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
+        const uint32_t rec_bytes = pl->rec_bytes, goff = pl->goff;
+        // lane s holds step s
+        uint4 sw = make_uint4(0, 0, 0, 0);
+        if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
+        const uint32_t slot0 = seed32 & p.cap_mask;
+        const uint32_t vs = p.ring_src[slot0], vd = p.ring_dst[slot0];
+        const uint32_t ssrc = pl->seed_src, sdst = pl->seed_dst;
+        if (iso && vs == vd) continue;
+        uint32_t f = 0, g = 0;
+        if (lane == (int)ssrc) f = vs;
+        if (lane == (int)sdst) f = vd;
+        const uint32_t rel0 = seed32 - p.lo32;
+        if (lane == (int)j) g = rel0;
+        const uint32_t *__restrict__ debi = p.debi[q];
+        unsigned long long warp_count = 0;
+        if (nsteps == 1) {
+            w_records++;
+            emit_chunk(p, lane, lane == 0, q, nv, ne, rec_bytes, goff, f, g, 0xffu, 0, 0xffu, 0,
+                       &warp_count);
+            if (p.count_only && lane == 0 && warp_count)
+                atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
+            continue;
+        }
+        // per-depth state, lane-distributed
+        uint32_t Lend = 0, Lcur = 0, Lmask = 0, Ltmin = 0, Ltmax = 0, Ltgt = 0, Ldsel = 0;
+        // current depth, uniform
+        uint32_t lvl = 1;
+        uint32_t qe, kind, from, to, dir, avoid, bound_v;
+        int32_t label;
+        uint32_t end, cur, mask, tmin, tmax, tgt, dsel;
+        const uint32_t last = nsteps - 1;
+
+        auto decode = [&](uint32_t s) {
+            uint32_t w0 = __shfl_sync(FULL, sw.x, s);
+            uint32_t w1 = __shfl_sync(FULL, sw.y, s);
+            uint32_t w3 = __shfl_sync(FULL, sw.w, s);
+            qe = w0 & 0xff; kind = (w0 >> 8) & 0xff; from = (w0 >> 16) & 0xff; to = w0 >> 24;
+            dir = w1 & 0xff; avoid = (w1 >> 8) & 0xff; label = (int32_t)(int16_t)(w1 >> 16);
+            bound_v = w3 & 0xffff;
+        };
+        auto open = [&](uint32_t s) {
+            decode(s);
+            const uint32_t w2 = __shfl_sync(FULL, sw.z, s);
+            const uint32_t pred = w2 & 0xffff, succ = w2 >> 16;
+            const uint32_t pe = (pred >> lane) & 1u, se = (succ >> lane) & 1u;
+            tmin = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
+            tmax = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
+            const uint32_t fv = __shfl_sync(FULL, f, from);
+            const uint32_t L = p.L;
+            uint32_t beg;
+            if (kind == K_EXTEND) {
+                dsel = dir;
+                const uint32_t *o = p.offs[dir];
+                if (label >= 0) { beg = o[fv * L + label]; end = o[fv * L + label + 1]; }
+                else            { beg = o[fv * L];         end = o[fv * L + L]; }
+                tgt = 0;
+            } else {
+                const uint32_t tv = __shfl_sync(FULL, f, to);
+                const uint32_t *oa = p.offs[dir], *ob = p.offs[dir ^ 1u];
+                uint32_t a0, a1, b0, b1;
+                if (label >= 0) {
+                    a0 = oa[fv * L + label]; a1 = oa[fv * L + label + 1];
+                    b0 = ob[tv * L + label]; b1 = ob[tv * L + label + 1];
+                } else {
+                    a0 = oa[fv * L]; a1 = oa[fv * L + L];
+                    b0 = ob[tv * L]; b1 = ob[tv * L + L];
+                }
+                if (a1 - a0 <= b1 - b0) { dsel = dir; tgt = tv; beg = a0; end = a1; }
+                else                    { dsel = dir ^ 1u; tgt = fv; beg = b0; end = b1; }
+                if (label >= 0) {
+                    const uint32_t *nb = p.nbr[dsel];
+                    uint32_t lb = warp_lower_bound(nb, beg, end, tgt, lane);
+                    uint32_t ub = warp_lower_bound(nb, lb, end, tgt + 1, lane);
+                    beg = lb; end = ub;
+                }
+            }
+            cur = beg; mask = 0;
+            if (lane == (int)s) { Lend = end; Ltmin = tmin; Ltmax = tmax; Ltgt = tgt; Ldsel = dsel; }
+        };
+        auto restore = [&](uint32_t s) {
+            decode(s);
+            end = __shfl_sync(FULL, Lend, s);
+            cur = __shfl_sync(FULL, Lcur, s);
+            mask = __shfl_sync(FULL, Lmask, s);
+            tmin = __shfl_sync(FULL, Ltmin, s);
+            tmax = __shfl_sync(FULL, Ltmax, s);
+            tgt = __shfl_sync(FULL, Ltgt, s);
+            dsel = __shfl_sync(FULL, Ldsel, s);
+        };
+
+        open(1);
+        while (lvl > 0) {
+            if (++iters > p.max_iters) {
+                if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                break;
+            }
+            if (mask == 0) {
+                if (cur >= end) {               // depth exhausted: backtrack
+                    lvl--;
+                    if (lvl > 0) restore(lvl);
+                    continue;
+                }
+                // test the next 32 candidates, one per lane
+                const uint32_t idx = cur + (uint32_t)lane;
+                bool ok = false;
+                uint32_t nb = 0, rel = 0;
+                if (idx < end) {
+                    nb = p.nbr[dsel][idx];
+                    const uint32_t sv = p.s32[dsel][idx];
+                    rel = sv - p.lo32;
+                    ok = rel < p.vis_len && rel >= tmin && rel < tmax;
+                    if (ok) ok = (debi[sv & p.cap_mask] >> qe) & 1u;
+                    if (ok && avoid) {
+                        ok = (uint32_t)(rel - p.brel_lo) >= p.brel_len;
+                        if (ok && p.batch_flag) ok = p.batch_flag[sv & p.cap_mask] == 0;
+                    }
+                    if (kind == K_CLOSE) ok = ok && nb == tgt;
+                }
+                if (kind == K_EXTEND && iso) {
+                    for (uint32_t bv = bound_v; bv; bv &= bv - 1) {
+                        const uint32_t fw = __shfl_sync(FULL, f, __ffs(bv) - 1);
+                        ok = ok && nb != fw;
+                    }
+                }
+                w_scanned += min(32u, end - cur);
+                cur += 32;
+                if (lvl == last) {
+                    w_records += __popc(__ballot_sync(FULL, ok));
+                    emit_chunk(p, lane, ok, q, nv, ne, rec_bytes, goff, f, g,
+                               kind == K_EXTEND ? to : 0xffu, nb, qe, rel, &warp_count);
+                    continue;
+                }
+                mask = __ballot_sync(FULL, ok);
+                continue;
+            }
+            // bind the next valid candidate of this depth and descend
+            const uint32_t b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            w_binds++;
+            const uint32_t idx = cur - 32 + b;
+            const uint32_t nb = p.nbr[dsel][idx];
+            const uint32_t rel = p.s32[dsel][idx] - p.lo32;
+            if (lane == (int)qe) g = rel;
+            if (kind == K_EXTEND && lane == (int)to) f = nb;
+            if (lane == (int)lvl) { Lcur = cur; Lmask = mask; }
+            lvl++;
+            open(lvl);
+        }
+        if (p.count_only && lane == 0 && warp_count)
+            atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
+        if (*p.status & ST_TIMEOUT) break;
+    }
+    if (lane == 0 && p.work) {
+        atomicAdd(&p.work[0], w_seeds);
+        atomicAdd(&p.work[1], w_scanned);
+        atomicAdd(&p.work[2], w_binds);
+        atomicAdd(&p.work[3], w_records);
+    }
+}
+
+// ------------------------------------------------------------------ expiry / deletion
+
+// Expired edges (seq in [seq_lo, seq_lo + n)): clear their DEBI words
+// (Sec. IV-A memory recycling) and take them off the degree counters.
+__global__ void k_expire(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, uint32_t L, uint32_t nq,
+                         uint32_t *const *debi, const uint32_t *r_src, const uint32_t *r_dst,
+                         const uint8_t *r_label, uint32_t *cnt0, uint32_t *cnt1,
+                         const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t slot = (uint32_t)(seq_lo + i) & cap_mask;
+    for (uint32_t q = 0; q < nq; q++) debi[q][slot] = 0;
+    const uint32_t lab = r_label[slot];
+    atomicSub(&cnt0[r_src[slot] * L + lab], 1u);
+    atomicSub(&cnt1[r_dst[slot] * L + lab], 1u);
+}
+
+// Validate an explicit deletion list: live, not yet deleted, no repeats.
+// Marks the batch flag of each slot.
+__global__ void k_delete_mark(const unsigned long long *seqs, uint32_t n, unsigned long long lo,
+                              unsigned long long hi, uint32_t cap_mask, const uint8_t *r_dead,
+                              uint8_t *batch_flag, uint32_t *status)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const unsigned long long s = seqs[i];
+    if (s < lo || s >= hi) { atomicOr(status, ST_BAD_DELETE); return; }
+    const uint32_t slot = (uint32_t)s & cap_mask;
+    if (r_dead[slot]) { atomicOr(status, ST_BAD_DELETE); return; }
+    unsigned int *w = reinterpret_cast<unsigned int *>(batch_flag + (slot & ~3u));
+    const unsigned int bit = 1u << ((slot & 3u) * 8);
+    const unsigned int old = atomicOr(w, bit);
+    if (old & bit) atomicOr(status, ST_BAD_DELETE);
+}
+
+// Apply (or, on a validation error, only undo the marks of) a deletion list.
+__global__ void k_delete_apply(const unsigned long long *seqs, uint32_t n, uint32_t cap_mask,
+                               uint32_t nq, uint32_t *const *debi, uint8_t *r_dead,
+                               uint8_t *batch_flag, const uint32_t *status)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t slot = (uint32_t)seqs[i] & cap_mask;
+    batch_flag[slot] = 0;
+    if (*status) return;
+    r_dead[slot] = 1;
+    for (uint32_t q = 0; q < nq; q++) debi[q][slot] = 0;
+}
+
+}  // namespace mn

@@ -1,0 +1,1124 @@
+// mn_graph.cu -- host runtime and C ABI (include/mnemonic.h) of the
+// incremental subgraph matcher (Mnemonic, arXiv 2206.09983) on one B300.
+//
+// One graph handle owns, on its device:
+//   an edge ring of capacity C (a power of two >= window + max batch) holding
+//     src, dst, label, attr, ts per edge at slot = seq mod C; slots of
+//     expired edges are reused (memory recycling, Sec. IV-A);
+//   a label-partitioned adjacency per direction: entries (key = v*L + label,
+//     nbr, seq32) sorted by (key, nbr, seq), double-buffered, rebuilt per
+//     batch by merging the sorted batch delta into the live base entries,
+//     plus offsets of every (vertex, label) segment;
+//   per query a DEBI word per slot (Sec. IV-A) and result lists per sign.
+// Every batch runs as one chain of kernels on the graph's stream with a
+// single host synchronisation at the end (to return the counts).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mn_device.cuh"
+
+using namespace mn;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DirArrays {
+    uint32_t *key = nullptr, *nbr = nullptr, *s32 = nullptr;
+};
+
+struct Ctrl {
+    uint32_t status;
+    uint32_t nseeds[3];
+    uint32_t next_seed[3];
+    uint32_t pad_;
+    long long last_ts;
+    unsigned long long work[4];
+    unsigned long long counts[64 * 3];
+};
+
+enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_COUNT };
+
+struct QueryHost {
+    uint32_t nv = 0, ne = 0, iso = 0, temporal = 0;
+    uint32_t rec_bytes = 0, goff = 0;
+    std::vector<uint32_t> vmask;
+    std::vector<mn_qedge> edges;
+    std::vector<std::pair<uint32_t, uint32_t>> prec;
+    Plan plans[MN_MAX_QE];
+    QueryDev dev;
+    uint32_t *debi = nullptr;
+    uint8_t *out[2] = {nullptr, nullptr};
+    unsigned long long out_cap[2] = {0, 0};
+};
+
+uint64_t next_pow2(uint64_t x)
+{
+    uint64_t p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+uint32_t cdiv(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+}  // namespace
+
+struct mn_graph {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint32_t V = 0, L = 0;
+    uint64_t W = 0, max_batch = 0, C = 0;
+    uint32_t cap_mask = 0;
+    uint64_t mem_budget = 0, mem_used = 0;
+    uint32_t max_queries = 0;
+    uint64_t default_out_cap = 0;
+    std::vector<uint32_t> vmask_host;
+    std::map<uint32_t, uint64_t> vmask_hist;
+
+    uint64_t lo = 0, hi = 0, merged_lo = 0, batch_id = 0;
+    long long last_ts = 0;
+    bool have_ts = false;
+
+    uint32_t *d_vmask = nullptr;
+    uint32_t *r_src = nullptr, *r_dst = nullptr;
+    uint8_t *r_label = nullptr, *r_dead = nullptr, *batch_flag = nullptr;
+    int32_t *r_attr = nullptr;
+    int64_t *r_ts = nullptr;
+
+    DirArrays base[2][2];   // [buffer][dir]
+    int cur = 0;
+    DirArrays tmp[2], delta[2];
+    uint32_t *cnt[2] = {nullptr, nullptr}, *offs[2] = {nullptr, nullptr};
+    unsigned long long *dkA[2] = {nullptr, nullptr}, *dkB[2] = {nullptr, nullptr};
+    uint32_t *dvA[2] = {nullptr, nullptr}, *dvB[2] = {nullptr, nullptr};
+    uint32_t *blk[2] = {nullptr, nullptr};
+    uint32_t nblk_cap = 0;
+
+    mn_edge *d_edges = nullptr;
+    unsigned long long *d_seqs = nullptr;
+
+    std::vector<QueryHost> queries;
+    QueryDev *d_queries = nullptr;
+    Plan *d_plans = nullptr;
+    uint32_t **d_debi_ptrs = nullptr;
+    uint8_t **d_out_ptrs = nullptr;
+    unsigned long long *d_out_cap = nullptr;
+
+    unsigned long long *d_seeds[3] = {nullptr, nullptr, nullptr};
+    uint64_t seed_cap[3] = {0, 0, 0};
+
+    Ctrl *d_ctrl = nullptr, *h_ctrl = nullptr;
+    std::vector<uint64_t> count_pos, count_neg;
+    unsigned long long max_iters = ~0ull;
+    int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
+    mn_stats stats{};
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+    cudaEvent_t ev_open = nullptr;
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+mn_status fail(mn_graph *g, mn_status st, const std::string &msg)
+{
+    if (g) g->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(g, MN_ERR_DEVICE, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKL()                                                                         \
+    do {                                                                              \
+        g->stats.kernel_launches++;                                                   \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(g, MN_ERR_DEVICE, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <class T>
+mn_status dalloc(mn_graph *g, T **p, uint64_t count, bool zero = true)
+{
+    const uint64_t bytes = std::max<uint64_t>(count, 1) * sizeof(T);
+    if (g->mem_budget && g->mem_used + bytes > g->mem_budget)
+        return fail(g, MN_ERR_OOM, "device memory budget exceeded");
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(g, MN_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    if (zero) {
+        e = cudaMemsetAsync(q, 0, bytes, g->stream);
+        if (e != cudaSuccess) return fail(g, MN_ERR_DEVICE, cudaGetErrorString(e));
+    }
+    g->mem_used += bytes;
+    g->allocs.push_back(q);
+    *p = reinterpret_cast<T *>(q);
+    return MN_OK;
+}
+
+void dfree(mn_graph *g, void *p, uint64_t bytes)
+{
+    if (!p) return;
+    cudaFree(p);
+    g->mem_used -= std::min(g->mem_used, bytes);
+    g->allocs.erase(std::remove(g->allocs.begin(), g->allocs.end(), p), g->allocs.end());
+}
+
+#define TRY(x)                        \
+    do {                              \
+        mn_status s_ = (x);           \
+        if (s_ != MN_OK) return s_;   \
+    } while (0)
+
+mn_status map_status(mn_graph *g, uint32_t st)
+{
+    if (st & ST_BAD_VERTEX) return fail(g, MN_ERR_INVALID_VERTEX, "vertex id or edge label out of range");
+    if (st & ST_TS_ORDER) return fail(g, MN_ERR_TS_ORDER, "timestamps must be strictly increasing");
+    if (st & ST_BAD_DELETE) return fail(g, MN_ERR_INVALID_ARG, "deleted seq not live, already deleted or repeated");
+    if (st & ST_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, "enumeration work budget exhausted");
+    return MN_OK;
+}
+
+// ---------------------------------------------------------------- stage timing
+
+cudaEvent_t take_event(mn_graph *g)
+{
+    if (!g->ev_pool.empty()) {
+        cudaEvent_t e = g->ev_pool.back();
+        g->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Mark the start of a stage on the graph's stream (timing on only).
+void stage_begin(mn_graph *g)
+{
+    if (!g->timing) return;
+    g->ev_open = take_event(g);
+    cudaEventRecord(g->ev_open, g->stream);
+}
+
+void stage_end(mn_graph *g, int stage)
+{
+    if (!g->timing || !g->ev_open) return;
+    cudaEvent_t e = take_event(g);
+    cudaEventRecord(e, g->stream);
+    g->ev_pending.push_back({stage, {g->ev_open, e}});
+    g->ev_open = nullptr;
+}
+
+// Accumulate the stage times whose end events have completed.
+void collect_timing(mn_graph *g)
+{
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> keep;
+    for (auto &p : g->ev_pending) {
+        if (cudaEventQuery(p.second.second) != cudaSuccess) {
+            cudaGetLastError();
+            keep.push_back(p);
+            continue;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+        double *dst[S_COUNT] = {&g->stats.ms_ingest, &g->stats.ms_adjacency, &g->stats.ms_seeds,
+                                &g->stats.ms_enumerate, &g->stats.ms_expire};
+        *dst[p.first] += ms;
+        g->ev_pool.push_back(p.second.first);
+        g->ev_pool.push_back(p.second.second);
+    }
+    g->ev_pending.swap(keep);
+}
+
+void collect_work(mn_graph *g)
+{
+    g->stats.seeds += g->h_ctrl->work[0];
+    g->stats.entries_scanned += g->h_ctrl->work[1];
+    g->stats.binds += g->h_ctrl->work[2];
+    g->stats.records += g->h_ctrl->work[3];
+    collect_timing(g);
+}
+
+// ---------------------------------------------------------------- query compiler
+
+// Root = the most selective query vertex (Sec. III preprocessing): fewest data
+// vertices whose labels contain the query vertex's labels, per unit of query
+// degree; ties to the smaller id.  Query tree = BFS tree from the root with
+// neighbours in ascending id.  Per starting query edge, the matching order of
+// Sec. V: for a tree edge (u_p, u) the path from u to the root, then the other
+// tree edges in BFS order; for a non-tree edge (u_x, u_y) the tree edges into
+// u_y and u_x, then the path from u_x to the root, then BFS order.  Query edges
+// whose endpoints are both bound are verified right away (verifyNte).
+mn_status compile_query(mn_graph *g, QueryHost &Q)
+{
+    const uint32_t nv = Q.nv, ne = Q.ne;
+    std::vector<uint64_t> cand(nv, 0);
+    for (uint32_t u = 0; u < nv; u++)
+        for (auto &kv : g->vmask_hist)
+            if ((kv.first & Q.vmask[u]) == Q.vmask[u]) cand[u] += kv.second;
+    std::vector<uint32_t> deg(nv, 0);
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> adj(nv);   // (nbr, edge)
+    for (uint32_t e = 0; e < ne; e++) {
+        deg[Q.edges[e].src]++;
+        deg[Q.edges[e].dst]++;
+        adj[Q.edges[e].src].push_back({Q.edges[e].dst, e});
+        adj[Q.edges[e].dst].push_back({Q.edges[e].src, e});
+    }
+    for (auto &a : adj) std::sort(a.begin(), a.end());
+    uint32_t root = 0;
+    for (uint32_t u = 1; u < nv; u++)
+        if ((double)cand[u] / deg[u] < (double)cand[root] / deg[root]) root = u;
+    std::vector<int> parent(nv, -1), tedge(nv, -1), bfs;
+    std::vector<char> seen(nv, 0);
+    bfs.push_back((int)root);
+    seen[root] = 1;
+    for (size_t h = 0; h < bfs.size(); h++) {
+        uint32_t u = (uint32_t)bfs[h];
+        for (auto &ne_ : adj[u])
+            if (!seen[ne_.first]) {
+                seen[ne_.first] = 1;
+                parent[ne_.first] = (int)u;
+                tedge[ne_.first] = (int)ne_.second;
+                bfs.push_back((int)ne_.first);
+            }
+    }
+    if (bfs.size() != nv) return fail(g, MN_ERR_INVALID_ARG, "query graph is not connected");
+    std::vector<char> is_tree(ne, 0);
+    std::vector<int> bfs_edges;
+    for (size_t h = 1; h < bfs.size(); h++) {
+        is_tree[tedge[bfs[h]]] = 1;
+        bfs_edges.push_back(tedge[bfs[h]]);
+    }
+    for (uint32_t j = 0; j < ne; j++) {
+        std::vector<int> order;
+        const uint32_t a = Q.edges[j].src, b = Q.edges[j].dst;
+        auto path_up = [&](int x) {
+            while (x != (int)root) { order.push_back(tedge[x]); x = parent[x]; }
+        };
+        if (is_tree[j]) {
+            int child = parent[b] == (int)a && tedge[b] == (int)j ? (int)b : (int)a;
+            path_up(child);
+        } else {
+            if (b != root) order.push_back(tedge[b]);
+            if (a != root) { order.push_back(tedge[a]); path_up(parent[a]); }
+        }
+        for (int e : bfs_edges) order.push_back(e);
+
+        Plan &P = Q.plans[j];
+        memset(&P, 0, sizeof(P));
+        std::vector<char> placed(ne, 0), bound(nv, 0);
+        uint32_t bound_mask = 0;
+        int ns = 0;
+        auto add_step = [&](uint32_t e, uint8_t kind, uint32_t from, uint32_t to, uint8_t dir) {
+            Step &s = P.step[ns++];
+            s.qe = (uint8_t)e; s.kind = kind; s.from = (uint8_t)from; s.to = (uint8_t)to;
+            s.dir = dir; s.avoid = e < j ? 1 : 0; s.label = (int16_t)Q.edges[e].label;
+            s.bound_v = (uint16_t)bound_mask;
+            uint16_t pred = 0, succ = 0;
+            for (auto &pr : Q.prec) {
+                if (pr.second == e && placed[pr.first]) pred |= (uint16_t)(1u << pr.first);
+                if (pr.first == e && placed[pr.second]) succ |= (uint16_t)(1u << pr.second);
+            }
+            s.pred = pred; s.succ = succ;
+            placed[e] = 1;
+        };
+        auto close_all = [&]() {
+            for (uint32_t e = 0; e < ne; e++)
+                if (!placed[e] && bound[Q.edges[e].src] && bound[Q.edges[e].dst])
+                    add_step(e, K_CLOSE, Q.edges[e].src, Q.edges[e].dst, 0);
+        };
+        add_step(j, K_EXTEND, a, b, 0);   // the seed
+        bound[a] = bound[b] = 1;
+        bound_mask = (1u << a) | (1u << b);
+        close_all();
+        for (size_t k = 0; k < order.size(); k++) {
+            const uint32_t e = (uint32_t)order[k];
+            if (placed[e]) continue;
+            const uint32_t s = Q.edges[e].src, d = Q.edges[e].dst;
+            if (bound[s] && !bound[d]) {
+                add_step(e, K_EXTEND, s, d, 0);
+                bound[d] = 1; bound_mask |= 1u << d;
+            } else if (bound[d] && !bound[s]) {
+                add_step(e, K_EXTEND, d, s, 1);
+                bound[s] = 1; bound_mask |= 1u << s;
+            } else if (!bound[s] && !bound[d]) {
+                return fail(g, MN_ERR_STATE, "matching order reached an unbound edge");
+            }
+            close_all();
+        }
+        if (ns != (int)ne) return fail(g, MN_ERR_STATE, "matching order does not cover the query");
+        P.nsteps = (uint8_t)ne; P.nv = (uint8_t)nv; P.ne = (uint8_t)ne; P.iso = (uint8_t)Q.iso;
+        P.seed_src = (uint8_t)a; P.seed_dst = (uint8_t)b;
+        P.rec_bytes = Q.rec_bytes; P.goff = Q.goff;
+    }
+    memset(&Q.dev, 0, sizeof(Q.dev));
+    Q.dev.ne = ne;
+    for (uint32_t e = 0; e < ne; e++) {
+        QPred &p = Q.dev.e[e];
+        p.label = Q.edges[e].label;
+        p.vmask_src = Q.vmask[Q.edges[e].src];
+        p.vmask_dst = Q.vmask[Q.edges[e].dst];
+        p.attr_lo = Q.edges[e].attr_lo; p.attr_hi = Q.edges[e].attr_hi;
+        p.ts_lo = Q.edges[e].ts_lo; p.ts_hi = Q.edges[e].ts_hi;
+    }
+    return MN_OK;
+}
+
+// ---------------------------------------------------------------- batch pieces
+
+mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
+{
+    if (need <= g->seed_cap[phase]) return MN_OK;
+    dfree(g, g->d_seeds[phase], g->seed_cap[phase] * sizeof(unsigned long long));
+    g->d_seeds[phase] = nullptr;
+    g->seed_cap[phase] = 0;
+    uint64_t cap = next_pow2(need);
+    TRY(dalloc(g, &g->d_seeds[phase], cap, false));
+    g->seed_cap[phase] = cap;
+    return MN_OK;
+}
+
+// Enumeration over seeds of `phase` (0 = new, 1 = removed, 2 = static) on
+// the adjacency buffer `buf`, visible seqs [lo, vis_hi), batch seqs
+// [b_lo, b_hi) or the per-slot batch flags.
+mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t vis_hi, uint64_t b_lo,
+                           uint64_t b_hi, bool use_flags, bool count_only)
+{
+    EnumParams p;
+    memset(&p, 0, sizeof(p));
+    for (int d = 0; d < 2; d++) {
+        p.nbr[d] = g->base[buf][d].nbr;
+        p.s32[d] = g->base[buf][d].s32;
+        p.offs[d] = g->offs[d];
+    }
+    p.L = g->L;
+    p.cap_mask = g->cap_mask;
+    p.ring_src = g->r_src;
+    p.ring_dst = g->r_dst;
+    p.debi = g->d_debi_ptrs;
+    p.plans = g->d_plans;
+    p.seeds = g->d_seeds[phase];
+    p.nseeds = &g->d_ctrl->nseeds[phase];
+    p.seed_cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
+    p.next_seed = &g->d_ctrl->next_seed[phase];
+    p.lo32 = (uint32_t)g->lo;
+    p.vis_len = (uint32_t)(vis_hi - g->lo);
+    p.lo = g->lo;
+    p.brel_lo = (uint32_t)(b_lo - g->lo);
+    p.brel_len = (uint32_t)(b_hi - b_lo);
+    p.batch_flag = use_flags ? g->batch_flag : nullptr;
+    p.sign = (uint32_t)phase;
+    p.counts = g->d_ctrl->counts;
+    p.out = g->d_out_ptrs;
+    p.out_cap = g->d_out_cap;
+    p.count_only = count_only ? 1u : 0u;
+    p.max_iters = g->max_iters;
+    p.status = &g->d_ctrl->status;
+    p.work = g->d_ctrl->work;
+    CK(cudaMemsetAsync(&g->d_ctrl->next_seed[phase], 0, sizeof(uint32_t), g->stream));
+    stage_begin(g);
+    k_enumerate<<<g->enum_grid, 256, 0, g->stream>>>(p);
+    CKL();
+    stage_end(g, S_ENUM);
+    g->stats.enumerate_launches++;
+    return MN_OK;
+}
+
+// Seeds of the edges with seq in [s_lo, s_lo + n) into phase's list.
+mn_status launch_seeds_range(mn_graph *g, int phase, uint64_t s_lo, uint64_t n, uint32_t qsel,
+                             uint32_t jmask)
+{
+    const uint32_t nql = qsel == 0xffffffffu ? (uint32_t)g->queries.size() : 1u;
+    uint64_t total_ne = 0;
+    if (qsel == 0xffffffffu) for (auto &Q : g->queries) total_ne += Q.ne;
+    else total_ne = __builtin_popcount(jmask & ((1u << g->queries[qsel].ne) - 1u));
+    TRY(ensure_seed_cap(g, phase, std::max<uint64_t>(1, n * total_ne)));
+    CK(cudaMemsetAsync(&g->d_ctrl->nseeds[phase], 0, sizeof(uint32_t), g->stream));
+    if (n == 0 || nql == 0) return MN_OK;
+    const uint64_t threads = n * nql;
+    stage_begin(g);
+    k_seeds_range<<<cdiv(threads, 256), 256, 0, g->stream>>>(
+        s_lo, (uint32_t)n, g->cap_mask, (uint32_t)g->queries.size(), g->d_debi_ptrs, qsel, jmask,
+        g->d_seeds[phase], &g->d_ctrl->nseeds[phase], (uint32_t)g->seed_cap[phase],
+        &g->d_ctrl->status);
+    CKL();
+    stage_end(g, S_SEEDS);
+    return MN_OK;
+}
+
+// Rebuild the adjacency into buffer 1-cur: live base entries merged with the
+// batch delta (n entries per direction); offsets from the degree counters.
+mn_status launch_adjacency_update(mn_graph *g, uint64_t n, uint64_t seq0)
+{
+    const uint32_t *st = &g->d_ctrl->status;
+    const uint32_t n_pad = cdiv(n, SORT_TILE) * SORT_TILE;
+    // sort the delta (both directions at once)
+    k_sort_tiles<<<dim3(n_pad / SORT_TILE, 2), 1024, 0, g->stream>>>(g->dkA[0], g->dvA[0], g->dkA[1],
+                                                                      g->dvA[1], st);
+    CKL();
+    unsigned long long *ks[2] = {g->dkA[0], g->dkA[1]}, *kd[2] = {g->dkB[0], g->dkB[1]};
+    uint32_t *vs[2] = {g->dvA[0], g->dvA[1]}, *vd[2] = {g->dvB[0], g->dvB[1]};
+    for (uint64_t R = SORT_TILE; R < n; R *= 2) {
+        const uint32_t threads = cdiv(n, MERGE_ITEMS);
+        k_merge_pass<<<dim3(cdiv(threads, 256), 2), 256, 0, g->stream>>>(
+            ks[0], vs[0], kd[0], vd[0], ks[1], vs[1], kd[1], vd[1], (uint32_t)n, (uint32_t)R, st);
+        CKL();
+        std::swap(ks[0], kd[0]); std::swap(ks[1], kd[1]);
+        std::swap(vs[0], vd[0]); std::swap(vs[1], vd[1]);
+    }
+    k_delta_finalize<<<dim3(cdiv(n, 256), 2), 256, 0, g->stream>>>(
+        ks[0], vs[0], ks[1], vs[1], g->delta[0].key, g->delta[0].nbr, g->delta[0].s32,
+        g->delta[1].key, g->delta[1].nbr, g->delta[1].s32, g->cnt[0], g->cnt[1], (uint32_t)n, seq0, st);
+    CKL();
+    // compact the live base entries
+    const uint64_t n_base = g->hi - g->merged_lo;
+    const uint64_t nA = g->hi - g->lo;
+    const uint32_t lo32 = (uint32_t)g->lo;
+    const uint32_t span = (uint32_t)(g->hi - g->lo);
+    DirArrays *B = g->base[g->cur];
+    if (n_base) {
+        const uint32_t nb = cdiv(n_base, CTILE);
+        k_live_count<<<dim3(nb, 2), CBLK, 0, g->stream>>>(B[0].s32, B[1].s32, (uint32_t)n_base,
+                                                           lo32, span, g->blk[0], g->blk[1], st);
+        CKL();
+        k_scan_blocks<<<2, 1024, 0, g->stream>>>(g->blk[0], g->blk[1], nb, nullptr, nullptr, st);
+        CKL();
+        k_compact<<<dim3(nb, 2), CBLK, 0, g->stream>>>(
+            B[0].key, B[0].nbr, B[0].s32, B[1].key, B[1].nbr, B[1].s32, g->tmp[0].key, g->tmp[0].nbr,
+            g->tmp[0].s32, g->tmp[1].key, g->tmp[1].nbr, g->tmp[1].s32, (uint32_t)n_base, lo32, span,
+            g->blk[0], g->blk[1], st);
+        CKL();
+    }
+    DirArrays *O = g->base[1 - g->cur];
+    const uint64_t nO = nA + n;
+    k_merge_csr<<<dim3(cdiv(cdiv(nO, MERGE_ITEMS), 256), 2), 256, 0, g->stream>>>(
+        g->tmp[0].key, g->tmp[0].nbr, g->tmp[0].s32, g->tmp[1].key, g->tmp[1].nbr, g->tmp[1].s32,
+        g->delta[0].key, g->delta[0].nbr, g->delta[0].s32, g->delta[1].key, g->delta[1].nbr,
+        g->delta[1].s32, O[0].key, O[0].nbr, O[0].s32, O[1].key, O[1].nbr, O[1].s32, (uint32_t)nA,
+        (uint32_t)n, st);
+    CKL();
+    // offsets of the (vertex, label) segments
+    const uint64_t nvl = (uint64_t)g->V * g->L;
+    const uint32_t nbo = cdiv(nvl, CTILE);
+    k_scan_reduce<<<dim3(nbo, 2), CBLK, 0, g->stream>>>(g->cnt[0], g->cnt[1], (uint32_t)nvl, g->blk[0],
+                                                         g->blk[1], st);
+    CKL();
+    k_scan_blocks<<<2, 1024, 0, g->stream>>>(g->blk[0], g->blk[1], nbo, nullptr, nullptr, st);
+    CKL();
+    k_scan_apply<<<dim3(nbo, 2), CBLK, 0, g->stream>>>(g->cnt[0], g->cnt[1], (uint32_t)nvl, g->blk[0],
+                                                        g->blk[1], g->offs[0], g->offs[1], st);
+    CKL();
+    return MN_OK;
+}
+
+mn_status read_ctrl(mn_graph *g)
+{
+    CK(cudaMemcpyAsync(g->h_ctrl, g->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    collect_work(g);
+    CK(cudaMemsetAsync(g->d_ctrl->work, 0, sizeof(g->h_ctrl->work), g->stream));
+    return MN_OK;
+}
+
+// Grow the result lists of `phase` to the exact counts (within the memory
+// budget).  Returns true in *regrown when something was too small.
+mn_status grow_outputs(mn_graph *g, int phase, bool *regrown, bool *over_budget)
+{
+    *regrown = false;
+    for (size_t q = 0; q < g->queries.size(); q++) {
+        QueryHost &Q = g->queries[q];
+        const unsigned long long c = g->h_ctrl->counts[q * 3 + phase];
+        if (c <= Q.out_cap[phase]) continue;
+        const uint64_t cap = next_pow2(c);
+        const uint64_t bytes = cap * Q.rec_bytes;
+        const uint64_t old = Q.out_cap[phase] * Q.rec_bytes;
+        if (g->mem_budget && g->mem_used - old + bytes > g->mem_budget) {
+            *over_budget = true;
+            continue;
+        }
+        dfree(g, Q.out[phase], old);
+        Q.out[phase] = nullptr;
+        Q.out_cap[phase] = 0;
+        TRY(dalloc(g, &Q.out[phase], bytes, false));
+        Q.out_cap[phase] = cap;
+        *regrown = true;
+    }
+    if (*regrown) {
+        std::vector<uint8_t *> ptrs(g->max_queries * 2, nullptr);
+        std::vector<unsigned long long> caps(g->max_queries * 2, 0);
+        for (size_t q = 0; q < g->queries.size(); q++)
+            for (int s = 0; s < 2; s++) {
+                ptrs[q * 2 + s] = g->queries[q].out[s];
+                caps[q * 2 + s] = g->queries[q].out_cap[s];
+            }
+        CK(cudaMemcpyAsync(g->d_out_ptrs, ptrs.data(), ptrs.size() * sizeof(uint8_t *),
+                           cudaMemcpyHostToDevice, g->stream));
+        CK(cudaMemcpyAsync(g->d_out_cap, caps.data(), caps.size() * sizeof(unsigned long long),
+                           cudaMemcpyHostToDevice, g->stream));
+    }
+    return MN_OK;
+}
+
+void fill_result(mn_graph *g, mn_batch_result *out, uint64_t seq_lo, uint64_t seq_hi,
+                 uint64_t ex_lo, uint64_t ex_hi)
+{
+    const size_t nq = g->queries.size();
+    g->count_pos.assign(nq, 0);
+    g->count_neg.assign(nq, 0);
+    for (size_t q = 0; q < nq; q++) {
+        g->count_pos[q] = g->h_ctrl->counts[q * 3 + 0];
+        g->count_neg[q] = g->h_ctrl->counts[q * 3 + 1];
+    }
+    if (!out) return;
+    out->batch_id = g->batch_id;
+    out->seq_lo = seq_lo;
+    out->seq_hi = seq_hi;
+    out->expired_lo = ex_lo;
+    out->expired_hi = ex_hi;
+    out->num_queries = (uint32_t)nq;
+    out->count_pos = g->count_pos.data();
+    out->count_neg = g->count_neg.data();
+}
+
+// Run enumeration phases, re-running any whose lists overflowed after
+// growing them to the exact counts.
+mn_status enumerate_phases(mn_graph *g, const int *phases, const int *bufs, int nph,
+                           uint64_t vis_hi, const uint64_t *blo, const uint64_t *bhi,
+                           bool use_flags, bool count_only, bool *over_budget)
+{
+    TRY(read_ctrl(g));
+    if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
+    if (count_only) return MN_OK;
+    for (int k = 0; k < nph; k++) {
+        bool regrown = false;
+        TRY(grow_outputs(g, phases[k], &regrown, over_budget));
+        if (!regrown) continue;
+        CK(cudaMemsetAsync(&g->d_ctrl->counts[0], 0, sizeof(g->h_ctrl->counts), g->stream));
+        // counts of the other phase must survive: re-run every phase
+        for (int r = 0; r < nph; r++)
+            TRY(launch_enumerate(g, phases[r], bufs[r], vis_hi, blo[r], bhi[r], use_flags, false));
+        TRY(read_ctrl(g));
+        if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
+    }
+    return MN_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
+{
+    mn_graph *g = nullptr;
+    if (!out) return fail(nullptr, MN_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, MN_ERR_INVALID_ARG, "cfg is NULL");
+    if (cfg->num_vertices == 0 || cfg->num_edge_labels == 0 || cfg->num_edge_labels > 256)
+        return fail(nullptr, MN_ERR_INVALID_ARG, "num_vertices must be > 0, num_edge_labels in 1..256");
+    if ((uint64_t)cfg->num_vertices * cfg->num_edge_labels >= 0xffffffffull)
+        return fail(nullptr, MN_ERR_INVALID_ARG, "num_vertices * num_edge_labels must be < 2^32");
+    if (cfg->max_batch == 0 || cfg->max_batch > (1ull << 26))
+        return fail(nullptr, MN_ERR_INVALID_ARG, "max_batch must be in 1..2^26");
+    if (cfg->max_queries == 0 || cfg->max_queries > 64)
+        return fail(nullptr, MN_ERR_INVALID_ARG, "max_queries must be in 1..64");
+    uint64_t need = cfg->window_edges ? cfg->window_edges + cfg->max_batch : cfg->edge_capacity;
+    if (need == 0) return fail(nullptr, MN_ERR_INVALID_ARG, "insert-only graphs need edge_capacity");
+    if (cfg->window_edges && cfg->max_batch > cfg->window_edges)
+        return fail(nullptr, MN_ERR_INVALID_ARG, "max_batch must not exceed window_edges");
+    if (need > (1ull << 30)) return fail(nullptr, MN_ERR_INVALID_ARG, "capacity above 2^30 edges");
+
+    g = new mn_graph();
+    g->device = cfg->device;
+    g->V = cfg->num_vertices;
+    g->L = cfg->num_edge_labels;
+    g->W = cfg->window_edges;
+    g->max_batch = cfg->max_batch;
+    g->C = next_pow2(std::max<uint64_t>(need, 1024));
+    g->cap_mask = (uint32_t)(g->C - 1);
+    g->mem_budget = cfg->mem_budget_bytes;
+    g->max_queries = cfg->max_queries;
+    g->default_out_cap = cfg->out_capacity ? cfg->out_capacity : (1ull << 20);
+    g->vmask_host.assign(g->V, 0);
+    if (cfg->vertex_label_mask)
+        memcpy(g->vmask_host.data(), cfg->vertex_label_mask, sizeof(uint32_t) * g->V);
+    for (uint32_t v = 0; v < g->V; v++) g->vmask_hist[g->vmask_host[v]]++;
+
+    auto bail = [&](mn_status s) {
+        std::string m = g->err;
+        mn_destroy_graph(g);
+        g_create_error = m;
+        return s;
+    };
+    cudaError_t e = cudaSetDevice(g->device);
+    if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
+    if (cfg->cuda_stream) {
+        g->stream = (cudaStream_t)cfg->cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
+        g->own_stream = true;
+    }
+    const uint64_t C = g->C;
+    const uint64_t nvl = (uint64_t)g->V * g->L;
+    mn_status s = MN_OK;
+#define A(x) do { s = (x); if (s != MN_OK) return bail(s); } while (0)
+    A(dalloc(g, &g->d_vmask, g->V));
+    A(dalloc(g, &g->r_src, C, false));
+    A(dalloc(g, &g->r_dst, C, false));
+    A(dalloc(g, &g->r_label, C, false));
+    A(dalloc(g, &g->r_dead, C));
+    A(dalloc(g, &g->batch_flag, C));
+    A(dalloc(g, &g->r_attr, C, false));
+    A(dalloc(g, &g->r_ts, C, false));
+    for (int b = 0; b < 2; b++)
+        for (int d = 0; d < 2; d++) {
+            A(dalloc(g, &g->base[b][d].key, C, false));
+            A(dalloc(g, &g->base[b][d].nbr, C, false));
+            A(dalloc(g, &g->base[b][d].s32, C, false));
+        }
+    const uint64_t mb_pad = (uint64_t)cdiv(g->max_batch, SORT_TILE) * SORT_TILE;
+    for (int d = 0; d < 2; d++) {
+        A(dalloc(g, &g->tmp[d].key, C, false));
+        A(dalloc(g, &g->tmp[d].nbr, C, false));
+        A(dalloc(g, &g->tmp[d].s32, C, false));
+        A(dalloc(g, &g->delta[d].key, g->max_batch, false));
+        A(dalloc(g, &g->delta[d].nbr, g->max_batch, false));
+        A(dalloc(g, &g->delta[d].s32, g->max_batch, false));
+        A(dalloc(g, &g->cnt[d], nvl));
+        A(dalloc(g, &g->offs[d], nvl + 1));
+        A(dalloc(g, &g->dkA[d], mb_pad, false));
+        A(dalloc(g, &g->dkB[d], mb_pad, false));
+        A(dalloc(g, &g->dvA[d], mb_pad, false));
+        A(dalloc(g, &g->dvB[d], mb_pad, false));
+    }
+    g->nblk_cap = cdiv(std::max<uint64_t>(C, nvl), CTILE) + 1;
+    for (int d = 0; d < 2; d++) A(dalloc(g, &g->blk[d], g->nblk_cap));
+    A(dalloc(g, &g->d_edges, g->max_batch, false));
+    A(dalloc(g, &g->d_seqs, g->max_batch, false));
+    A(dalloc(g, &g->d_queries, g->max_queries));
+    A(dalloc(g, &g->d_plans, (uint64_t)g->max_queries * MN_MAX_QE));
+    A(dalloc(g, &g->d_debi_ptrs, g->max_queries));
+    A(dalloc(g, &g->d_out_ptrs, (uint64_t)g->max_queries * 2));
+    A(dalloc(g, &g->d_out_cap, (uint64_t)g->max_queries * 2));
+    A(dalloc(g, &g->d_ctrl, 1));
+#undef A
+    {
+        int nsm = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, 256, 0);
+        if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
+        g->enum_grid = nsm * std::max(per_sm, 1);
+    }
+    e = cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl));
+    if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_OOM); }
+    memset(g->h_ctrl, 0, sizeof(Ctrl));
+    e = cudaMemcpyAsync(g->d_vmask, g->vmask_host.data(), sizeof(uint32_t) * g->V,
+                        cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
+    *out = g;
+    return MN_OK;
+}
+
+void mn_destroy_graph(mn_graph *g)
+{
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (void *p : g->allocs) cudaFree(p);
+    g->allocs.clear();
+    for (auto &p : g->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
+    for (auto e : g->ev_pool) cudaEventDestroy(e);
+    if (g->ev_open) cudaEventDestroy(g->ev_open);
+    if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+const char *mn_last_error(const mn_graph *g)
+{
+    if (!g) return g_create_error.c_str();
+    return g->err.c_str();
+}
+
+mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query_id)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (!d || !query_id || !d->edges) return fail(g, MN_ERR_INVALID_ARG, "NULL argument");
+    if (g->queries.size() >= g->max_queries) return fail(g, MN_ERR_STATE, "max_queries reached");
+    if (d->nv < 2 || d->nv > MN_MAX_QV || d->ne < 1 || d->ne > MN_MAX_QE)
+        return fail(g, MN_ERR_INVALID_ARG, "query needs 2..16 vertices and 1..16 edges");
+    if (d->semantics != MN_ISO && d->semantics != MN_HOMO)
+        return fail(g, MN_ERR_INVALID_ARG, "semantics must be MN_ISO or MN_HOMO");
+    QueryHost Q;
+    Q.nv = d->nv; Q.ne = d->ne;
+    Q.iso = d->semantics == MN_ISO;
+    Q.temporal = d->temporal;
+    Q.vmask.assign(d->nv, 0);
+    if (d->vlabel_mask) memcpy(Q.vmask.data(), d->vlabel_mask, sizeof(uint32_t) * d->nv);
+    Q.edges.assign(d->edges, d->edges + d->ne);
+    for (uint32_t e = 0; e < d->ne; e++) {
+        const mn_qedge &x = Q.edges[e];
+        if (x.src >= d->nv || x.dst >= d->nv || x.src == x.dst)
+            return fail(g, MN_ERR_INVALID_ARG, "query edge endpoints must be distinct and < nv");
+        if (x.label < -1 || x.label >= (int32_t)g->L)
+            return fail(g, MN_ERR_INVALID_ARG, "query edge label must be -1 or < num_edge_labels");
+        for (uint32_t f = 0; f < e; f++)
+            if (Q.edges[f].src == x.src && Q.edges[f].dst == x.dst)
+                return fail(g, MN_ERR_INVALID_ARG, "two query edges with the same (src, dst)");
+    }
+    if (d->temporal == MN_TEMPORAL_CHAIN) {
+        for (uint32_t e = 0; e + 1 < d->ne; e++) Q.prec.push_back({e, e + 1});
+    } else if (d->temporal == MN_TEMPORAL_PAIRS) {
+        if (d->n_prec && !d->prec) return fail(g, MN_ERR_INVALID_ARG, "prec is NULL");
+        for (uint32_t k = 0; k < d->n_prec; k++) {
+            uint32_t a = d->prec[2 * k], b = d->prec[2 * k + 1];
+            if (a >= d->ne || b >= d->ne || a == b)
+                return fail(g, MN_ERR_INVALID_ARG, "precedence pair out of range");
+            Q.prec.push_back({a, b});
+        }
+    } else if (d->temporal != MN_TEMPORAL_NONE) {
+        return fail(g, MN_ERR_INVALID_ARG, "unknown temporal mode");
+    }
+    Q.goff = (4 * Q.nv + 7) / 8 * 8;
+    Q.rec_bytes = Q.goff + 8 * Q.ne;
+    TRY(compile_query(g, Q));
+
+    const uint32_t qid = (uint32_t)g->queries.size();
+    TRY(dalloc(g, &Q.debi, g->C));
+    for (int s = 0; s < 2; s++) {
+        TRY(dalloc(g, &Q.out[s], g->default_out_cap * Q.rec_bytes, false));
+        Q.out_cap[s] = g->default_out_cap;
+    }
+    CK(cudaMemcpyAsync(g->d_queries + qid, &Q.dev, sizeof(QueryDev), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_plans + (uint64_t)qid * MN_MAX_QE, Q.plans, sizeof(Q.plans),
+                       cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_debi_ptrs + qid, &Q.debi, sizeof(uint32_t *), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_out_ptrs + 2 * qid, Q.out, 2 * sizeof(uint8_t *), cudaMemcpyHostToDevice,
+                       g->stream));
+    CK(cudaMemcpyAsync(g->d_out_cap + 2 * qid, Q.out_cap, 2 * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, g->stream));
+    const uint64_t live = g->hi - g->lo;
+    if (live) {
+        k_match_range<<<cdiv(live, 256), 256, 0, g->stream>>>(
+            g->lo, (uint32_t)live, g->cap_mask, g->r_src, g->r_dst, g->r_label, g->r_attr, g->r_ts,
+            g->r_dead, g->d_vmask, g->d_queries + qid, Q.debi);
+        CKL();
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    g->queries.push_back(Q);
+    *query_id = qid;
+    return MN_OK;
+}
+
+mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags,
+                          mn_batch_result *out)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (n && !edges) return fail(g, MN_ERR_INVALID_ARG, "edges is NULL");
+    if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
+    if (!g->W && g->hi + n - g->lo > g->C) return fail(g, MN_ERR_ADMISSION, "edge ring is full");
+    CK(cudaSetDevice(g->device));
+    const bool count_only = (flags & MN_COUNT_ONLY) != 0;
+    const uint64_t hi_new = g->hi + n;
+    const uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
+    CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
+    if (n) {
+        const mn_edge *src = edges;
+        if (!(flags & MN_DEVICE_PTR)) {
+            CK(cudaMemcpyAsync(g->d_edges, edges, n * sizeof(mn_edge), cudaMemcpyHostToDevice, g->stream));
+            src = g->d_edges;
+        }
+        IngestParams ip;
+        memset(&ip, 0, sizeof(ip));
+        ip.edges = src;
+        ip.n = (uint32_t)n;
+        ip.n_pad = cdiv(n, SORT_TILE) * SORT_TILE;
+        ip.seq0 = g->hi;
+        ip.last_ts = g->have_ts ? g->last_ts : INT64_MIN;
+        ip.V = g->V; ip.L = g->L; ip.cap_mask = g->cap_mask;
+        ip.r_src = g->r_src; ip.r_dst = g->r_dst; ip.r_label = g->r_label; ip.r_dead = g->r_dead;
+        ip.r_attr = g->r_attr; ip.r_ts = g->r_ts;
+        ip.vmask = g->d_vmask;
+        ip.nq = (uint32_t)g->queries.size();
+        ip.queries = g->d_queries;
+        ip.debi = g->d_debi_ptrs;
+        for (int d = 0; d < 2; d++) { ip.dkey[d] = g->dkA[d]; ip.dval[d] = g->dvA[d]; }
+        ip.status = &g->d_ctrl->status;
+        ip.last_ts_out = &g->d_ctrl->last_ts;
+        stage_begin(g);
+        k_ingest<<<cdiv(ip.n_pad, 256), 256, 0, g->stream>>>(ip);
+        CKL();
+        stage_end(g, S_INGEST);
+        stage_begin(g);
+        TRY(launch_adjacency_update(g, n, g->hi));
+        stage_end(g, S_ADJ);
+    }
+    const int nbuf = n ? 1 - g->cur : g->cur;
+    int phases[2], bufs[2], nph = 0;
+    uint64_t blo[2], bhi[2];
+    if (n && !g->queries.empty()) {
+        TRY(launch_seeds_range(g, 0, g->hi, n, 0xffffffffu, 0xffffu));
+        TRY(launch_enumerate(g, 0, nbuf, hi_new, g->hi, hi_new, false, count_only));
+        phases[nph] = 0; bufs[nph] = nbuf; blo[nph] = g->hi; bhi[nph] = hi_new; nph++;
+    }
+    if (x && !g->queries.empty()) {
+        TRY(launch_seeds_range(g, 1, g->lo, x, 0xffffffffu, 0xffffu));
+        TRY(launch_enumerate(g, 1, nbuf, hi_new, g->lo, g->lo + x, false, count_only));
+        phases[nph] = 1; bufs[nph] = nbuf; blo[nph] = g->lo; bhi[nph] = g->lo + x; nph++;
+    }
+    bool over_budget = false;
+    const mn_status est = enumerate_phases(g, phases, bufs, nph, hi_new, blo, bhi, false, count_only,
+                                           &over_budget);
+    if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
+    // commit (also after a timeout: the adjacency update ran; counts are partial)
+    const std::string timeout_msg = g->err;
+    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+    const uint64_t seq_lo = g->hi;
+    if (n) {
+        g->cur = 1 - g->cur;
+        g->merged_lo = g->lo;
+        g->last_ts = g->h_ctrl->last_ts;
+        g->have_ts = true;
+    }
+    g->hi = hi_new;
+    const uint64_t ex_lo = g->lo;
+    if (x) {
+        stage_begin(g);
+        k_expire<<<cdiv(x, 256), 256, 0, g->stream>>>(g->lo, (uint32_t)x, g->cap_mask, g->L,
+                                                      (uint32_t)g->queries.size(), g->d_debi_ptrs,
+                                                      g->r_src, g->r_dst, g->r_label, g->cnt[0],
+                                                      g->cnt[1], &g->d_ctrl->status);
+        CKL();
+        stage_end(g, S_EXPIRE);
+        g->lo += x;
+    }
+    g->batch_id++;
+    g->stats.batches++;
+    fill_result(g, out, seq_lo, hi_new, ex_lo, ex_lo + x);
+    if (est == MN_ERR_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, timeout_msg);
+    if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
+    return MN_OK;
+}
+
+mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_t flags,
+                          mn_batch_result *out)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (n && !seqs) return fail(g, MN_ERR_INVALID_ARG, "seqs is NULL");
+    if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
+    CK(cudaSetDevice(g->device));
+    const bool count_only = (flags & MN_COUNT_ONLY) != 0;
+    CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
+    const unsigned long long *ds = reinterpret_cast<const unsigned long long *>(seqs);
+    if (n && !(flags & MN_DEVICE_PTR)) {
+        CK(cudaMemcpyAsync(g->d_seqs, seqs, n * sizeof(uint64_t), cudaMemcpyHostToDevice, g->stream));
+        ds = g->d_seqs;
+    }
+    const uint32_t nq = (uint32_t)g->queries.size();
+    if (n) {
+        k_delete_mark<<<cdiv(n, 256), 256, 0, g->stream>>>(ds, (uint32_t)n, g->lo, g->hi, g->cap_mask,
+                                                           g->r_dead, g->batch_flag, &g->d_ctrl->status);
+        CKL();
+    }
+    int phases[1] = {1}, bufs[1] = {g->cur}, nph = 0;
+    uint64_t blo[1] = {0}, bhi[1] = {0};
+    if (n && nq) {
+        uint64_t total_ne = 0;
+        for (auto &Q : g->queries) total_ne += Q.ne;
+        TRY(ensure_seed_cap(g, 1, n * total_ne));
+        k_seeds_list<<<cdiv(n * nq, 256), 256, 0, g->stream>>>(ds, (uint32_t)n, g->cap_mask, nq,
+                                                                g->d_debi_ptrs, g->d_seeds[1],
+                                                                &g->d_ctrl->nseeds[1],
+                                                                (uint32_t)g->seed_cap[1], &g->d_ctrl->status);
+        CKL();
+        TRY(launch_enumerate(g, 1, g->cur, g->hi, g->lo, g->lo, true, count_only));
+        blo[0] = g->lo; bhi[0] = g->lo;
+        nph = 1;
+    }
+    bool over_budget = false;
+    mn_status st = enumerate_phases(g, phases, bufs, nph, g->hi, blo, bhi, true, count_only, &over_budget);
+    if (n) {
+        k_delete_apply<<<cdiv(n, 256), 256, 0, g->stream>>>(ds, (uint32_t)n, g->cap_mask, nq,
+                                                            g->d_debi_ptrs, g->r_dead, g->batch_flag,
+                                                            &g->d_ctrl->status);
+        CKL();
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    if (st != MN_OK) return st;
+    g->batch_id++;
+    g->stats.batches++;
+    fill_result(g, out, g->hi, g->hi, 0, 0);
+    if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
+    return MN_OK;
+}
+
+mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id, int32_t sign,
+                              uint64_t offset, uint64_t max_records, void *dst, uint32_t dst_flags,
+                              uint64_t *n_written)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (!n_written) return fail(g, MN_ERR_INVALID_ARG, "n_written is NULL");
+    *n_written = 0;
+    if (query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "unknown query id");
+    if (sign != 1 && sign != -1) return fail(g, MN_ERR_INVALID_ARG, "sign must be +1 or -1");
+    if (batch_id != g->batch_id || batch_id == 0)
+        return fail(g, MN_ERR_STATE, "only the last batch's lists are kept");
+    const int s = sign > 0 ? 0 : 1;
+    const QueryHost &Q = g->queries[query_id];
+    const uint64_t total = s == 0 ? g->count_pos[query_id] : g->count_neg[query_id];
+    const uint64_t avail = std::min<uint64_t>(total, Q.out_cap[s]);
+    if (offset >= avail || max_records == 0) return MN_OK;
+    const uint64_t cnt = std::min<uint64_t>(max_records, avail - offset);
+    if (!dst) return fail(g, MN_ERR_INVALID_ARG, "dst is NULL");
+    CK(cudaSetDevice(g->device));
+    CK(cudaMemcpyAsync(dst, Q.out[s] + offset * Q.rec_bytes, cnt * Q.rec_bytes,
+                       (dst_flags & MN_DST_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    *n_written = cnt;
+    return MN_OK;
+}
+
+mn_status mn_record_layout(const mn_graph *g, uint32_t query_id, uint32_t *nv, uint32_t *ne,
+                           uint32_t *record_bytes)
+{
+    if (!g || query_id >= g->queries.size()) return MN_ERR_INVALID_ARG;
+    const QueryHost &Q = g->queries[query_id];
+    if (nv) *nv = Q.nv;
+    if (ne) *ne = Q.ne;
+    if (record_bytes) *record_bytes = Q.rec_bytes;
+    return MN_OK;
+}
+
+mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (!count || query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(g->device));
+    CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
+    const uint64_t live = g->hi - g->lo;
+    TRY(launch_seeds_range(g, 2, g->lo, live, query_id, 1u));
+    TRY(launch_enumerate(g, 2, g->cur, g->hi, g->lo, g->lo, false, true));
+    TRY(read_ctrl(g));
+    if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
+    *count = g->h_ctrl->counts[query_id * 3 + 2];
+    return MN_OK;
+}
+
+mn_status mn_read_debi(mn_graph *g, uint32_t query_id, uint64_t seq_lo, uint64_t seq_hi,
+                       uint32_t *words)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (query_id >= g->queries.size() || seq_hi < seq_lo || (seq_hi > seq_lo && !words))
+        return fail(g, MN_ERR_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(g->device));
+    std::vector<uint32_t> all(g->C);
+    CK(cudaMemcpyAsync(all.data(), g->queries[query_id].debi, g->C * sizeof(uint32_t),
+                       cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    for (uint64_t s = seq_lo; s < seq_hi; s++)
+        words[s - seq_lo] = (s >= g->lo && s < g->hi) ? all[s & g->cap_mask] : 0u;
+    return MN_OK;
+}
+
+mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *key, uint32_t *nbr,
+                            uint64_t *seq, uint64_t *n)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (dir > 1 || !n) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
+    CK(cudaSetDevice(g->device));
+    const uint64_t m = g->hi - g->merged_lo;
+    std::vector<uint32_t> k(m), b(m), s(m);
+    std::vector<uint8_t> dead(g->C);
+    const DirArrays &D = g->base[g->cur][dir];
+    if (m) {
+        CK(cudaMemcpyAsync(k.data(), D.key, m * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(b.data(), D.nbr, m * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(s.data(), D.s32, m * 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaMemcpyAsync(dead.data(), g->r_dead, g->C, cudaMemcpyDeviceToHost, g->stream));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    uint64_t w = 0;
+    for (uint64_t i = 0; i < m; i++) {
+        const uint64_t full = g->lo + (uint32_t)(s[i] - (uint32_t)g->lo);
+        if ((uint32_t)(s[i] - (uint32_t)g->lo) >= (uint32_t)(g->hi - g->lo)) continue;
+        if (dead[full & g->cap_mask]) continue;
+        if (w < cap) {
+            if (key) key[w] = k[i];
+            if (nbr) nbr[w] = b[i];
+            if (seq) seq[w] = full;
+        }
+        w++;
+    }
+    *n = w;
+    if (w > cap) return fail(g, MN_ERR_INVALID_ARG, "arrays too small");
+    return MN_OK;
+}
+
+mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi, uint32_t *num_queries)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    if (seq_lo) *seq_lo = g->lo;
+    if (seq_hi) *seq_hi = g->hi;
+    if (num_queries) *num_queries = (uint32_t)g->queries.size();
+    return MN_OK;
+}
+
+mn_status mn_set_timing(mn_graph *g, int enable)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    g->timing = enable != 0;
+    return MN_OK;
+}
+
+mn_status mn_get_stats(const mn_graph *cg, mn_stats *out)
+{
+    if (!cg || !out) return MN_ERR_INVALID_ARG;
+    mn_graph *g = const_cast<mn_graph *>(cg);
+    CK(cudaSetDevice(g->device));
+    CK(cudaStreamSynchronize(g->stream));
+    collect_timing(g);
+    *out = g->stats;
+    return MN_OK;
+}
+
+mn_status mn_reset_stats(mn_graph *g)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    CK(cudaSetDevice(g->device));
+    CK(cudaStreamSynchronize(g->stream));
+    collect_timing(g);
+    g->stats = mn_stats{};
+    return MN_OK;
+}
+
+// Test hook: per-warp loop budget of the enumerator (0 restores no limit).
+// A tiny budget makes a bounded device loop give up and report MN_ERR_TIMEOUT.
+mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    g->max_iters = max_iters ? max_iters : ~0ull;
+    return MN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,330 @@
+"""Python binding of the C ABI in include/mnemonic.h (ctypes; marshalling only).
+
+Every step of the matching path runs in the CUDA library libmnemonic.so built
+from csrc/; this module only converts arguments.  If the library has not been
+built, every call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmnemonic.so")
+
+MN_OK = 0
+STATUS_NAMES = {
+    -1: "MN_ERR_INVALID_ARG", -2: "MN_ERR_INVALID_VERTEX", -3: "MN_ERR_TS_ORDER",
+    -4: "MN_ERR_OOM", -5: "MN_ERR_ADMISSION", -6: "MN_ERR_OUTPUT_OVERFLOW",
+    -7: "MN_ERR_TIMEOUT", -8: "MN_ERR_DEVICE", -9: "MN_ERR_STATE",
+}
+MN_ISO, MN_HOMO = 0, 1
+MN_TEMPORAL = {"none": 0, "chain": 1, "pairs": 2}
+MN_DEVICE_PTR = 0x1
+MN_COUNT_ONLY = 0x2
+MN_DST_DEVICE = 0x1
+MN_MAX_QV = 16
+MN_MAX_QE = 16
+
+EDGE_DTYPE = np.dtype([("src", "<u4"), ("dst", "<u4"), ("label", "<u4"),
+                       ("attr", "<i4"), ("ts", "<i8")])
+
+EXPORTS = [
+    "mn_create_graph", "mn_destroy_graph", "mn_register_query", "mn_insert_batch",
+    "mn_delete_batch", "mn_fetch_embeddings", "mn_record_layout", "mn_count_static",
+    "mn_read_debi", "mn_read_adjacency", "mn_graph_info", "mn_set_work_budget",
+    "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_last_error",
+]
+
+
+class MnError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Config(C.Structure):
+    _fields_ = [("num_vertices", C.c_uint32), ("num_edge_labels", C.c_uint32),
+                ("vertex_label_mask", C.c_void_p), ("window_edges", C.c_uint64),
+                ("max_batch", C.c_uint64), ("edge_capacity", C.c_uint64),
+                ("out_capacity", C.c_uint64), ("mem_budget_bytes", C.c_uint64),
+                ("max_queries", C.c_uint32), ("device", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class _QEdge(C.Structure):
+    _fields_ = [("src", C.c_uint32), ("dst", C.c_uint32), ("label", C.c_int32),
+                ("attr_lo", C.c_int32), ("attr_hi", C.c_int32), ("pad_", C.c_int32),
+                ("ts_lo", C.c_int64), ("ts_hi", C.c_int64)]
+
+
+class _QueryDesc(C.Structure):
+    _fields_ = [("nv", C.c_uint32), ("ne", C.c_uint32), ("vlabel_mask", C.c_void_p),
+                ("edges", C.POINTER(_QEdge)), ("semantics", C.c_uint32),
+                ("temporal", C.c_uint32), ("n_prec", C.c_uint32), ("prec", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("batches", C.c_uint64),
+                ("enumerate_launches", C.c_uint64), ("ms_ingest", C.c_double),
+                ("ms_adjacency", C.c_double), ("ms_seeds", C.c_double),
+                ("ms_enumerate", C.c_double), ("ms_expire", C.c_double),
+                ("seeds", C.c_uint64), ("entries_scanned", C.c_uint64),
+                ("binds", C.c_uint64), ("records", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _BatchResult(C.Structure):
+    _fields_ = [("batch_id", C.c_uint64), ("seq_lo", C.c_uint64), ("seq_hi", C.c_uint64),
+                ("expired_lo", C.c_uint64), ("expired_hi", C.c_uint64),
+                ("num_queries", C.c_uint32), ("count_pos", C.POINTER(C.c_uint64)),
+                ("count_neg", C.POINTER(C.c_uint64))]
+
+
+assert C.sizeof(_QEdge) == 40 and EDGE_DTYPE.itemsize == 24
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libmnemonic.so (raises if it is missing: no CPU fallback exists)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library {p} is not built; run paper_2206_09983_b300.build.build()")
+    lib = C.CDLL(p)
+    S = C.c_int32
+    P = C.c_void_p
+    U64 = C.c_uint64
+    sig = {
+        "mn_create_graph": (S, [C.POINTER(_Config), C.POINTER(P)]),
+        "mn_destroy_graph": (None, [P]),
+        "mn_register_query": (S, [P, C.POINTER(_QueryDesc), C.POINTER(C.c_uint32)]),
+        "mn_insert_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
+        "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
+        "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
+                                    C.POINTER(U64)]),
+        "mn_record_layout": (S, [P, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                                 C.POINTER(C.c_uint32)]),
+        "mn_count_static": (S, [P, C.c_uint32, C.POINTER(U64)]),
+        "mn_read_debi": (S, [P, C.c_uint32, U64, U64, P]),
+        "mn_read_adjacency": (S, [P, C.c_uint32, U64, P, P, P, C.POINTER(U64)]),
+        "mn_graph_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(C.c_uint32)]),
+        "mn_set_work_budget": (S, [P, U64]),
+        "mn_set_timing": (S, [P, C.c_int32]),
+        "mn_get_stats": (S, [P, C.POINTER(Stats)]),
+        "mn_reset_stats": (S, [P]),
+        "mn_last_error": (C.c_char_p, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def edges_from_stream(stream: dict, lo: int, hi: int) -> np.ndarray:
+    """Pack stream edges [lo, hi) into the C ABI's 24-byte mn_edge records."""
+    a = np.empty(hi - lo, dtype=EDGE_DTYPE)
+    a["src"] = stream["src"][lo:hi]
+    a["dst"] = stream["dst"][lo:hi]
+    a["label"] = stream["label"][lo:hi]
+    a["attr"] = stream["attr"][lo:hi]
+    a["ts"] = stream["ts"][lo:hi]
+    return a
+
+
+@dataclass
+class BatchResult:
+    batch_id: int
+    seq_lo: int
+    seq_hi: int
+    expired_lo: int
+    expired_hi: int
+    count_pos: list
+    count_neg: list
+
+
+class Graph:
+    """One streaming data graph on one CUDA device (mn_graph handle)."""
+
+    def __init__(self, num_vertices: int, num_edge_labels: int, vmask=None, window: int = 0,
+                 max_batch: int = 1 << 16, edge_capacity: int = 0, out_capacity: int = 0,
+                 mem_budget: int = 0, max_queries: int = 8, device: int = 0, stream: int = 0):
+        self._lib = load()
+        self._vmask = None if vmask is None else np.ascontiguousarray(vmask, dtype=np.uint32)
+        cfg = _Config(num_vertices, num_edge_labels,
+                      None if self._vmask is None else self._vmask.ctypes.data,
+                      window, max_batch, edge_capacity, out_capacity, mem_budget, max_queries,
+                      device, stream or None)
+        h = C.c_void_p()
+        st = self._lib.mn_create_graph(C.byref(cfg), C.byref(h))
+        if st != MN_OK:
+            raise MnError(st, self._lib.mn_last_error(None).decode())
+        self._h = h
+        self.layouts = []
+        self.last = None
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, st):
+        if st != MN_OK:
+            raise MnError(st, self._lib.mn_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mn_destroy_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -------------------------------------------------------------- queries
+    def register_query(self, q: dict) -> int:
+        ne = len(q["edges"])
+        edges = (_QEdge * ne)()
+        for i, (s, d, lab, alo, ahi, tlo, thi) in enumerate(q["edges"]):
+            edges[i] = _QEdge(s, d, lab, alo, ahi, 0, tlo, thi)
+        vm = np.ascontiguousarray(q["vmask"], dtype=np.uint32)
+        prec = np.ascontiguousarray(np.array(q.get("prec", []), dtype=np.uint32).reshape(-1))
+        desc = _QueryDesc(q["nv"], ne, vm.ctypes.data, edges, MN_ISO if q["iso"] else MN_HOMO,
+                          MN_TEMPORAL[q["temporal"]], len(q.get("prec", [])),
+                          prec.ctypes.data if prec.size else None)
+        qid = C.c_uint32()
+        self._check(self._lib.mn_register_query(self._h, C.byref(desc), C.byref(qid)))
+        nv, nee, rb = C.c_uint32(), C.c_uint32(), C.c_uint32()
+        self._check(self._lib.mn_record_layout(self._h, qid.value, C.byref(nv), C.byref(nee),
+                                               C.byref(rb)))
+        self.layouts.append((nv.value, nee.value, rb.value))
+        return qid.value
+
+    # -------------------------------------------------------------- batches
+    def _result(self, r: _BatchResult) -> BatchResult:
+        nq = r.num_queries
+        res = BatchResult(r.batch_id, r.seq_lo, r.seq_hi, r.expired_lo, r.expired_hi,
+                          [r.count_pos[i] for i in range(nq)], [r.count_neg[i] for i in range(nq)])
+        self.last = res
+        return res
+
+    def insert(self, edges, count_only: bool = False, device_ptr: int | None = None,
+               n: int | None = None) -> BatchResult:
+        """Insert a batch: a numpy EDGE_DTYPE array (host), or a device pointer
+        to n packed mn_edge records (device_ptr, n)."""
+        flags = MN_COUNT_ONLY if count_only else 0
+        r = _BatchResult()
+        if device_ptr is not None:
+            st = self._lib.mn_insert_batch(self._h, C.c_void_p(device_ptr), n, flags | MN_DEVICE_PTR,
+                                           C.byref(r))
+        else:
+            a = np.ascontiguousarray(edges, dtype=EDGE_DTYPE)
+            st = self._lib.mn_insert_batch(self._h, a.ctypes.data if len(a) else None, len(a),
+                                           flags, C.byref(r))
+        self._check(st)
+        return self._result(r)
+
+    def insert_ptr(self, ptr: int, n: int, flags: int = 0) -> BatchResult:
+        """Insert n packed mn_edge records at host address ptr (e.g. pinned)."""
+        r = _BatchResult()
+        self._check(self._lib.mn_insert_batch(self._h, C.c_void_p(ptr), n, flags, C.byref(r)))
+        return self._result(r)
+
+    def delete(self, seqs, count_only: bool = False) -> BatchResult:
+        a = np.ascontiguousarray(seqs, dtype=np.uint64)
+        r = _BatchResult()
+        flags = MN_COUNT_ONLY if count_only else 0
+        self._check(self._lib.mn_delete_batch(self._h, a.ctypes.data if len(a) else None, len(a),
+                                              flags, C.byref(r)))
+        return self._result(r)
+
+    def fetch(self, qid: int, sign: int, offset: int = 0, max_records: int | None = None):
+        """Records of the last batch as (vertices [n, nv] uint32, seqs [n, ne] uint64)."""
+        nv, ne, rb = self.layouts[qid]
+        total = (self.last.count_pos if sign > 0 else self.last.count_neg)[qid]
+        m = total - offset if max_records is None else max_records
+        m = max(0, min(m, total - offset))
+        buf = np.empty(m * rb, dtype=np.uint8)
+        nw = C.c_uint64()
+        self._check(self._lib.mn_fetch_embeddings(self._h, self.last.batch_id, qid, sign, offset, m,
+                                                  buf.ctypes.data if m else None, 0, C.byref(nw)))
+        n = nw.value
+        goff = (4 * nv + 7) // 8 * 8
+        rows = buf[: n * rb].reshape(n, rb)
+        verts = rows[:, : 4 * nv].copy().view(np.uint32).reshape(n, nv)
+        seqs = rows[:, goff: goff + 8 * ne].copy().view(np.uint64).reshape(n, ne)
+        return verts, seqs
+
+    def fetch_rows(self, qid: int, sign: int) -> np.ndarray:
+        """Sorted uint64 rows (f..., seq...) -- the oracle's row format."""
+        v, s = self.fetch(qid, sign)
+        rows = np.concatenate([v.astype(np.uint64), s], axis=1)
+        if len(rows):
+            rows = rows[np.lexsort(rows.T[::-1])]
+        return rows
+
+    def fetch_device(self, qid: int, sign: int, dst_ptr: int, offset: int = 0,
+                     max_records: int = 0) -> int:
+        nw = C.c_uint64()
+        self._check(self._lib.mn_fetch_embeddings(self._h, self.last.batch_id, qid, sign, offset,
+                                                  max_records, C.c_void_p(dst_ptr), MN_DST_DEVICE,
+                                                  C.byref(nw)))
+        return nw.value
+
+    # -------------------------------------------------------------- inspection
+    def count_static(self, qid: int) -> int:
+        c = C.c_uint64()
+        self._check(self._lib.mn_count_static(self._h, qid, C.byref(c)))
+        return c.value
+
+    def read_debi(self, qid: int, lo: int, hi: int) -> np.ndarray:
+        out = np.zeros(hi - lo, dtype=np.uint32)
+        self._check(self._lib.mn_read_debi(self._h, qid, lo, hi,
+                                           out.ctypes.data if hi > lo else None))
+        return out
+
+    def read_adjacency(self, direction: int):
+        n = C.c_uint64()
+        st = self._lib.mn_read_adjacency(self._h, direction, 0, None, None, None, C.byref(n))
+        if st != MN_OK and n.value == 0:
+            self._check(st)
+        m = n.value
+        k = np.zeros(m, dtype=np.uint32)
+        b = np.zeros(m, dtype=np.uint32)
+        s = np.zeros(m, dtype=np.uint64)
+        self._check(self._lib.mn_read_adjacency(self._h, direction, m, k.ctypes.data, b.ctypes.data,
+                                                s.ctypes.data, C.byref(n)))
+        return k, b, s
+
+    def info(self):
+        lo, hi, nq = C.c_uint64(), C.c_uint64(), C.c_uint32()
+        self._check(self._lib.mn_graph_info(self._h, C.byref(lo), C.byref(hi), C.byref(nq)))
+        return lo.value, hi.value, nq.value
+
+    def set_work_budget(self, max_iters: int):
+        self._check(self._lib.mn_set_work_budget(self._h, max_iters))
+
+    def set_timing(self, on: bool):
+        self._check(self._lib.mn_set_timing(self._h, 1 if on else 0))
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.mn_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def reset_stats(self):
+        self._check(self._lib.mn_reset_stats(self._h))
