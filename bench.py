@@ -1,0 +1,334 @@
+#!/usr/bin/env python
+"""Benchmark of the incremental matching hot path (Mnemonic, arXiv 2206.09983).
+
+Metric: inserted edges per second (and p50/p99 batch latency) at exact counts
+on the sliding-window R-MAT workload: 2^20 vertices, 2^24 edges, window 2^22,
+batches of 65,536 insertions each expiring 65,536 edges, four standing queries
+(4-vertex path, 4-cycle, 5-star, 6-vertex tree; isomorphism; increasing
+timestamps).  One step = one batch through the whole path: ingest and
+edgeMatcher, adjacency update, work units, enumeration of new embeddings,
+enumeration of expired embeddings, DEBI clear.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank runs an independent replica of the stream
+(the path does not shard; weak scaling); value = sum over ranks.
+--impl reference times the CPU oracle on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "inserted edges/sec and p99 batch latency at exact counts"
+UNIT = "edges/s"
+CTRL_NOTE = "working set > 126 MB L2 (edge ring 176 MB, adjacency 2 x 2 x 96 MB); no flush"
+
+
+def env_rank():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+            if k in d:
+                return float(d[k]), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+
+def oracle_sample(stream, queries, W, B, batch_index, sample, seed=7):
+    """Time the CPU oracle on `sample` edges of one batch of the window
+    stream: dS+ (embeddings containing a sampled new edge) for every query."""
+    from oracle import oracle
+    lo = batch_index * B
+    hi_new = lo + W + B
+    rng = np.random.default_rng(seed + batch_index)
+    pick = rng.choice(B, size=sample, replace=False)
+    mask = np.zeros(hi_new - lo, dtype=np.uint8)
+    mask[W + pick] = 1
+    t = time.perf_counter()
+    rows = 0
+    for q in queries:
+        rows += len(oracle.delta(stream, lo, hi_new, 0, 0, q, batch_mask=mask))
+    return time.perf_counter() - t, rows
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2206_09983_b300 import workloads
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    stream = workloads.rmat20_stream()
+    qs = workloads.rmat20_queries()
+    times, edges = [], 0
+    for k in range(args.warmup + args.steps):
+        dt, _ = oracle_sample(stream, qs, W, B, k, args.ref_sample)
+        if k >= args.warmup:
+            times.append(dt)
+            edges += args.ref_sample
+    total = sum(times)
+    value = edges / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": w["name"], "vertices": 1 << w["scale"], "window": W, "batch": B,
+                   "queries": workloads.QUERY_NAMES},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.ref_sample} random inserted edges per batch (dS+ of all 4 "
+                                   f"queries, adjacency rebuild included), batches {args.warmup}.."
+                                   f"{args.warmup + args.steps - 1} of the window stream"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=256)
+    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return rc
+
+    import torch
+    from paper_2206_09983_b300 import build, workloads
+    from paper_2206_09983_b300 import mnemonic as M
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    K, WU = args.steps, max(3, args.warmup)
+    need = W + B * (2 * (WU + K) + 2)
+    stream = workloads.rmat20_stream()
+    n = len(stream["src"])
+    assert n >= need, "stream too short for the requested steps"
+    packed = M.edges_from_stream(stream, 0, n)
+    d_edges = torch.from_numpy(packed.view(np.uint8)).to(dev)
+    base_ptr = d_edges.data_ptr()
+    qs = workloads.rmat20_queries()
+    cur_stream = torch.cuda.current_stream(dev)
+    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
+                window=W, max_batch=B, max_queries=len(qs), device=local,
+                stream=cur_stream.cuda_stream, out_capacity=1 << 21)
+    for lo in range(0, W, B):                                   # preload the window
+        g.insert(None, device_ptr=base_ptr + 24 * lo, n=B, count_only=True)
+    for q in qs:
+        g.register_query(q)
+    pos = W
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-resident run (value)
+    for _ in range(WU):
+        g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+        pos += B
+    g.set_timing(True)
+    g.reset_stats()
+    barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, counts = [], []
+    ev0.record(cur_stream)
+    for _ in range(K):
+        t0 = time.perf_counter()
+        r = g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+        lat.append(time.perf_counter() - t0)
+        counts.append((sum(r.count_pos), sum(r.count_neg)))
+        pos += B
+    ev1.record(cur_stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier()
+    dev_ms = ev0.elapsed_time(ev1)
+    st = g.stats()
+    g.set_timing(False)
+
+    # ---- end-to-end run through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(packed.view(np.uint8)[24 * pos: 24 * (pos + B * (WU + K))].copy())
+        host = host.pin_memory()
+        hp = host.data_ptr()
+        for k in range(WU):
+            g.insert_ptr(hp + 24 * B * k, B)
+        st0 = g.stats()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        elat = []
+        for k in range(WU, WU + K):
+            t1 = time.perf_counter()
+            g.insert_ptr(hp + 24 * B * k, B)
+            elat.append(time.perf_counter() - t1)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        st1 = g.stats()
+        e2e = {"value": K * B / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // K,
+               "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // K,
+               "p50_ms": 1e3 * statistics.median(elat),
+               "p99_ms": 1e3 * float(np.percentile(elat, 99))}
+        pos += B * (WU + K)
+    g.close()
+
+    # ---- aggregate over ranks (max time)
+    dev_s = dev_ms / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dev_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_s = float(t.item())
+    value = world * K * B / dev_s
+
+    # ---- roofline of the dominant stage, from the live event timings
+    peak, peak_kind = measured_peaks()
+    stage_ms = {"enumerate": st["ms_enumerate"], "adjacency": st["ms_adjacency"],
+                "ingest": st["ms_ingest"], "seeds": st["ms_seeds"], "expire": st["ms_expire"]}
+    rec_bytes = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
+    enum_bytes = (st["entries_scanned"] * 12 + st["records"] * (sum(rec_bytes) / len(rec_bytes))
+                  + st["seeds"] * 16)
+    launches = max(1, st["enumerate_launches"])
+    enum_ms_per = st["ms_enumerate"] / launches
+    roof = {"kernel": "k_enumerate", "bound": "hbm",
+            "achieved": (enum_bytes / launches) / (enum_ms_per / 1e3) / 1e9 if enum_ms_per else None,
+            "peak": peak, "unit": "GB/s", "traffic": None,
+            "peak_source": f"{peak_kind} HBM copy bandwidth",
+            "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per}
+    roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
+    nq = len(qs)
+    adj_bytes_per_batch = 2 * (2 * (W + B) * 12)     # read + write of both directions' entries
+    adj = {"kernel": "adjacency update (sort+compact+merge+offsets)",
+           "ms_per_batch": st["ms_adjacency"] / K,
+           "achieved": adj_bytes_per_batch / (st["ms_adjacency"] / K / 1e3) / 1e9 if st["ms_adjacency"] else None,
+           "unit": "GB/s", "bytes_per_batch": adj_bytes_per_batch}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": WU,
+        "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": w["name"], "vertices": 1 << w["scale"], "edges": w["num_edges"],
+                   "window": W, "batch": B, "queries": workloads.QUERY_NAMES,
+                   "semantics": "isomorphism, increasing timestamps", "l2": CTRL_NOTE,
+                   "path": "plain GPU path (per-batch launches, paper matching order)"},
+        "latency_ms": {"p50": 1e3 * statistics.median(lat), "p99": 1e3 * float(np.percentile(lat, 99)),
+                       "max": 1e3 * max(lat)},
+        "embeddings_per_step": {"new": float(np.mean([c[0] for c in counts])),
+                                "removed": float(np.mean([c[1] for c in counts]))},
+        "stage_ms_per_step": {k: v / K for k, v in stage_ms.items()},
+        "work_per_step": {k: st[k] / K for k in ("seeds", "entries_scanned", "binds", "records")},
+        "gpu_launches": st["kernel_launches"],
+        "roofline": roof,
+        "adjacency_roofline": adj,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        dt, rows = oracle_sample(stream, qs, W, B, (pos - W) // B - 1, args.cpu_sample)
+        line["cpu_baseline"] = {
+            "value": args.cpu_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{args.cpu_sample} random inserted edges of one batch, dS+ of all {nq} "
+                      f"queries on the {W}-edge window (adjacency rebuild included), "
+                      f"single-threaded C oracle; {rows} embeddings, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -218,6 +218,8 @@ typedef struct {
     uint64_t entries_scanned;
     uint64_t binds;
     uint64_t records;
+    uint64_t h2d_bytes;            /* bytes the library copied host -> device */
+    uint64_t d2h_bytes;            /* bytes copied device -> host (counts, status) */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

@@ -531,6 +531,7 @@ mn_status read_ctrl(mn_graph *g)
 {
     CK(cudaMemcpyAsync(g->h_ctrl, g->d_ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    g->stats.d2h_bytes += sizeof(Ctrl);
     collect_work(g);
     CK(cudaMemsetAsync(g->d_ctrl->work, 0, sizeof(g->h_ctrl->work), g->stream));
     return MN_OK;
@@ -846,6 +847,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         const mn_edge *src = edges;
         if (!(flags & MN_DEVICE_PTR)) {
             CK(cudaMemcpyAsync(g->d_edges, edges, n * sizeof(mn_edge), cudaMemcpyHostToDevice, g->stream));
+            g->stats.h2d_bytes += n * sizeof(mn_edge);
             src = g->d_edges;
         }
         IngestParams ip;
@@ -932,6 +934,7 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
     const unsigned long long *ds = reinterpret_cast<const unsigned long long *>(seqs);
     if (n && !(flags & MN_DEVICE_PTR)) {
         CK(cudaMemcpyAsync(g->d_seqs, seqs, n * sizeof(uint64_t), cudaMemcpyHostToDevice, g->stream));
+        g->stats.h2d_bytes += n * sizeof(uint64_t);
         ds = g->d_seqs;
     }
     const uint32_t nq = (uint32_t)g->queries.size();

@@ -1,0 +1,76 @@
+"""Seeded rejection search for the labels of the rmat20_window queries.
+
+Runs only the CPU oracle.  For each shape (4-vertex path, 4-cycle, 5-star,
+6-vertex tree; isomorphism; timestamps increasing along the query edges) it
+draws edge labels from the stream's own label frequencies (Zipf(1.2) over 8)
+and, per query vertex, either one of the 4 vertex labels or "any", then
+estimates |dS+| of the first
+batch after the preloaded window from a random sample of the batch's edges
+(embeddings that contain a sampled edge, scaled to the whole batch).  The
+first draw whose estimate lies in [2^16, 2^20] is kept (if none does in 200
+draws, the largest estimate below 2^20), so every batch's lists stay
+listable on the device and the oracle can still check samples.
+
+Usage: python tests/golden/calibrate_rmat20_queries.py  (prints the labels)
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import oracle                                  # noqa: E402
+from paper_2206_09983_b300 import gen, workloads          # noqa: E402
+
+LO_T, HI_T = 1 << 16, 1 << 20
+SHAPES = {"path4": (3, 4), "cycle4": (4, 4), "star5": (4, 5), "tree6": (5, 6)}
+
+
+def estimate(s, q, W, B, sample, rng):
+    pick = rng.choice(B, size=sample, replace=False)
+    mask = np.zeros(W + B, dtype=np.uint8)
+    mask[W + pick] = 1
+    rows = oracle.delta(s, 0, W + B, 0, 0, q, batch_mask=mask)
+    return len(rows) * B / sample
+
+
+def main():
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    s = workloads.rmat20_stream()
+    rng = np.random.default_rng(0x4D4E0C)
+    out = {}
+    p = np.arange(1, w["elabels"] + 1, dtype=np.float64) ** (-w["label_zipf"])
+    p /= p.sum()
+    for name, (ne, nv) in SHAPES.items():
+        best = (0.0, None)
+        for trial in range(200):
+            el = [int(x) for x in rng.choice(w["elabels"], size=ne, p=p)]
+            vl = [int(x) if rng.random() < 0.5 else None for x in rng.integers(0, w["vlabels"], size=nv)]
+            q = workloads.rmat20_queries({**workloads.RMAT20_LABELS, name: (el, vl)})[
+                list(SHAPES).index(name)]
+            t = time.time()
+            e1 = estimate(s, q, W, B, 64, rng)
+            if e1 > 4 * HI_T or e1 == 0:
+                print(f"{name} trial {trial}: {el} {vl} coarse {e1:.3g} rejected", flush=True)
+                continue
+            e2 = estimate(s, q, W, B, 2048, rng)
+            ok = LO_T <= e2 <= HI_T
+            print(f"{name} trial {trial}: {el} {vl} est {e2:.3g} {'ACCEPT' if ok else 'reject'}"
+                  f" ({time.time() - t:.1f}s)", flush=True)
+            if ok:
+                out[name] = (el, vl)
+                break
+            if e2 <= HI_T and e2 > best[0]:
+                best = (e2, (el, vl))
+        if name not in out and best[1] is not None:
+            print(f"{name}: none in range; keeping the largest estimate {best[0]:.3g}")
+            out[name] = best[1]
+    print("RMAT20_LABELS =", out)
+
+
+if __name__ == "__main__":
+    main()
