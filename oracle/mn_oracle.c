@@ -230,10 +230,12 @@ typedef struct {
     int order[OR_MAXE];
     uint32_t f[OR_MAXV];
     int bound[OR_MAXV];
+    int ebound[OR_MAXE];
     uint64_t g[OR_MAXE];
     int need_batch;
     or_result *out;
     uint64_t count;
+    uint64_t nodes, max_nodes;  /* DFS nodes visited; 0 = no budget */
 } dfs_ctx;
 
 static void build_adjacency(dfs_ctx *c)
@@ -297,12 +299,29 @@ static int used_elsewhere(const dfs_ctx *c, uint32_t v)
 
 static void dfs(dfs_ctx *c, int k);
 
+/* Precedence pairs whose other edge is already bound must already hold for
+ * edge e mapped to data edge i (a necessary condition of the leaf check). */
+static int temporal_ok(const dfs_ctx *c, int e, uint64_t i)
+{
+    const or_query *q = c->q;
+    const or_graph *G = c->G;
+    for (int p = 0; p < q->nprec; p++) {
+        int a = q->prec_a[p], b = q->prec_b[p];
+        if (a == e && c->ebound[b] && !(G->ts[i] < G->ts[c->g[b]])) return 0;
+        if (b == e && c->ebound[a] && !(G->ts[c->g[a]] < G->ts[i])) return 0;
+    }
+    return 1;
+}
+
 static void try_edge(dfs_ctx *c, int k, int e, uint64_t i)
 {
     const or_graph *G = c->G;
     const or_query *q = c->q;
     int a = q->esrc[e], b = q->edst[e];
+    if (c->max_nodes && c->nodes >= c->max_nodes) return;
+    c->nodes++;
     if (!edge_match(G, q, e, i)) return;
+    if (!temporal_ok(c, e, i)) return;
     int bind_a = !c->bound[a], bind_b = !c->bound[b];
     if (!bind_a && c->f[a] != G->src[i]) return;
     if (!bind_b && c->f[b] != G->dst[i]) return;
@@ -318,7 +337,9 @@ static void try_edge(dfs_ctx *c, int k, int e, uint64_t i)
     if (bind_a) { c->f[a] = G->src[i]; c->bound[a] = 1; }
     if (bind_b) { c->f[b] = G->dst[i]; c->bound[b] = 1; }
     c->g[e] = i;
+    c->ebound[e] = 1;
     dfs(c, k + 1);
+    c->ebound[e] = 0;
     if (bind_a) c->bound[a] = 0;
     if (bind_b) c->bound[b] = 0;
 }
@@ -351,6 +372,7 @@ static void dfs(dfs_ctx *c, int k)
 static void seed(dfs_ctx *c, int e, uint64_t x)
 {
     memset(c->bound, 0, sizeof(c->bound));
+    memset(c->ebound, 0, sizeof(c->ebound));
     connected_order(c->q, e, c->order);
     try_edge(c, 0, e, x);
 }
@@ -417,6 +439,50 @@ uint64_t or_delta_count(const or_graph *G, const or_query *q)
     free(scratch.rows);
     free_adjacency(&c);
     return total;
+}
+
+/* |dS| with a DFS node budget (for sizing workloads): returns 1 and leaves
+ * *count partial when the budget runs out, else 0 with the exact count.
+ * Embeddings are counted once, at the first query edge mapped to a batch
+ * edge (the seed's query edge), as in or_delta_count. */
+int or_delta_count_budget(const or_graph *G, const or_query *q, uint64_t max_nodes,
+                          uint64_t *count)
+{
+    dfs_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.G = G; c.q = q; c.need_batch = 1; c.max_nodes = max_nodes;
+    *count = 0;
+    int tmp[OR_MAXE];
+    if (!connected_order(q, 0, tmp) || G->in_batch == NULL) return 0;
+    or_result scratch;
+    memset(&scratch, 0, sizeof(scratch));
+    scratch.width = q->nv + q->ne;
+    build_adjacency(&c);
+    for (uint64_t x = 0; x < G->m && !(max_nodes && c.nodes >= max_nodes); x++) {
+        if (!G->in_batch[x] || !edge_live(G, x)) continue;
+        for (int e = 0; e < q->ne; e++) {
+            c.out = &scratch;
+            scratch.n = 0;
+            seed(&c, e, x);
+            for (uint64_t r = 0; r < scratch.n; r++) {
+                const uint64_t *row = scratch.rows + r * scratch.width;
+                int first = 1;
+                for (int i = 0; i < e && first; i++) {
+                    uint64_t sq = row[q->nv + i];
+                    uint64_t lo = 0, hi = G->m;
+                    while (lo < hi) {
+                        uint64_t mid = (lo + hi) / 2;
+                        if (G->seq[mid] < sq) lo = mid + 1; else hi = mid;
+                    }
+                    if (lo < G->m && G->seq[lo] == sq && G->in_batch[lo]) first = 0;
+                }
+                *count += (uint64_t)first;
+            }
+        }
+    }
+    free(scratch.rows);
+    free_adjacency(&c);
+    return (max_nodes && c.nodes >= max_nodes) ? 1 : 0;
 }
 
 /* |S(G)|: every embedding has exactly one image of query edge 0. */

@@ -83,6 +83,9 @@ def _load(path: str | None = None):
         fn = getattr(lib, name)
         fn.restype = C.c_uint64
         fn.argtypes = [C.POINTER(_Graph), C.POINTER(_Query)]
+    lib.or_delta_count_budget.restype = C.c_int
+    lib.or_delta_count_budget.argtypes = [C.POINTER(_Graph), C.POINTER(_Query), C.c_uint64,
+                                          C.POINTER(C.c_uint64)]
     lib.or_debi_words.restype = None
     lib.or_debi_words.argtypes = [C.POINTER(_Graph), C.POINTER(_Query), C.c_void_p]
     lib.or_result_free.restype = None
@@ -184,6 +187,17 @@ def delta_count_first_edge(stream, lo, hi, batch_lo, batch_hi, q, lib_path=None)
     gv = _GraphView(stream, lo, hi, None, ib)
     qs = _query_struct(q)
     return int(lib.or_delta_count(C.byref(gv.g), C.byref(qs)))
+
+
+def delta_count_budget(stream, lo, hi, q, batch_mask, max_nodes, lib_path=None):
+    """(count, complete): |dS| for the flagged batch edges, or a partial count
+    with complete=False when the DFS node budget ran out."""
+    lib = _load(lib_path)
+    gv = _GraphView(stream, lo, hi, None, batch_mask)
+    qs = _query_struct(q)
+    cnt = C.c_uint64()
+    aborted = lib.or_delta_count_budget(C.byref(gv.g), C.byref(qs), max_nodes, C.byref(cnt))
+    return int(cnt.value), not aborted
 
 
 def brute_force(stream: dict, lo: int, hi: int, q: dict, batch_lo=None, batch_hi=None,

@@ -6,8 +6,10 @@ draws edge labels from the stream's own label frequencies (Zipf(1.2) over 8)
 and, per query vertex, either one of the 4 vertex labels or "any", then
 estimates |dS+| of the first
 batch after the preloaded window from a random sample of the batch's edges
-(embeddings that contain a sampled edge, scaled to the whole batch).  The
-first draw whose estimate lies in [2^16, 2^20] is kept (if none does in 200
+(embeddings that contain a sampled edge, scaled to the whole batch), in two
+stages of 64 and 1024 sampled edges with a DFS node budget, so that
+explosive draws are dropped early (reported as est -1).  The
+first draw whose estimate lies in [2^15, 2^20] is kept (if none does in 200
 draws, the largest estimate below 2^20), so every batch's lists stay
 listable on the device and the oracle can still check samples.
 
@@ -25,16 +27,18 @@ sys.path.insert(0, ROOT)
 from oracle import oracle                                  # noqa: E402
 from paper_2206_09983_b300 import gen, workloads          # noqa: E402
 
-LO_T, HI_T = 1 << 16, 1 << 20
+LO_T, HI_T = 1 << 15, 1 << 20
 SHAPES = {"path4": (3, 4), "cycle4": (4, 4), "star5": (4, 5), "tree6": (5, 6)}
 
 
-def estimate(s, q, W, B, sample, rng):
+def estimate(s, q, W, B, sample, rng, max_nodes):
+    """Estimated |dS+| of the whole batch from a sample of its edges, or None
+    when the oracle's DFS node budget runs out (an explosive draw)."""
     pick = rng.choice(B, size=sample, replace=False)
     mask = np.zeros(W + B, dtype=np.uint8)
     mask[W + pick] = 1
-    rows = oracle.delta(s, 0, W + B, 0, 0, q, batch_mask=mask)
-    return len(rows) * B / sample
+    cnt, complete = oracle.delta_count_budget(s, 0, W + B, q, mask, max_nodes)
+    return cnt * B / sample if complete else None
 
 
 def main():
@@ -53,17 +57,20 @@ def main():
             q = workloads.rmat20_queries({**workloads.RMAT20_LABELS, name: (el, vl)})[
                 list(SHAPES).index(name)]
             t = time.time()
-            e1 = estimate(s, q, W, B, 64, rng)
-            if e1 > 4 * HI_T or e1 == 0:
-                print(f"{name} trial {trial}: {el} {vl} coarse {e1:.3g} rejected", flush=True)
-                continue
-            e2 = estimate(s, q, W, B, 2048, rng)
-            ok = LO_T <= e2 <= HI_T
-            print(f"{name} trial {trial}: {el} {vl} est {e2:.3g} {'ACCEPT' if ok else 'reject'}"
-                  f" ({time.time() - t:.1f}s)", flush=True)
+            est, ok = 0.0, False
+            for stage, (sample, budget) in enumerate(((64, 2 * 10**7), (1024, 2 * 10**8))):
+                est = estimate(s, q, W, B, sample, rng, budget)
+                if est is None or est > 16 * HI_T or est == 0:
+                    break
+            else:
+                ok = LO_T <= est <= HI_T
+            est = -1.0 if est is None else est
+            print(f"{name} trial {trial}: {el} {vl} est {est:.3g} (sample {sample}) "
+                  f"{'ACCEPT' if ok else 'reject'} ({time.time() - t:.1f}s)", flush=True)
             if ok:
                 out[name] = (el, vl)
                 break
+            e2 = est if sample == 1024 else 0.0
             if e2 <= HI_T and e2 > best[0]:
                 best = (e2, (el, vl))
         if name not in out and best[1] is not None:

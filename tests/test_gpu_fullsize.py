@@ -1,0 +1,106 @@
+"""Parity at the benchmark's full size (rmat20_window: 2^20 vertices, window
+2^22 edges, batches of 65,536, the four calibrated queries), in the same
+launch configuration as bench.py (device-resident batches, count-only
+preload, queries registered on the full window).
+
+The oracle cannot list a whole batch quickly, so per batch and query:
+* sampled exactness: for a seeded sample of the batch's edges, the GPU records
+  that contain a sampled edge equal the oracle's embeddings containing a
+  sampled edge (the oracle's delta with the sample as its batch);
+* properties of every record: it is a valid embedding of the live window
+  (endpoints, labels, vertex labels, injectivity, temporal order), it contains
+  a batch edge, and no record repeats.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle
+from paper_2206_09983_b300 import workloads
+from paper_2206_09983_b300 import mnemonic as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def run():
+    import torch
+    from paper_2206_09983_b300 import build
+    build.build()
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    s = workloads.rmat20_stream()
+    packed = M.edges_from_stream(s, 0, W + 2 * B)
+    d = torch.from_numpy(packed.view(np.uint8)).cuda()
+    qs = workloads.rmat20_queries()
+    g = M.Graph(s["num_vertices"], s["num_edge_labels"], vmask=s["vmask"], window=W, max_batch=B,
+                max_queries=len(qs), stream=torch.cuda.current_stream().cuda_stream,
+                out_capacity=1 << 21)
+    for lo in range(0, W, B):
+        g.insert(None, device_ptr=d.data_ptr() + 24 * lo, n=B, count_only=True)
+    qids = [g.register_query(q) for q in qs]
+    out = []
+    for k in range(2):
+        hi = W + k * B
+        r = g.insert(None, device_ptr=d.data_ptr() + 24 * hi, n=B)
+        rows = {(qi, sg): g.fetch_rows(qi, sg) for qi in qids for sg in (+1, -1)}
+        out.append((k * B, hi, hi + B, r, rows))
+    g.close()
+    return s, qs, out
+
+
+def check_valid(s, q, rows, lo, hi_new, blo, bhi):
+    nv, ne = q["nv"], len(q["edges"])
+    f = rows[:, :nv].astype(np.int64)
+    g = rows[:, nv:].astype(np.int64)
+    assert ((g >= lo) & (g < hi_new)).all(), "edge outside the live window"
+    for e, (a, b, lab, alo, ahi, tlo, thi) in enumerate(q["edges"]):
+        sq = g[:, e]
+        assert (s["src"][sq] == f[:, a]).all() and (s["dst"][sq] == f[:, b]).all()
+        if lab >= 0:
+            assert (s["label"][sq] == lab).all()
+        assert ((s["attr"][sq] >= alo) & (s["attr"][sq] < ahi)).all()
+    for u in range(nv):
+        m = np.uint32(q["vmask"][u])
+        assert ((s["vmask"][f[:, u]] & m) == m).all()
+    if q["iso"]:
+        fs = np.sort(f, axis=1)
+        assert (np.diff(fs, axis=1) != 0).all(), "vertex map not injective"
+    for a, b in oracle.precedence_pairs(q):
+        assert (s["ts"][g[:, a]] < s["ts"][g[:, b]]).all()
+    inb = (g >= blo) & (g < bhi)
+    assert inb.any(axis=1).all(), "record without a batch edge"
+    if len(rows) > 1:
+        assert len(np.unique(rows, axis=0)) == len(rows), "repeated record"
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_fullsize_records_are_valid_and_unique(run, k):
+    s, qs, out = run
+    lo, hi, hi_new, r, rows = out[k]
+    B = hi_new - hi
+    for qi, q in enumerate(qs):
+        pos = rows[(qi, +1)]
+        neg = rows[(qi, -1)]
+        assert len(pos) == r.count_pos[qi] and len(neg) == r.count_neg[qi]
+        check_valid(s, q, pos, lo, hi_new, hi, hi_new)
+        check_valid(s, q, neg, lo, hi_new, lo, lo + B)
+
+
+@pytest.mark.parametrize("k", [0, 1])
+def test_fullsize_sampled_exact(run, k):
+    s, qs, out = run
+    lo, hi, hi_new, r, rows = out[k]
+    B = hi_new - hi
+    rng = np.random.default_rng(1234 + k)
+    for sign, base in ((+1, hi), (-1, lo)):
+        pick = np.sort(rng.choice(B, size=48, replace=False)) + base
+        mask = np.zeros(hi_new - lo, dtype=np.uint8)
+        mask[pick - lo] = 1
+        for qi, q in enumerate(qs):
+            got = rows[(qi, sign)]
+            nv = q["nv"]
+            sel = np.isin(got[:, nv:], pick.astype(np.uint64)).any(axis=1)
+            want = oracle.delta(s, lo, hi_new, 0, 0, q, batch_mask=mask)
+            sub = got[sel]
+            assert sub.shape == want.shape, f"query {qi} sign {sign}: {sub.shape} vs {want.shape}"
+            assert (sub == want).all()
