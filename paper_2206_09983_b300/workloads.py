@@ -39,10 +39,10 @@ def _vm(labels):
 
 # (edge labels, vertex labels) per shape, from the seeded rejection search.
 RMAT20_LABELS = {
-    "path4": ([7, 6, 7], [None, 2, None, 1]),
-    "cycle4": ([3, 5, 4, 6], [None, None, 0, None]),
-    "star5": ([6, 7, 5, 7], [None, 1, 3, 0, 2]),
-    "tree6": ([7, 5, 6, 7, 6], [None, 1, None, 3, 2, 0]),
+    "path4": ([1, 2, 2], [3, None, None, 2]),
+    "cycle4": ([0, 1, 0, 0], [3, None, 0, None]),
+    "star5": ([1, 0, 2, 5], [0, 2, 3, 3, 2]),
+    "tree6": ([7, 2, 5, 5, 7], [3, None, 0, 2, None, 3]),
 }
 
 
