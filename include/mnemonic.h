@@ -175,6 +175,30 @@ mn_status mn_record_layout(const mn_graph *g, uint32_t query_id, uint32_t *nv, u
  * edge at query edge 0. */
 mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
 
+/* Largest live window mn_count_static_noalloc accepts: its seed scratch
+ * holds one 8-byte work unit per live edge. */
+#define MN_NOALLOC_MAX_SEEDS (1u << 22)
+
+/* The same count as mn_count_static, for callers that must not allocate
+ * device memory during the call: code that runs while a memory pool is fully
+ * reserved by another framework, real-time or serving loops that cannot
+ * afford an allocation's latency or failure, and code whose allocations are
+ * audited.  mn_count_static grows its seed buffer with cudaMalloc when the
+ * window grows; this variant never calls cudaMalloc, cudaFree or any
+ * allocating routine.  Its scratch is one fixed array in the library's
+ * device memory (32 MiB plus 2 KiB; every GPU that loads the library holds it
+ * until the process exits).  The paper has no counterpart.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls share the array and it keeps the last call's contents; the
+ *     call clears what must start at zero.  Calls that overlap on the GPU
+ *     (two threads, two graphs, or two streams at once) race on it: run them
+ *     one after another.
+ *   - A live window larger than MN_NOALLOC_MAX_SEEDS edges is rejected with
+ *     MN_ERR_INVALID_ARG before any work is queued. */
+mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *count);
+
 /* Copy the DEBI words (Sec. IV-A; bit e = the edge matches query edge e) of
  * the edges with seq in [seq_lo, seq_hi) to host memory `words` (uint32
  * each); edges not live read 0. */

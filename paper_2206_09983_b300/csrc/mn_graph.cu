@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1025,6 +1026,104 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     *count = g->h_ctrl->counts[query_id * 3 + 2];
+    return MN_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation count
+
+namespace {
+
+// Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status, seed
+// count and seed cursor (u32 each), [4, 8) work counters, [8, 200) counts,
+// [256, 256 + MN_NOALLOC_MAX_SEEDS) seeds.
+constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SEEDS = 256;
+constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
+static __device__ __align__(256) unsigned long long mn_noalloc_scratch[NA_WORDS];
+
+std::mutex na_mutex;
+void *na_addr[256];   // device address of the scratch per device ordinal (set-up once)
+
+// Device address of the scratch on g's device (which must be current).  In
+// host code the symbol is only a host-side stand-in; the kernel needs this
+// address.
+mn_status noalloc_scratch(mn_graph *g, unsigned long long **out)
+{
+    if (g->device < 0 || g->device >= 256) return fail(g, MN_ERR_INVALID_ARG, "device ordinal");
+    std::lock_guard<std::mutex> lock(na_mutex);
+    if (!na_addr[g->device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, mn_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            return fail(g, MN_ERR_DEVICE, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        na_addr[g->device] = ptr;
+    }
+    *out = reinterpret_cast<unsigned long long *>(na_addr[g->device]);
+    return MN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *count)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (!count || query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
+    const uint64_t live = g->hi - g->lo;
+    if (live > MN_NOALLOC_MAX_SEEDS)
+        return fail(g, MN_ERR_INVALID_ARG,
+                    "live window of " + std::to_string(live) +
+                        " edges exceeds the no-allocation scratch (at most 4194304 edges)");
+    CK(cudaSetDevice(g->device));
+    unsigned long long *base = nullptr;
+    TRY(noalloc_scratch(g, &base));
+    uint32_t *ctl = reinterpret_cast<uint32_t *>(base);
+    unsigned long long *seeds = base + NA_SEEDS;
+    CK(cudaMemsetAsync(base, 0, NA_SEEDS * sizeof(unsigned long long), g->stream));
+    if (live) {
+        k_seeds_range<<<cdiv(live, 256), 256, 0, g->stream>>>(
+            g->lo, (uint32_t)live, g->cap_mask, (uint32_t)g->queries.size(), g->d_debi_ptrs,
+            query_id, 1u, seeds, &ctl[1], MN_NOALLOC_MAX_SEEDS, &ctl[0]);
+        CKL();
+    }
+    EnumParams p;
+    memset(&p, 0, sizeof(p));
+    for (int d = 0; d < 2; d++) {
+        p.nbr[d] = g->base[g->cur][d].nbr;
+        p.s32[d] = g->base[g->cur][d].s32;
+        p.offs[d] = g->offs[d];
+    }
+    p.L = g->L;
+    p.cap_mask = g->cap_mask;
+    p.ring_src = g->r_src;
+    p.ring_dst = g->r_dst;
+    p.debi = g->d_debi_ptrs;
+    p.plans = g->d_plans;
+    p.seeds = seeds;
+    p.nseeds = &ctl[1];
+    p.seed_cap = MN_NOALLOC_MAX_SEEDS;
+    p.next_seed = &ctl[2];
+    p.lo32 = (uint32_t)g->lo;
+    p.vis_len = (uint32_t)live;
+    p.lo = g->lo;
+    p.sign = 2;
+    p.counts = base + NA_COUNTS;
+    p.count_only = 1;
+    p.max_iters = g->max_iters;
+    p.status = &ctl[0];
+    p.work = base + NA_WORK;
+    k_enumerate<<<g->enum_grid, 256, 0, g->stream>>>(p);
+    CKL();
+    uint32_t st = 0;
+    unsigned long long c = 0;
+    CK(cudaMemcpyAsync(&st, &ctl[0], sizeof(st), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&c, base + NA_COUNTS + query_id * 3 + 2, sizeof(c), cudaMemcpyDeviceToHost,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (st) return map_status(g, st);
+    *count = c;
     return MN_OK;
 }
 

@@ -36,7 +36,8 @@ EXPORTS = [
     "mn_create_graph", "mn_destroy_graph", "mn_register_query", "mn_insert_batch",
     "mn_delete_batch", "mn_fetch_embeddings", "mn_record_layout", "mn_count_static",
     "mn_read_debi", "mn_read_adjacency", "mn_graph_info", "mn_set_work_budget",
-    "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_last_error",
+    "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
+    "mn_last_error",
 ]
 
 
@@ -114,6 +115,7 @@ def load(path: str | None = None):
         "mn_record_layout": (S, [P, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                                  C.POINTER(C.c_uint32)]),
         "mn_count_static": (S, [P, C.c_uint32, C.POINTER(U64)]),
+        "mn_count_static_noalloc": (S, [P, C.c_uint32, C.POINTER(U64)]),
         "mn_read_debi": (S, [P, C.c_uint32, U64, U64, P]),
         "mn_read_adjacency": (S, [P, C.c_uint32, U64, P, P, P, C.POINTER(U64)]),
         "mn_graph_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(C.c_uint32)]),
@@ -290,6 +292,12 @@ class Graph:
     def count_static(self, qid: int) -> int:
         c = C.c_uint64()
         self._check(self._lib.mn_count_static(self._h, qid, C.byref(c)))
+        return c.value
+
+    def count_static_noalloc(self, qid: int) -> int:
+        """mn_count_static_noalloc: the static count without any device allocation."""
+        c = C.c_uint64()
+        self._check(self._lib.mn_count_static_noalloc(self._h, qid, C.byref(c)))
         return c.value
 
     def read_debi(self, qid: int, lo: int, hi: int) -> np.ndarray:
