@@ -219,13 +219,14 @@ def main():
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat, counts = [], []
+    lat, counts, per_q = [], [], []
     ev0.record(cur_stream)
     for _ in range(K):
         t0 = time.perf_counter()
         r = g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
         lat.append(time.perf_counter() - t0)
         counts.append((sum(r.count_pos), sum(r.count_neg)))
+        per_q.append((list(r.count_pos), list(r.count_neg)))
         pos += B
     ev1.record(cur_stream)
     torch.cuda.synchronize()
@@ -306,6 +307,10 @@ def main():
                        "max": 1e3 * max(lat)},
         "embeddings_per_step": {"new": float(np.mean([c[0] for c in counts])),
                                 "removed": float(np.mean([c[1] for c in counts]))},
+        "embeddings_per_step_by_query": {
+            name: {"new": float(np.mean([c[0][i] for c in per_q])),
+                   "removed": float(np.mean([c[1][i] for c in per_q]))}
+            for i, name in enumerate(workloads.QUERY_NAMES)},
         "stage_ms_per_step": {k: v / K for k, v in stage_ms.items()},
         "work_per_step": {k: st[k] / K for k in ("seeds", "entries_scanned", "binds", "records")},
         "gpu_launches": st["kernel_launches"],

@@ -95,27 +95,6 @@ __device__ __forceinline__ uint32_t match_word(const QueryDev *q, uint32_t label
     return w;
 }
 
-// First i in [lo, hi) with a[i] >= t (hi if none); all 32 lanes cooperate,
-// each round probing 32 evenly spaced positions.
-__device__ __forceinline__ uint32_t warp_lower_bound(const uint32_t *__restrict__ a, uint32_t lo,
-                                                     uint32_t hi, uint32_t t, int lane)
-{
-    while (hi - lo > 32) {
-        uint32_t stride = (hi - lo + 31) >> 5;
-        uint32_t pos = lo + (uint32_t)lane * stride;
-        bool less = pos < hi && a[pos] < t;
-        uint32_t k = __popc(__ballot_sync(FULL, less));
-        if (k == 0) return lo;
-        uint32_t nlo = lo + (k - 1) * stride + 1;
-        uint32_t nhi = lo + k * stride;
-        lo = nlo;
-        hi = nhi < hi ? nhi : hi;
-    }
-    uint32_t pos = lo + (uint32_t)lane;
-    bool less = pos < hi && a[pos] < t;
-    return lo + __popc(__ballot_sync(FULL, less));
-}
-
 // Block-wide exclusive scan of one value per thread (blockDim multiple of 32,
 // at most 1024).  Returns the exclusive prefix; *total gets the block sum.
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
@@ -150,6 +129,21 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
 
 // ------------------------------------------------------------------ ingest
 
+// The four adjacency orders kept per graph: 0 = out by neighbour, 1 = in by
+// neighbour, 2 = out by arrival, 3 = in by arrival.  Both orders group entries
+// by key = v * L + label; within a (vertex, label) segment the neighbour order
+// sorts by (nbr, seq) and the arrival order by seq.
+constexpr int NPROB = 4;
+
+struct SortSet {
+    unsigned long long *k[NPROB];
+    uint32_t *v[NPROB];
+};
+
+struct Adj4 {
+    uint32_t *key[NPROB], *nbr[NPROB], *s32[NPROB];
+};
+
 struct IngestParams {
     const mn_edge *edges;
     uint32_t n, n_pad;
@@ -164,23 +158,22 @@ struct IngestParams {
     uint32_t nq;
     const QueryDev *queries;
     uint32_t *const *debi;
-    unsigned long long *dkey[2];
-    uint32_t *dval[2];
+    SortSet sort;
     uint32_t *status;
     long long *last_ts_out;
 };
 
 // Append the batch to the ring, compute its DEBI words for every query
 // (edgeMatcher, Sec. III / IV-A) and emit the sort keys of its adjacency
-// entries.  Invalid batches are flagged in *status; every later kernel of the
-// batch checks the flag, and ring slots written here were free.
+// entries in both orders.  Invalid batches are flagged in *status; every
+// later kernel of the batch checks the flag, and ring slots written here were
+// free.
 __global__ void k_ingest(IngestParams p)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= p.n_pad) return;
     if (i >= p.n) {
-        p.dkey[0][i] = ~0ull; p.dval[0][i] = ~0u;
-        p.dkey[1][i] = ~0ull; p.dval[1][i] = ~0u;
+        for (int t = 0; t < NPROB; t++) { p.sort.k[t][i] = ~0ull; p.sort.v[t][i] = ~0u; }
         return;
     }
     const mn_edge e = p.edges[i];
@@ -202,12 +195,13 @@ __global__ void k_ingest(IngestParams p)
     for (uint32_t q = 0; q < p.nq; q++)
         p.debi[q][slot] = err ? 0u : match_word(&p.queries[q], e.label, e.attr, e.ts, ms, md);
     const uint32_t L = p.L;
-    const uint32_t ks = err ? 0u : e.src * L + e.label;
-    const uint32_t kd = err ? 0u : e.dst * L + e.label;
-    p.dkey[0][i] = ((unsigned long long)ks << 32) | e.dst;
-    p.dkey[1][i] = ((unsigned long long)kd << 32) | e.src;
-    p.dval[0][i] = i;
-    p.dval[1][i] = i;
+    const unsigned long long ks = err ? 0ull : (unsigned long long)(e.src * L + e.label) << 32;
+    const unsigned long long kd = err ? 0ull : (unsigned long long)(e.dst * L + e.label) << 32;
+    p.sort.k[0][i] = ks | e.dst;
+    p.sort.k[1][i] = kd | e.src;
+    p.sort.k[2][i] = ks | i;
+    p.sort.k[3][i] = kd | i;
+    for (int t = 0; t < NPROB; t++) p.sort.v[t][i] = i;
 }
 
 // Bulk edgeMatcher over live slots [seq_lo, seq_hi) for one query
@@ -237,16 +231,14 @@ __device__ __forceinline__ bool kv_greater(unsigned long long ka, uint32_t va,
     return ka > kb || (ka == kb && va > vb);
 }
 
-// Bitonic sort of SORT_TILE (key, index) pairs per block; blockIdx.y = direction.
-__global__ void __launch_bounds__(1024) k_sort_tiles(unsigned long long *key0, uint32_t *val0,
-                                                     unsigned long long *key1, uint32_t *val1,
-                                                     const uint32_t *status)
+// Bitonic sort of SORT_TILE (key, index) pairs per block; blockIdx.y = problem.
+__global__ void __launch_bounds__(1024) k_sort_tiles(SortSet s, const uint32_t *status)
 {
     if (*status) return;
     __shared__ unsigned long long sk[SORT_TILE];
     __shared__ uint32_t sv[SORT_TILE];
-    unsigned long long *key = blockIdx.y ? key1 : key0;
-    uint32_t *val = blockIdx.y ? val1 : val0;
+    unsigned long long *key = s.k[blockIdx.y];
+    uint32_t *val = s.v[blockIdx.y];
     const uint32_t base = blockIdx.x * SORT_TILE;
     for (int i = threadIdx.x; i < SORT_TILE; i += blockDim.x) {
         sk[i] = key[base + i];
@@ -278,18 +270,15 @@ __global__ void __launch_bounds__(1024) k_sort_tiles(unsigned long long *key0, u
 constexpr int MERGE_ITEMS = 8;
 
 // One pass of a bottom-up merge sort: merge neighbouring sorted runs of
-// length R into runs of 2R (merge path per thread).  blockIdx.y = direction.
-__global__ void k_merge_pass(const unsigned long long *ks0, const uint32_t *vs0,
-                             unsigned long long *kd0, uint32_t *vd0,
-                             const unsigned long long *ks1, const uint32_t *vs1,
-                             unsigned long long *kd1, uint32_t *vd1,
-                             uint32_t n, uint32_t R, const uint32_t *status)
+// length R into runs of 2R (merge path per thread).  blockIdx.y = problem.
+__global__ void k_merge_pass(SortSet src, SortSet dst, uint32_t n, uint32_t R,
+                             const uint32_t *status)
 {
     if (*status) return;
-    const unsigned long long *ks = blockIdx.y ? ks1 : ks0;
-    const uint32_t *vs = blockIdx.y ? vs1 : vs0;
-    unsigned long long *kd = blockIdx.y ? kd1 : kd0;
-    uint32_t *vd = blockIdx.y ? vd1 : vd0;
+    const unsigned long long *ks = src.k[blockIdx.y];
+    const uint32_t *vs = src.v[blockIdx.y];
+    unsigned long long *kd = dst.k[blockIdx.y];
+    uint32_t *vd = dst.v[blockIdx.y];
     const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
     if (o >= n) return;
     const uint32_t pbase = o / (2 * R) * (2 * R);
@@ -312,40 +301,37 @@ __global__ void k_merge_pass(const unsigned long long *ks0, const uint32_t *vs0,
     }
 }
 
-// Sorted (key, index) pairs -> delta adjacency entries, and +1 on the
-// (vertex, label) degree counters.  blockIdx.y = direction.
-__global__ void k_delta_finalize(const unsigned long long *k0, const uint32_t *v0,
-                                 const unsigned long long *k1, const uint32_t *v1,
-                                 uint32_t *dk0, uint32_t *dn0, uint32_t *ds0,
-                                 uint32_t *dk1, uint32_t *dn1, uint32_t *ds1,
-                                 uint32_t *cnt0, uint32_t *cnt1,
-                                 uint32_t n, uint64_t seq0, const uint32_t *status)
+// Sorted (key, index) pairs -> delta adjacency entries of each problem, and
+// +1 on the (vertex, label) degree counters (counted once, from the
+// neighbour-order problems).  blockIdx.y = problem.
+__global__ void k_delta_finalize(SortSet s, Adj4 d, const mn_edge *edges, uint32_t *cnt0,
+                                 uint32_t *cnt1, uint32_t n, uint64_t seq0, const uint32_t *status)
 {
     if (*status) return;
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const unsigned long long k = blockIdx.y ? k1[i] : k0[i];
-    const uint32_t v = blockIdx.y ? v1[i] : v0[i];
-    uint32_t *dk = blockIdx.y ? dk1 : dk0, *dn = blockIdx.y ? dn1 : dn0, *ds = blockIdx.y ? ds1 : ds0;
+    const int t = blockIdx.y;
+    const unsigned long long k = s.k[t][i];
+    const uint32_t v = s.v[t][i];
     const uint32_t key = (uint32_t)(k >> 32);
-    dk[i] = key;
-    dn[i] = (uint32_t)k;
-    ds[i] = (uint32_t)(seq0 + v);
-    atomicAdd(blockIdx.y ? &cnt1[key] : &cnt0[key], 1u);
+    d.key[t][i] = key;
+    d.nbr[t][i] = t < 2 ? (uint32_t)k : ((t & 1) ? edges[v].src : edges[v].dst);
+    d.s32[t][i] = (uint32_t)(seq0 + v);
+    if (t == 0) atomicAdd(&cnt0[key], 1u);
+    if (t == 1) atomicAdd(&cnt1[key], 1u);
 }
 
 // ------------------------------------------------------------------ base compaction
 
 constexpr int CBLK = 256, CITEMS = 8, CTILE = CBLK * CITEMS;
 
-// Live entries (seq >= lo) per tile of the base adjacency.
-__global__ void __launch_bounds__(CBLK) k_live_count(const uint32_t *s0, const uint32_t *s1,
-                                                     uint32_t n, uint32_t lo32, uint32_t live_span,
-                                                     uint32_t *bc0, uint32_t *bc1,
+// Live entries (seq >= lo) per tile of the base adjacency; blockIdx.y = problem.
+__global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_t lo32,
+                                                     uint32_t live_span, Adj4 blk,
                                                      const uint32_t *status)
 {
     if (*status) return;
-    const uint32_t *s = blockIdx.y ? s1 : s0;
+    const uint32_t *s = a.s32[blockIdx.y];
     const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
     uint32_t c = 0;
 #pragma unroll
@@ -355,49 +341,39 @@ __global__ void __launch_bounds__(CBLK) k_live_count(const uint32_t *s0, const u
     }
     uint32_t total;
     block_excl_scan(c, &total);
-    if (threadIdx.x == 0) (blockIdx.y ? bc1 : bc0)[blockIdx.x] = total;
+    if (threadIdx.x == 0) blk.key[blockIdx.y][blockIdx.x] = total;
 }
 
-// In-place exclusive scan of nb values per direction (one block per
-// direction); writes the grand total to tot[dir].
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t *b0, uint32_t *b1, uint32_t nb,
-                                                      uint32_t *tot0, uint32_t *tot1,
-                                                      const uint32_t *status)
+// In-place exclusive scan of nb values per problem (one block per problem,
+// blockIdx.x = problem, arrays in b.key[]).
+__global__ void __launch_bounds__(1024) k_scan_blocks(Adj4 b, uint32_t nb, const uint32_t *status)
 {
     if (*status) return;
-    uint32_t *b = blockIdx.x ? b1 : b0;
+    uint32_t *a = b.key[blockIdx.x];
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (uint32_t base = 0; base < nb; base += blockDim.x) {
         uint32_t i = base + threadIdx.x;
-        uint32_t v = i < nb ? b[i] : 0;
+        uint32_t v = i < nb ? a[i] : 0;
         uint32_t total;
         uint32_t ex = block_excl_scan(v, &total);
-        if (i < nb) b[i] = carry + ex;
+        if (i < nb) a[i] = carry + ex;
         __syncthreads();
         if (threadIdx.x == 0) carry += total;
         __syncthreads();
     }
-    if (threadIdx.x == 0) {
-        uint32_t *tot = blockIdx.x ? tot1 : tot0;
-        if (tot) *tot = carry;
-    }
 }
 
 // Stable compaction of the live base entries into the merge input.
-__global__ void __launch_bounds__(CBLK) k_compact(
-    const uint32_t *k0, const uint32_t *n0, const uint32_t *s0,
-    const uint32_t *k1, const uint32_t *n1, const uint32_t *s1,
-    uint32_t *tk0, uint32_t *tn0, uint32_t *ts0,
-    uint32_t *tk1, uint32_t *tn1, uint32_t *ts1,
-    uint32_t n, uint32_t lo32, uint32_t live_span,
-    const uint32_t *bc0, const uint32_t *bc1, const uint32_t *status)
+__global__ void __launch_bounds__(CBLK) k_compact(Adj4 a, Adj4 out, uint32_t n, uint32_t lo32,
+                                                  uint32_t live_span, Adj4 blk,
+                                                  const uint32_t *status)
 {
     if (*status) return;
-    const bool d1 = blockIdx.y != 0;
-    const uint32_t *K = d1 ? k1 : k0, *N = d1 ? n1 : n0, *S = d1 ? s1 : s0;
-    uint32_t *TK = d1 ? tk1 : tk0, *TN = d1 ? tn1 : tn0, *TS = d1 ? ts1 : ts0;
+    const int t0 = blockIdx.y;
+    const uint32_t *K = a.key[t0], *N = a.nbr[t0], *S = a.s32[t0];
+    uint32_t *TK = out.key[t0], *TN = out.nbr[t0], *TS = out.s32[t0];
     const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
     uint32_t sv[CITEMS];
     uint32_t c = 0;
@@ -408,7 +384,7 @@ __global__ void __launch_bounds__(CBLK) k_compact(
         c += (i < n && (uint32_t)(sv[t] - lo32) < live_span) ? 1u : 0u;
     }
     uint32_t total;
-    uint32_t pos = block_excl_scan(c, &total) + (d1 ? bc1 : bc0)[blockIdx.x];
+    uint32_t pos = block_excl_scan(c, &total) + blk.key[t0][blockIdx.x];
 #pragma unroll
     for (int t = 0; t < CITEMS; t++) {
         uint32_t i = base + t;
@@ -422,26 +398,26 @@ __global__ void __launch_bounds__(CBLK) k_compact(
 }
 
 // Merge the compacted base A (nA entries) with the sorted delta B (nB) into
-// the new adjacency; order (key, nbr), base first on ties (older seqs).
-__global__ void k_merge_csr(
-    const uint32_t *ak0, const uint32_t *an0, const uint32_t *as0,
-    const uint32_t *ak1, const uint32_t *an1, const uint32_t *as1,
-    const uint32_t *bk0, const uint32_t *bn0, const uint32_t *bs0,
-    const uint32_t *bk1, const uint32_t *bn1, const uint32_t *bs1,
-    uint32_t *ok0, uint32_t *on0, uint32_t *os0,
-    uint32_t *ok1, uint32_t *on1, uint32_t *os1,
-    uint32_t nA, uint32_t nB, const uint32_t *status)
+// the new adjacency.  Neighbour order (problems 0, 1) compares (key, nbr);
+// arrival order (2, 3) compares key only; ties take the base first (older).
+__global__ void k_merge_csr(Adj4 A, Adj4 B, Adj4 O, uint32_t nA, uint32_t nB,
+                            const uint32_t *status)
 {
     if (*status) return;
-    const bool d1 = blockIdx.y != 0;
-    const uint32_t *AK = d1 ? ak1 : ak0, *AN = d1 ? an1 : an0, *AS = d1 ? as1 : as0;
-    const uint32_t *BK = d1 ? bk1 : bk0, *BN = d1 ? bn1 : bn0, *BS = d1 ? bs1 : bs0;
-    uint32_t *OK = d1 ? ok1 : ok0, *ON = d1 ? on1 : on0, *OS = d1 ? os1 : os0;
+    const int t = blockIdx.y;
+    const uint32_t *AK = A.key[t], *AN = A.nbr[t], *AS = A.s32[t];
+    const uint32_t *BK = B.key[t], *BN = B.nbr[t], *BS = B.s32[t];
+    uint32_t *OK = O.key[t], *ON = O.nbr[t], *OS = O.s32[t];
+    const bool by_nbr = t < 2;
     const uint32_t n = nA + nB;
     const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
     if (o >= n) return;
-    auto keyA = [&](uint32_t i) { return ((unsigned long long)AK[i] << 32) | AN[i]; };
-    auto keyB = [&](uint32_t i) { return ((unsigned long long)BK[i] << 32) | BN[i]; };
+    auto keyA = [&](uint32_t i) {
+        return ((unsigned long long)AK[i] << 32) | (by_nbr ? AN[i] : 0u);
+    };
+    auto keyB = [&](uint32_t i) {
+        return ((unsigned long long)BK[i] << 32) | (by_nbr ? BN[i] : 0u);
+    };
     uint32_t lo = o > nB ? o - nB : 0, hi = min(o, nA);
     while (lo < hi) {
         uint32_t mid = (lo + hi) >> 1;
@@ -449,10 +425,10 @@ __global__ void k_merge_csr(
         else hi = mid;
     }
     uint32_t i = lo, j = o - lo;
-    for (int t = 0; t < MERGE_ITEMS && o + t < n; t++) {
+    for (int u = 0; u < MERGE_ITEMS && o + u < n; u++) {
         bool takeA = j >= nB || (i < nA && keyA(i) <= keyB(j));
-        if (takeA) { OK[o + t] = AK[i]; ON[o + t] = AN[i]; OS[o + t] = AS[i]; i++; }
-        else       { OK[o + t] = BK[j]; ON[o + t] = BN[j]; OS[o + t] = BS[j]; j++; }
+        if (takeA) { OK[o + u] = AK[i]; ON[o + u] = AN[i]; OS[o + u] = AS[i]; i++; }
+        else       { OK[o + u] = BK[j]; ON[o + u] = BN[j]; OS[o + u] = BS[j]; j++; }
     }
 }
 
@@ -582,9 +558,36 @@ __global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_
 
 // ------------------------------------------------------------------ enumerator
 
+// A split-off subtree: the partial embedding bound above depth `lvl` (f, g)
+// and the adjacency index range [beg, end) still to explore at depth `lvl`.
+struct alignas(16) Task {
+    uint32_t qj_lvl;            // query | seed edge << 16 | depth << 24
+    uint32_t beg, end;
+    uint32_t ready;             // epoch of the launch that published the task
+    uint32_t pad_[4];
+    uint32_t f[MN_MAX_QV];      // data vertex per query vertex
+    uint32_t g[MN_MAX_QE];      // seq (relative to the adjacency base) per query edge
+};
+static_assert(sizeof(Task) == 160, "Task is 160 bytes");
+
+// Scheduler words of one enumerator launch (zeroed before the launch).
+struct Sched {
+    uint32_t next_seed;         // seed cursor
+    uint32_t q_head, q_tail;    // task queue: taken / reserved slots
+    uint32_t idle;              // warps waiting for work
+    uint32_t busy;              // warps running a seed or a task
+    uint32_t pad_[3];
+};
+
+constexpr int ENUM_WARPS = 8;              // warps per block
+constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
+constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 4 us per poll)
+constexpr uint32_t READY_SPINS = 1u << 22; // bound on waiting for a reserved task
+constexpr uint32_t SPLIT_MIN = 64;         // split a depth's range only above this many entries
+
 struct EnumParams {
-    const uint32_t *nbr[2];
-    const uint32_t *s32[2];
+    const uint32_t *nbr[NPROB];         // 0,1: by neighbour (out, in); 2,3: by arrival
+    const uint32_t *s32[NPROB];
     const uint32_t *offs[2];
     uint32_t L, cap_mask;
     const uint32_t *ring_src, *ring_dst;
@@ -593,11 +596,14 @@ struct EnumParams {
     const unsigned long long *seeds;
     const uint32_t *nseeds;
     uint32_t seed_cap;
-    uint32_t *next_seed;
-    uint32_t lo32, vis_len;             // visible seqs: rel = seq32 - lo32 < vis_len
-    unsigned long long lo;
-    uint32_t brel_lo, brel_len;         // batch seqs, relative to lo
-    const uint8_t *batch_flag;          // optional per-slot batch flags
+    Sched *sched;
+    Task *tasks;                        // NULL: no splitting
+    uint32_t task_cap, epoch;
+    uint32_t base32;                    // lowest seq held by the adjacency (low 32 bits)
+    unsigned long long base;
+    uint32_t vis_lo, vis_hi;            // visible seqs, relative to base
+    uint32_t av_lo, av_hi;              // seqs allowed on query edges before the seed edge
+    const uint8_t *batch_flag;          // optional per-slot batch flags (explicit deletes)
     uint32_t sign;                      // 0 new, 1 removed, 2 static count
     unsigned long long *counts;         // [query * 3 + sign]
     uint8_t *const *out;                // [query * 2 + sign]
@@ -608,218 +614,403 @@ struct EnumParams {
     unsigned long long *work;           // [seeds, entries tested, binds, records]
 };
 
-// Emit the embeddings completed by the valid lanes of one chunk: f/g are
-// lane-distributed (lane u holds f(u), lane e holds rel seq of g(e)); the
-// lane's own candidate supplies vertex `to_new` (if < 16) and edge `qe_new`.
-__device__ __forceinline__ void emit_chunk(const EnumParams &p, int lane, bool ok, uint32_t q,
-                                           uint32_t nv, uint32_t ne, uint32_t rec_bytes,
-                                           uint32_t goff, uint32_t f, uint32_t g,
-                                           uint32_t to_new, uint32_t nb, uint32_t qe_new,
-                                           uint32_t rel, unsigned long long *warp_count)
+__device__ __forceinline__ uint32_t vload(const uint32_t *p)
 {
-    const uint32_t m = __ballot_sync(FULL, ok);
-    if (!m) return;
-    const uint32_t cnt = __popc(m);
-    if (p.count_only) {
-        *warp_count += cnt;
-        return;
-    }
-    unsigned long long base = 0;
-    if (lane == 0) base = atomicAdd(&p.counts[q * 3 + p.sign], (unsigned long long)cnt);
-    base = __shfl_sync(FULL, base, 0);
-    const unsigned long long idx = base + __popc(m & lanemask_lt());
-    const bool wr = ok && idx < p.out_cap[q * 2 + p.sign];
-    uint8_t *rec = p.out[q * 2 + p.sign] + idx * rec_bytes;
-    for (uint32_t u = 0; u < nv; u++) {
-        uint32_t fu = __shfl_sync(FULL, f, u);
-        if (u == to_new) fu = nb;
-        if (wr) reinterpret_cast<uint32_t *>(rec)[u] = fu;
-    }
-    if ((nv & 1) && wr) reinterpret_cast<uint32_t *>(rec)[nv] = 0;
-    for (uint32_t e = 0; e < ne; e++) {
-        uint32_t ge = __shfl_sync(FULL, g, e);
-        if (e == qe_new) ge = rel;
-        if (wr) reinterpret_cast<unsigned long long *>(rec + goff)[e] = p.lo + ge;
-    }
+    return *reinterpret_cast<const volatile uint32_t *>(p);
 }
 
-// Warp-per-seed backtracking enumerator (Sec. III enumerator, Sec. V work
-// units, matching orders and masks).  Persistent: warps pull seeds from a
-// global counter (pull-based distribution of work units).  Per warp, lane s
-// holds the state of depth s; candidates of a depth are tested 32 at a time,
-// one per lane, against DEBI, liveness, the batch mask, the temporal bounds
-// and injectivity.
-__global__ void __launch_bounds__(256) k_enumerate(EnumParams p)
+// First i in [lo, hi) with key(i) >= t (hi if none) for a key that is
+// non-decreasing over [lo, hi); 32 lanes probe 32 positions per round.
+template <class KeyFn>
+__device__ __forceinline__ uint32_t warp_lower_bound_by(KeyFn key, uint32_t lo, uint32_t hi,
+                                                        uint32_t t, int lane)
 {
+    while (hi - lo > 32) {
+        uint32_t stride = (hi - lo + 31) >> 5;
+        uint32_t pos = lo + (uint32_t)lane * stride;
+        bool less = pos < hi && key(pos) < t;
+        uint32_t k = __popc(__ballot_sync(FULL, less));
+        if (k == 0) return lo;
+        uint32_t nlo = lo + (k - 1) * stride + 1;
+        uint32_t nhi = lo + k * stride;
+        lo = nlo;
+        hi = nhi < hi ? nhi : hi;
+    }
+    uint32_t pos = lo + (uint32_t)lane;
+    bool less = pos < hi && key(pos) < t;
+    return lo + __popc(__ballot_sync(FULL, less));
+}
+
+// Warp-per-unit backtracking enumerator (Sec. III enumerator, Sec. V work
+// units, matching orders and masks).  Persistent: warps take split-off
+// subtrees from a global task queue first, then seeds (pull-based
+// distribution of work units).  Lane s holds the state of depth s; the
+// candidates of a depth are tested 32 at a time, one per lane.  A depth's
+// candidate range is the (vertex, label) slice of the adjacency narrowed by
+// binary search to the seqs allowed by the temporal bounds, the window and
+// the batch mask; what remains is tested against the DEBI bit and
+// injectivity.  When other warps are idle, a warp hands the upper half of a
+// large range to the queue.  Embeddings are staged per warp in shared memory
+// and written out in contiguous blocks.
+__global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
+{
+    __shared__ __align__(16) unsigned char stage_all[ENUM_WARPS][STAGE_BYTES];
     if (*p.status) return;
     const int lane = threadIdx.x & 31;
+    unsigned char *stage = stage_all[threadIdx.x >> 5];
     const uint32_t nseeds = min(*p.nseeds, p.seed_cap);
+    Sched *sc = p.sched;
     unsigned long long iters = 0;
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0;
+    uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0;
+
+    // write the staged records of query st_q to its list
+    auto flush = [&]() {
+        if (st_n == 0) return;
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(&p.counts[st_q * 3 + p.sign], (unsigned long long)st_n);
+        base = __shfl_sync(FULL, base, 0);
+        const unsigned long long cap = p.out_cap[st_q * 2 + p.sign];
+        const unsigned long long nw = base >= cap ? 0ull : min((unsigned long long)st_n, cap - base);
+        unsigned long long *dst =
+            reinterpret_cast<unsigned long long *>(p.out[st_q * 2 + p.sign] + base * st_rb);
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(stage);
+        const uint32_t words = (uint32_t)(nw * st_rb / 8);
+        for (uint32_t w = lane; w < words; w += 32) dst[w] = src[w];
+        st_n = 0;
+        __syncwarp();
+    };
+
     for (;;) {
-        uint32_t sid = 0;
-        if (lane == 0) sid = atomicAdd(p.next_seed, 1u);
-        sid = __shfl_sync(FULL, sid, 0);
-        if (sid >= nseeds) break;
-        w_seeds++;
-        const unsigned long long sd = p.seeds[sid];
-        const uint32_t seed32 = (uint32_t)(sd >> 32);
-        const uint32_t q = (uint32_t)(sd >> 8) & 0xffffu;
-        const uint32_t j = (uint32_t)sd & 0xffu;
+        // ---------------------------------------------------------- take a unit
+        uint32_t kind = 0, unit = 0;
+        if (lane == 0) {
+            if (p.tasks) {
+                uint32_t h = vload(&sc->q_head);
+                const uint32_t t = min(vload(&sc->q_tail), p.task_cap);
+                while (h < t) {
+                    const uint32_t prev = atomicCAS(&sc->q_head, h, h + 1);
+                    if (prev == h) { kind = 2; unit = h; break; }
+                    h = prev;
+                }
+            }
+            if (!kind) {
+                const uint32_t s = atomicAdd(&sc->next_seed, 1u);
+                if (s < nseeds) { kind = 1; unit = s; }
+            }
+            if (kind) atomicAdd(&sc->busy, 1u);
+        }
+        kind = __shfl_sync(FULL, kind, 0);
+        unit = __shfl_sync(FULL, unit, 0);
+        if (!kind) {
+            // idle: wait (bounded) until a task appears or no warp is busy
+            uint32_t more = 0;
+            if (lane == 0 && p.tasks) {
+                atomicAdd(&sc->idle, 1u);
+                uint32_t nap = 128;
+                for (uint32_t it = 0; it < IDLE_SPINS; it++) {
+                    __threadfence();
+                    if (vload(&sc->q_head) < min(vload(&sc->q_tail), p.task_cap)) { more = 1; break; }
+                    if (vload(&sc->busy) == 0) break;
+                    __nanosleep(nap);
+                    nap = min(nap * 2, 4096u);
+                }
+                atomicSub(&sc->idle, 1u);
+            }
+            if (__shfl_sync(FULL, more, 0)) continue;
+            break;
+        }
+
+        // ---------------------------------------------------------- set up the unit
+        uint32_t q, j, root, f = 0, g = 0, tbeg = 0, tend = 0;
+        bool skip = false;
+        if (kind == 1) {
+            w_seeds++;
+            const unsigned long long sd = p.seeds[unit];
+            const uint32_t seed32 = (uint32_t)(sd >> 32);
+            q = (uint32_t)(sd >> 8) & 0xffffu;
+            j = (uint32_t)sd & 0xffu;
+            const Plan *pl = &p.plans[q * MN_MAX_QE + j];
+            const uint32_t slot0 = seed32 & p.cap_mask;
+            const uint32_t vs = p.ring_src[slot0], vd = p.ring_dst[slot0];
+            if (pl->iso && vs == vd) skip = true;
+            if (lane == (int)pl->seed_src) f = vs;
+            if (lane == (int)pl->seed_dst) f = vd;
+            if (lane == (int)j) g = seed32 - p.base32;
+            root = 1;
+        } else {
+            Task *T = &p.tasks[unit];
+            uint32_t ok = 1;
+            if (lane == 0) {
+                uint32_t it = 0;
+                while (vload(&T->ready) != p.epoch) {
+                    if (++it > READY_SPINS) { ok = 0; atomicOr(p.status, ST_TIMEOUT); break; }
+                    __nanosleep(64);
+                }
+                __threadfence();
+            }
+            ok = __shfl_sync(FULL, ok, 0);
+            if (!ok) {
+                if (lane == 0) atomicSub(&sc->busy, 1u);
+                break;
+            }
+            const uint32_t h = __ldcg(&T->qj_lvl);
+            q = h & 0xffffu;
+            j = (h >> 16) & 0xffu;
+            root = h >> 24;
+            tbeg = __ldcg(&T->beg);
+            tend = __ldcg(&T->end);
+            f = __ldcg(&T->f[lane & 15]);
+            g = __ldcg(&T->g[lane & 15]);
+        }
         const Plan *pl = &p.plans[q * MN_MAX_QE + j];
         const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
         const uint32_t rec_bytes = pl->rec_bytes, goff = pl->goff;
-        // lane s holds step s
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
-        const uint32_t slot0 = seed32 & p.cap_mask;
-        const uint32_t vs = p.ring_src[slot0], vd = p.ring_dst[slot0];
-        const uint32_t ssrc = pl->seed_src, sdst = pl->seed_dst;
-        if (iso && vs == vd) continue;
-        uint32_t f = 0, g = 0;
-        if (lane == (int)ssrc) f = vs;
-        if (lane == (int)sdst) f = vd;
-        const uint32_t rel0 = seed32 - p.lo32;
-        if (lane == (int)j) g = rel0;
         const uint32_t *__restrict__ debi = p.debi[q];
         unsigned long long warp_count = 0;
-        if (nsteps == 1) {
-            w_records++;
-            emit_chunk(p, lane, lane == 0, q, nv, ne, rec_bytes, goff, f, g, 0xffu, 0, 0xffu, 0,
-                       &warp_count);
-            if (p.count_only && lane == 0 && warp_count)
-                atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
-            continue;
-        }
-        // per-depth state, lane-distributed
-        uint32_t Lend = 0, Lcur = 0, Lmask = 0, Ltmin = 0, Ltmax = 0, Ltgt = 0, Ldsel = 0;
-        // current depth, uniform
-        uint32_t lvl = 1;
-        uint32_t qe, kind, from, to, dir, avoid, bound_v;
-        int32_t label;
-        uint32_t end, cur, mask, tmin, tmax, tgt, dsel;
-        const uint32_t last = nsteps - 1;
+        const bool direct = rec_bytes * 32 > STAGE_BYTES;
 
-        auto decode = [&](uint32_t s) {
-            uint32_t w0 = __shfl_sync(FULL, sw.x, s);
-            uint32_t w1 = __shfl_sync(FULL, sw.y, s);
-            uint32_t w3 = __shfl_sync(FULL, sw.w, s);
-            qe = w0 & 0xff; kind = (w0 >> 8) & 0xff; from = (w0 >> 16) & 0xff; to = w0 >> 24;
-            dir = w1 & 0xff; avoid = (w1 >> 8) & 0xff; label = (int32_t)(int16_t)(w1 >> 16);
-            bound_v = w3 & 0xffff;
-        };
-        auto open = [&](uint32_t s) {
-            decode(s);
-            const uint32_t w2 = __shfl_sync(FULL, sw.z, s);
-            const uint32_t pred = w2 & 0xffff, succ = w2 >> 16;
-            const uint32_t pe = (pred >> lane) & 1u, se = (succ >> lane) & 1u;
-            tmin = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
-            tmax = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
-            const uint32_t fv = __shfl_sync(FULL, f, from);
-            const uint32_t L = p.L;
-            uint32_t beg;
-            if (kind == K_EXTEND) {
-                dsel = dir;
-                const uint32_t *o = p.offs[dir];
-                if (label >= 0) { beg = o[fv * L + label]; end = o[fv * L + label + 1]; }
-                else            { beg = o[fv * L];         end = o[fv * L + L]; }
-                tgt = 0;
+        // emit the embeddings completed by the valid lanes of one chunk
+        auto emit = [&](bool ok, uint32_t to_new, uint32_t nb, uint32_t qe_new, uint32_t rel) {
+            const uint32_t m = __ballot_sync(FULL, ok);
+            if (!m) return;
+            const uint32_t cnt = __popc(m);
+            w_records += cnt;
+            if (p.count_only) { warp_count += cnt; return; }
+            const uint32_t rank = __popc(m & lanemask_lt());
+            unsigned char *rec;
+            unsigned long long gbase = 0;
+            bool wr = ok;
+            if (direct) {
+                if (lane == 0) gbase = atomicAdd(&p.counts[q * 3 + p.sign], (unsigned long long)cnt);
+                gbase = __shfl_sync(FULL, gbase, 0) + rank;
+                wr = ok && gbase < p.out_cap[q * 2 + p.sign];
+                rec = p.out[q * 2 + p.sign] + gbase * rec_bytes;
             } else {
-                const uint32_t tv = __shfl_sync(FULL, f, to);
-                const uint32_t *oa = p.offs[dir], *ob = p.offs[dir ^ 1u];
-                uint32_t a0, a1, b0, b1;
-                if (label >= 0) {
-                    a0 = oa[fv * L + label]; a1 = oa[fv * L + label + 1];
-                    b0 = ob[tv * L + label]; b1 = ob[tv * L + label + 1];
-                } else {
-                    a0 = oa[fv * L]; a1 = oa[fv * L + L];
-                    b0 = ob[tv * L]; b1 = ob[tv * L + L];
+                if (st_q != q || (st_n + cnt) * rec_bytes > STAGE_BYTES) {
+                    flush();
+                    st_q = q;
+                    st_rb = rec_bytes;
                 }
-                if (a1 - a0 <= b1 - b0) { dsel = dir; tgt = tv; beg = a0; end = a1; }
-                else                    { dsel = dir ^ 1u; tgt = fv; beg = b0; end = b1; }
-                if (label >= 0) {
-                    const uint32_t *nb = p.nbr[dsel];
-                    uint32_t lb = warp_lower_bound(nb, beg, end, tgt, lane);
-                    uint32_t ub = warp_lower_bound(nb, lb, end, tgt + 1, lane);
-                    beg = lb; end = ub;
-                }
+                rec = stage + (st_n + rank) * rec_bytes;
             }
-            cur = beg; mask = 0;
-            if (lane == (int)s) { Lend = end; Ltmin = tmin; Ltmax = tmax; Ltgt = tgt; Ldsel = dsel; }
-        };
-        auto restore = [&](uint32_t s) {
-            decode(s);
-            end = __shfl_sync(FULL, Lend, s);
-            cur = __shfl_sync(FULL, Lcur, s);
-            mask = __shfl_sync(FULL, Lmask, s);
-            tmin = __shfl_sync(FULL, Ltmin, s);
-            tmax = __shfl_sync(FULL, Ltmax, s);
-            tgt = __shfl_sync(FULL, Ltgt, s);
-            dsel = __shfl_sync(FULL, Ldsel, s);
+            for (uint32_t u = 0; u < nv; u++) {
+                uint32_t fu = __shfl_sync(FULL, f, u);
+                if (u == to_new) fu = nb;
+                if (wr) reinterpret_cast<uint32_t *>(rec)[u] = fu;
+            }
+            if ((nv & 1) && wr) reinterpret_cast<uint32_t *>(rec)[nv] = 0;
+            for (uint32_t e = 0; e < ne; e++) {
+                uint32_t ge = __shfl_sync(FULL, g, e);
+                if (e == qe_new) ge = rel;
+                if (wr) reinterpret_cast<unsigned long long *>(rec + goff)[e] = p.base + ge;
+            }
+            if (!direct) st_n += cnt;
+            __syncwarp();
         };
 
-        open(1);
-        while (lvl > 0) {
-            if (++iters > p.max_iters) {
-                if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
-                break;
-            }
-            if (mask == 0) {
-                if (cur >= end) {               // depth exhausted: backtrack
-                    lvl--;
-                    if (lvl > 0) restore(lvl);
+        if (!skip && root >= nsteps) {
+            emit(lane == 0, 0xffu, 0, 0xffu, 0);   // one-edge query: the seed is the embedding
+            skip = true;
+        }
+        if (!skip) {
+            // per-depth state, lane-distributed (lane s holds depth s)
+            uint32_t Lend = 0, Lcur = 0, Lmask = 0, Llo = 0, Lhi = 0, Ltgt = 0, Ldsel = 0;
+            uint32_t lvl = root;
+            uint32_t qe, kind_s, from, to, dir, avoid, bound_v;
+            int32_t label;
+            uint32_t end, cur, mask, tlo, thi, tgt, dsel;
+            const uint32_t last = nsteps - 1;
+
+            auto decode = [&](uint32_t s) {
+                uint32_t w0 = __shfl_sync(FULL, sw.x, s);
+                uint32_t w1 = __shfl_sync(FULL, sw.y, s);
+                uint32_t w3 = __shfl_sync(FULL, sw.w, s);
+                qe = w0 & 0xff; kind_s = (w0 >> 8) & 0xff; from = (w0 >> 16) & 0xff; to = w0 >> 24;
+                dir = w1 & 0xff; avoid = (w1 >> 8) & 0xff; label = (int32_t)(int16_t)(w1 >> 16);
+                bound_v = w3 & 0xffff;
+            };
+            auto open = [&](uint32_t s, bool from_task) {
+                decode(s);
+                const uint32_t w2 = __shfl_sync(FULL, sw.z, s);
+                const uint32_t pred = w2 & 0xffff, succ = w2 >> 16;
+                const uint32_t pe = (pred >> lane) & 1u, se = (succ >> lane) & 1u;
+                tlo = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
+                thi = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
+                tlo = max(tlo, avoid ? p.av_lo : p.vis_lo);
+                thi = min(thi, avoid ? p.av_hi : p.vis_hi);
+                const uint32_t fv = __shfl_sync(FULL, f, from);
+                const uint32_t L = p.L;
+                uint32_t beg;
+                if (kind_s == K_EXTEND) {
+                    dsel = dir + 2;                          // arrival order
+                    const uint32_t *o = p.offs[dir];
+                    if (label >= 0) { beg = o[fv * L + label]; end = o[fv * L + label + 1]; }
+                    else            { beg = o[fv * L];         end = o[fv * L + L]; }
+                    tgt = 0;
+                    if (label >= 0 && !from_task && beg < end) {
+                        const uint32_t *sq = p.s32[dsel];
+                        const uint32_t b32 = p.base32;
+                        auto key = [&](uint32_t i) { return sq[i] - b32; };
+                        const uint32_t nb0 = warp_lower_bound_by(key, beg, end, tlo, lane);
+                        end = tlo < thi ? warp_lower_bound_by(key, nb0, end, thi, lane) : nb0;
+                        beg = nb0;
+                    }
+                } else {
+                    const uint32_t tv = __shfl_sync(FULL, f, to);
+                    const uint32_t *oa = p.offs[dir], *ob = p.offs[dir ^ 1u];
+                    uint32_t a0, a1, b0, b1;
+                    if (label >= 0) {
+                        a0 = oa[fv * L + label]; a1 = oa[fv * L + label + 1];
+                        b0 = ob[tv * L + label]; b1 = ob[tv * L + label + 1];
+                    } else {
+                        a0 = oa[fv * L]; a1 = oa[fv * L + L];
+                        b0 = ob[tv * L]; b1 = ob[tv * L + L];
+                    }
+                    if (a1 - a0 <= b1 - b0) { dsel = dir; tgt = tv; beg = a0; end = a1; }
+                    else                    { dsel = dir ^ 1u; tgt = fv; beg = b0; end = b1; }
+                    if (label >= 0 && !from_task && beg < end) {
+                        const uint32_t *nbv = p.nbr[dsel];
+                        auto keyn = [&](uint32_t i) { return nbv[i]; };
+                        uint32_t lb = warp_lower_bound_by(keyn, beg, end, tgt, lane);
+                        uint32_t ub = warp_lower_bound_by(keyn, lb, end, tgt + 1, lane);
+                        if (lb < ub) {
+                            const uint32_t *sq = p.s32[dsel];
+                            const uint32_t b32 = p.base32;
+                            auto key = [&](uint32_t i) { return sq[i] - b32; };
+                            const uint32_t nb0 = warp_lower_bound_by(key, lb, ub, tlo, lane);
+                            ub = tlo < thi ? warp_lower_bound_by(key, nb0, ub, thi, lane) : nb0;
+                            lb = nb0;
+                        }
+                        beg = lb; end = ub;
+                    }
+                }
+                if (from_task) { beg = tbeg; end = tend; }
+                cur = beg; mask = 0;
+                if (lane == (int)s) { Lend = end; Llo = tlo; Lhi = thi; Ltgt = tgt; Ldsel = dsel; }
+            };
+            auto restore = [&](uint32_t s) {
+                decode(s);
+                end = __shfl_sync(FULL, Lend, s);
+                cur = __shfl_sync(FULL, Lcur, s);
+                mask = __shfl_sync(FULL, Lmask, s);
+                tlo = __shfl_sync(FULL, Llo, s);
+                thi = __shfl_sync(FULL, Lhi, s);
+                tgt = __shfl_sync(FULL, Ltgt, s);
+                dsel = __shfl_sync(FULL, Ldsel, s);
+            };
+            // hand [mid, e) of depth l to the queue; false if the queue is full
+            auto push = [&](uint32_t l, uint32_t mid, uint32_t e) -> bool {
+                uint32_t slot = 0;
+                if (lane == 0) slot = atomicAdd(&sc->q_tail, 1u);
+                slot = __shfl_sync(FULL, slot, 0);
+                if (slot >= p.task_cap) return false;
+                Task *T = &p.tasks[slot];
+                const uint32_t gg = __shfl_sync(FULL, g, lane & 15);
+                reinterpret_cast<uint32_t *>(T)[8 + lane] = lane < 16 ? f : gg;
+                if (lane == 0) {
+                    T->qj_lvl = q | (j << 16) | (l << 24);
+                    T->beg = mid;
+                    T->end = e;
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) *reinterpret_cast<volatile uint32_t *>(&T->ready) = p.epoch;
+                return true;
+            };
+
+            open(lvl, kind == 2);
+            while (lvl >= root) {
+                if (++iters > p.max_iters) {
+                    if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                    break;
+                }
+                if (mask == 0) {
+                    if (cur >= end) {               // depth exhausted: backtrack
+                        lvl--;
+                        if (lvl >= root) restore(lvl);
+                        continue;
+                    }
+                    // when some warp is idle, hand it half of the shallowest
+                    // depth that still has a large unexplored range
+                    if (p.tasks) {
+                        uint32_t idle = 0;
+                        if (lane == 0) idle = vload(&sc->idle);
+                        idle = __shfl_sync(FULL, idle, 0);
+                        if (idle) {
+                            // unexplored range per depth: lanes root..lvl-1 hold
+                            // [Lcur, Lend); this depth keeps its next chunk
+                            uint32_t rb = 0, re = 0;
+                            if ((uint32_t)lane >= root && (uint32_t)lane < lvl) { rb = Lcur; re = Lend; }
+                            if ((uint32_t)lane == lvl) { rb = min(cur + 32, end); re = end; }
+                            const uint32_t big = __ballot_sync(FULL, re > rb && re - rb >= SPLIT_MIN);
+                            if (big) {
+                                const uint32_t l = __ffs(big) - 1;
+                                const uint32_t b0 = __shfl_sync(FULL, rb, l);
+                                const uint32_t e0 = __shfl_sync(FULL, re, l);
+                                const uint32_t mid = b0 + (e0 - b0) / 2;
+                                if (push(l, mid, e0)) {
+                                    if (lane == (int)l) Lend = mid;
+                                    if (l == lvl) end = mid;
+                                }
+                            }
+                        }
+                    }
+                    // test the next 32 candidates, one per lane
+                    const uint32_t idx = cur + (uint32_t)lane;
+                    bool ok = false;
+                    uint32_t nb = 0, rel = 0;
+                    if (idx < end) {
+                        nb = p.nbr[dsel][idx];
+                        const uint32_t sv = p.s32[dsel][idx];
+                        rel = sv - p.base32;
+                        ok = rel >= tlo && rel < thi;
+                        if (ok) ok = (debi[sv & p.cap_mask] >> qe) & 1u;
+                        if (ok && avoid && p.batch_flag) ok = p.batch_flag[sv & p.cap_mask] == 0;
+                        if (kind_s == K_CLOSE) ok = ok && nb == tgt;
+                    }
+                    if (kind_s == K_EXTEND && iso) {
+                        for (uint32_t bv = bound_v; bv; bv &= bv - 1) {
+                            const uint32_t fw = __shfl_sync(FULL, f, __ffs(bv) - 1);
+                            ok = ok && nb != fw;
+                        }
+                    }
+                    w_scanned += min(32u, end - cur);
+                    cur += 32;
+                    if (lvl == last) {
+                        emit(ok, kind_s == K_EXTEND ? to : 0xffu, nb, qe, rel);
+                        continue;
+                    }
+                    mask = __ballot_sync(FULL, ok);
                     continue;
                 }
-                // test the next 32 candidates, one per lane
-                const uint32_t idx = cur + (uint32_t)lane;
-                bool ok = false;
-                uint32_t nb = 0, rel = 0;
-                if (idx < end) {
-                    nb = p.nbr[dsel][idx];
-                    const uint32_t sv = p.s32[dsel][idx];
-                    rel = sv - p.lo32;
-                    ok = rel < p.vis_len && rel >= tmin && rel < tmax;
-                    if (ok) ok = (debi[sv & p.cap_mask] >> qe) & 1u;
-                    if (ok && avoid) {
-                        ok = (uint32_t)(rel - p.brel_lo) >= p.brel_len;
-                        if (ok && p.batch_flag) ok = p.batch_flag[sv & p.cap_mask] == 0;
-                    }
-                    if (kind == K_CLOSE) ok = ok && nb == tgt;
-                }
-                if (kind == K_EXTEND && iso) {
-                    for (uint32_t bv = bound_v; bv; bv &= bv - 1) {
-                        const uint32_t fw = __shfl_sync(FULL, f, __ffs(bv) - 1);
-                        ok = ok && nb != fw;
-                    }
-                }
-                w_scanned += min(32u, end - cur);
-                cur += 32;
-                if (lvl == last) {
-                    w_records += __popc(__ballot_sync(FULL, ok));
-                    emit_chunk(p, lane, ok, q, nv, ne, rec_bytes, goff, f, g,
-                               kind == K_EXTEND ? to : 0xffu, nb, qe, rel, &warp_count);
-                    continue;
-                }
-                mask = __ballot_sync(FULL, ok);
-                continue;
+                // bind the next valid candidate of this depth and descend
+                const uint32_t b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                w_binds++;
+                const uint32_t idx = cur - 32 + b;
+                const uint32_t nb = p.nbr[dsel][idx];
+                const uint32_t rel = p.s32[dsel][idx] - p.base32;
+                if (lane == (int)qe) g = rel;
+                if (kind_s == K_EXTEND && lane == (int)to) f = nb;
+                if (lane == (int)lvl) { Lcur = cur; Lmask = mask; }
+                lvl++;
+                open(lvl, false);
             }
-            // bind the next valid candidate of this depth and descend
-            const uint32_t b = __ffs(mask) - 1;
-            mask &= mask - 1;
-            w_binds++;
-            const uint32_t idx = cur - 32 + b;
-            const uint32_t nb = p.nbr[dsel][idx];
-            const uint32_t rel = p.s32[dsel][idx] - p.lo32;
-            if (lane == (int)qe) g = rel;
-            if (kind == K_EXTEND && lane == (int)to) f = nb;
-            if (lane == (int)lvl) { Lcur = cur; Lmask = mask; }
-            lvl++;
-            open(lvl);
         }
         if (p.count_only && lane == 0 && warp_count)
             atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
-        if (*p.status & ST_TIMEOUT) break;
+        if (lane == 0) {
+            __threadfence();
+            atomicSub(&sc->busy, 1u);
+        }
+        uint32_t stop = 0;
+        if (lane == 0) stop = vload(p.status) & ST_TIMEOUT;
+        if (__shfl_sync(FULL, stop, 0)) break;
     }
+    flush();
     if (lane == 0 && p.work) {
         atomicAdd(&p.work[0], w_seeds);
         atomicAdd(&p.work[1], w_scanned);

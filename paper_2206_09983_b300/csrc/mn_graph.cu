@@ -91,14 +91,18 @@ struct mn_graph {
     int32_t *r_attr = nullptr;
     int64_t *r_ts = nullptr;
 
-    DirArrays base[2][2];   // [buffer][dir]
+    // adjacency problems: 0 out / 1 in by neighbour, 2 out / 3 in by arrival
+    DirArrays base[2][NPROB];   // [buffer][problem]
     int cur = 0;
-    DirArrays tmp[2], delta[2];
+    DirArrays tmp[NPROB], delta[NPROB];
     uint32_t *cnt[2] = {nullptr, nullptr}, *offs[2] = {nullptr, nullptr};
-    unsigned long long *dkA[2] = {nullptr, nullptr}, *dkB[2] = {nullptr, nullptr};
-    uint32_t *dvA[2] = {nullptr, nullptr}, *dvB[2] = {nullptr, nullptr};
-    uint32_t *blk[2] = {nullptr, nullptr};
+    unsigned long long *dkA[NPROB] = {}, *dkB[NPROB] = {};
+    uint32_t *dvA[NPROB] = {}, *dvB[NPROB] = {};
+    uint32_t *blk[NPROB] = {};
     uint32_t nblk_cap = 0;
+    Sched *d_sched = nullptr;   // one scheduler block per enumeration phase
+    Task *d_tasks = nullptr;
+    uint32_t task_cap = 0, epoch = 0;
 
     mn_edge *d_edges = nullptr;
     unsigned long long *d_seqs = nullptr;
@@ -396,18 +400,20 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
 }
 
 // Enumeration over seeds of `phase` (0 = new, 1 = removed, 2 = static) on
-// the adjacency buffer `buf`, visible seqs [lo, vis_hi), batch seqs
-// [b_lo, b_hi) or the per-slot batch flags.
-mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t vis_hi, uint64_t b_lo,
-                           uint64_t b_hi, bool use_flags, bool count_only)
+// adjacency buffer `buf` whose lowest seq is `base`; visible seqs
+// [g->lo, vis_hi); query edges before the seed edge may use seqs
+// [av_lo, av_hi) only (the batch's complement), or, with use_flags, any
+// visible seq whose slot is not flagged.
+mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint64_t vis_hi,
+                           uint64_t av_lo, uint64_t av_hi, bool use_flags, bool count_only)
 {
     EnumParams p;
     memset(&p, 0, sizeof(p));
-    for (int d = 0; d < 2; d++) {
-        p.nbr[d] = g->base[buf][d].nbr;
-        p.s32[d] = g->base[buf][d].s32;
-        p.offs[d] = g->offs[d];
+    for (int t = 0; t < NPROB; t++) {
+        p.nbr[t] = g->base[buf][t].nbr;
+        p.s32[t] = g->base[buf][t].s32;
     }
+    for (int d = 0; d < 2; d++) p.offs[d] = g->offs[d];
     p.L = g->L;
     p.cap_mask = g->cap_mask;
     p.ring_src = g->r_src;
@@ -417,12 +423,16 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t vis_hi, uin
     p.seeds = g->d_seeds[phase];
     p.nseeds = &g->d_ctrl->nseeds[phase];
     p.seed_cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
-    p.next_seed = &g->d_ctrl->next_seed[phase];
-    p.lo32 = (uint32_t)g->lo;
-    p.vis_len = (uint32_t)(vis_hi - g->lo);
-    p.lo = g->lo;
-    p.brel_lo = (uint32_t)(b_lo - g->lo);
-    p.brel_len = (uint32_t)(b_hi - b_lo);
+    p.sched = g->d_sched + phase;
+    p.tasks = g->d_tasks;
+    p.task_cap = g->task_cap;
+    p.epoch = ++g->epoch;
+    p.base32 = (uint32_t)base;
+    p.base = base;
+    p.vis_lo = (uint32_t)(g->lo - base);
+    p.vis_hi = (uint32_t)(vis_hi - base);
+    p.av_lo = (uint32_t)(av_lo - base);
+    p.av_hi = (uint32_t)(av_hi - base);
     p.batch_flag = use_flags ? g->batch_flag : nullptr;
     p.sign = (uint32_t)phase;
     p.counts = g->d_ctrl->counts;
@@ -432,9 +442,9 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t vis_hi, uin
     p.max_iters = g->max_iters;
     p.status = &g->d_ctrl->status;
     p.work = g->d_ctrl->work;
-    CK(cudaMemsetAsync(&g->d_ctrl->next_seed[phase], 0, sizeof(uint32_t), g->stream));
+    CK(cudaMemsetAsync(g->d_sched + phase, 0, sizeof(Sched), g->stream));
     stage_begin(g);
-    k_enumerate<<<g->enum_grid, 256, 0, g->stream>>>(p);
+    k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     stage_end(g, S_ENUM);
     g->stats.enumerate_launches++;
@@ -464,63 +474,65 @@ mn_status launch_seeds_range(mn_graph *g, int phase, uint64_t s_lo, uint64_t n, 
 }
 
 // Rebuild the adjacency into buffer 1-cur: live base entries merged with the
-// batch delta (n entries per direction); offsets from the degree counters.
-mn_status launch_adjacency_update(mn_graph *g, uint64_t n, uint64_t seq0)
+// batch delta (n entries per problem); offsets from the degree counters.
+mn_status launch_adjacency_update(mn_graph *g, uint64_t n, const mn_edge *d_edges, uint64_t seq0)
 {
     const uint32_t *st = &g->d_ctrl->status;
     const uint32_t n_pad = cdiv(n, SORT_TILE) * SORT_TILE;
-    // sort the delta (both directions at once)
-    k_sort_tiles<<<dim3(n_pad / SORT_TILE, 2), 1024, 0, g->stream>>>(g->dkA[0], g->dvA[0], g->dkA[1],
-                                                                      g->dvA[1], st);
+    SortSet A, Bs;
+    for (int t = 0; t < NPROB; t++) {
+        A.k[t] = g->dkA[t]; A.v[t] = g->dvA[t];
+        Bs.k[t] = g->dkB[t]; Bs.v[t] = g->dvB[t];
+    }
+    // sort the delta (all four problems at once)
+    k_sort_tiles<<<dim3(n_pad / SORT_TILE, NPROB), 1024, 0, g->stream>>>(A, st);
     CKL();
-    unsigned long long *ks[2] = {g->dkA[0], g->dkA[1]}, *kd[2] = {g->dkB[0], g->dkB[1]};
-    uint32_t *vs[2] = {g->dvA[0], g->dvA[1]}, *vd[2] = {g->dvB[0], g->dvB[1]};
     for (uint64_t R = SORT_TILE; R < n; R *= 2) {
         const uint32_t threads = cdiv(n, MERGE_ITEMS);
-        k_merge_pass<<<dim3(cdiv(threads, 256), 2), 256, 0, g->stream>>>(
-            ks[0], vs[0], kd[0], vd[0], ks[1], vs[1], kd[1], vd[1], (uint32_t)n, (uint32_t)R, st);
+        k_merge_pass<<<dim3(cdiv(threads, 256), NPROB), 256, 0, g->stream>>>(A, Bs, (uint32_t)n,
+                                                                             (uint32_t)R, st);
         CKL();
-        std::swap(ks[0], kd[0]); std::swap(ks[1], kd[1]);
-        std::swap(vs[0], vd[0]); std::swap(vs[1], vd[1]);
+        std::swap(A, Bs);
     }
-    k_delta_finalize<<<dim3(cdiv(n, 256), 2), 256, 0, g->stream>>>(
-        ks[0], vs[0], ks[1], vs[1], g->delta[0].key, g->delta[0].nbr, g->delta[0].s32,
-        g->delta[1].key, g->delta[1].nbr, g->delta[1].s32, g->cnt[0], g->cnt[1], (uint32_t)n, seq0, st);
+    auto adj4 = [](DirArrays *d) {
+        Adj4 a;
+        for (int t = 0; t < NPROB; t++) { a.key[t] = d[t].key; a.nbr[t] = d[t].nbr; a.s32[t] = d[t].s32; }
+        return a;
+    };
+    Adj4 D = adj4(g->delta);
+    k_delta_finalize<<<dim3(cdiv(n, 256), NPROB), 256, 0, g->stream>>>(A, D, d_edges, g->cnt[0],
+                                                                       g->cnt[1], (uint32_t)n, seq0, st);
     CKL();
+    Adj4 blk;
+    for (int t = 0; t < NPROB; t++) { blk.key[t] = g->blk[t]; blk.nbr[t] = nullptr; blk.s32[t] = nullptr; }
     // compact the live base entries
     const uint64_t n_base = g->hi - g->merged_lo;
     const uint64_t nA = g->hi - g->lo;
     const uint32_t lo32 = (uint32_t)g->lo;
     const uint32_t span = (uint32_t)(g->hi - g->lo);
-    DirArrays *B = g->base[g->cur];
+    Adj4 Bse = adj4(g->base[g->cur]);
+    Adj4 T = adj4(g->tmp);
     if (n_base) {
         const uint32_t nb = cdiv(n_base, CTILE);
-        k_live_count<<<dim3(nb, 2), CBLK, 0, g->stream>>>(B[0].s32, B[1].s32, (uint32_t)n_base,
-                                                           lo32, span, g->blk[0], g->blk[1], st);
+        k_live_count<<<dim3(nb, NPROB), CBLK, 0, g->stream>>>(Bse, (uint32_t)n_base, lo32, span, blk, st);
         CKL();
-        k_scan_blocks<<<2, 1024, 0, g->stream>>>(g->blk[0], g->blk[1], nb, nullptr, nullptr, st);
+        k_scan_blocks<<<NPROB, 1024, 0, g->stream>>>(blk, nb, st);
         CKL();
-        k_compact<<<dim3(nb, 2), CBLK, 0, g->stream>>>(
-            B[0].key, B[0].nbr, B[0].s32, B[1].key, B[1].nbr, B[1].s32, g->tmp[0].key, g->tmp[0].nbr,
-            g->tmp[0].s32, g->tmp[1].key, g->tmp[1].nbr, g->tmp[1].s32, (uint32_t)n_base, lo32, span,
-            g->blk[0], g->blk[1], st);
+        k_compact<<<dim3(nb, NPROB), CBLK, 0, g->stream>>>(Bse, T, (uint32_t)n_base, lo32, span, blk, st);
         CKL();
     }
-    DirArrays *O = g->base[1 - g->cur];
+    Adj4 O = adj4(g->base[1 - g->cur]);
     const uint64_t nO = nA + n;
-    k_merge_csr<<<dim3(cdiv(cdiv(nO, MERGE_ITEMS), 256), 2), 256, 0, g->stream>>>(
-        g->tmp[0].key, g->tmp[0].nbr, g->tmp[0].s32, g->tmp[1].key, g->tmp[1].nbr, g->tmp[1].s32,
-        g->delta[0].key, g->delta[0].nbr, g->delta[0].s32, g->delta[1].key, g->delta[1].nbr,
-        g->delta[1].s32, O[0].key, O[0].nbr, O[0].s32, O[1].key, O[1].nbr, O[1].s32, (uint32_t)nA,
-        (uint32_t)n, st);
+    k_merge_csr<<<dim3(cdiv(cdiv(nO, MERGE_ITEMS), 256), NPROB), 256, 0, g->stream>>>(
+        T, D, O, (uint32_t)nA, (uint32_t)n, st);
     CKL();
-    // offsets of the (vertex, label) segments
+    // offsets of the (vertex, label) segments (shared by both orders)
     const uint64_t nvl = (uint64_t)g->V * g->L;
     const uint32_t nbo = cdiv(nvl, CTILE);
     k_scan_reduce<<<dim3(nbo, 2), CBLK, 0, g->stream>>>(g->cnt[0], g->cnt[1], (uint32_t)nvl, g->blk[0],
                                                          g->blk[1], st);
     CKL();
-    k_scan_blocks<<<2, 1024, 0, g->stream>>>(g->blk[0], g->blk[1], nbo, nullptr, nullptr, st);
+    k_scan_blocks<<<2, 1024, 0, g->stream>>>(blk, nbo, st);
     CKL();
     k_scan_apply<<<dim3(nbo, 2), CBLK, 0, g->stream>>>(g->cnt[0], g->cnt[1], (uint32_t)nvl, g->blk[0],
                                                         g->blk[1], g->offs[0], g->offs[1], st);
@@ -598,23 +610,29 @@ void fill_result(mn_graph *g, mn_batch_result *out, uint64_t seq_lo, uint64_t se
     out->count_neg = g->count_neg.data();
 }
 
-// Run enumeration phases, re-running any whose lists overflowed after
+// One enumeration phase as launched (kept to re-run it after growing lists).
+struct Phase {
+    int phase, buf;
+    uint64_t base, vis_hi, av_lo, av_hi;
+    bool flags;
+};
+
+// Check the phases' status, re-running any whose lists overflowed after
 // growing them to the exact counts.
-mn_status enumerate_phases(mn_graph *g, const int *phases, const int *bufs, int nph,
-                           uint64_t vis_hi, const uint64_t *blo, const uint64_t *bhi,
-                           bool use_flags, bool count_only, bool *over_budget)
+mn_status enumerate_phases(mn_graph *g, const Phase *ph, int nph, bool count_only, bool *over_budget)
 {
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     if (count_only) return MN_OK;
     for (int k = 0; k < nph; k++) {
         bool regrown = false;
-        TRY(grow_outputs(g, phases[k], &regrown, over_budget));
+        TRY(grow_outputs(g, ph[k].phase, &regrown, over_budget));
         if (!regrown) continue;
         CK(cudaMemsetAsync(&g->d_ctrl->counts[0], 0, sizeof(g->h_ctrl->counts), g->stream));
         // counts of the other phase must survive: re-run every phase
         for (int r = 0; r < nph; r++)
-            TRY(launch_enumerate(g, phases[r], bufs[r], vis_hi, blo[r], bhi[r], use_flags, false));
+            TRY(launch_enumerate(g, ph[r].phase, ph[r].buf, ph[r].base, ph[r].vis_hi, ph[r].av_lo,
+                                 ph[r].av_hi, ph[r].flags, false));
         TRY(read_ctrl(g));
         if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     }
@@ -691,28 +709,33 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
     A(dalloc(g, &g->r_attr, C, false));
     A(dalloc(g, &g->r_ts, C, false));
     for (int b = 0; b < 2; b++)
-        for (int d = 0; d < 2; d++) {
-            A(dalloc(g, &g->base[b][d].key, C, false));
-            A(dalloc(g, &g->base[b][d].nbr, C, false));
-            A(dalloc(g, &g->base[b][d].s32, C, false));
+        for (int t = 0; t < NPROB; t++) {
+            A(dalloc(g, &g->base[b][t].key, C, false));
+            A(dalloc(g, &g->base[b][t].nbr, C, false));
+            A(dalloc(g, &g->base[b][t].s32, C, false));
         }
     const uint64_t mb_pad = (uint64_t)cdiv(g->max_batch, SORT_TILE) * SORT_TILE;
+    for (int t = 0; t < NPROB; t++) {
+        A(dalloc(g, &g->tmp[t].key, C, false));
+        A(dalloc(g, &g->tmp[t].nbr, C, false));
+        A(dalloc(g, &g->tmp[t].s32, C, false));
+        A(dalloc(g, &g->delta[t].key, g->max_batch, false));
+        A(dalloc(g, &g->delta[t].nbr, g->max_batch, false));
+        A(dalloc(g, &g->delta[t].s32, g->max_batch, false));
+        A(dalloc(g, &g->dkA[t], mb_pad, false));
+        A(dalloc(g, &g->dkB[t], mb_pad, false));
+        A(dalloc(g, &g->dvA[t], mb_pad, false));
+        A(dalloc(g, &g->dvB[t], mb_pad, false));
+    }
     for (int d = 0; d < 2; d++) {
-        A(dalloc(g, &g->tmp[d].key, C, false));
-        A(dalloc(g, &g->tmp[d].nbr, C, false));
-        A(dalloc(g, &g->tmp[d].s32, C, false));
-        A(dalloc(g, &g->delta[d].key, g->max_batch, false));
-        A(dalloc(g, &g->delta[d].nbr, g->max_batch, false));
-        A(dalloc(g, &g->delta[d].s32, g->max_batch, false));
         A(dalloc(g, &g->cnt[d], nvl));
         A(dalloc(g, &g->offs[d], nvl + 1));
-        A(dalloc(g, &g->dkA[d], mb_pad, false));
-        A(dalloc(g, &g->dkB[d], mb_pad, false));
-        A(dalloc(g, &g->dvA[d], mb_pad, false));
-        A(dalloc(g, &g->dvB[d], mb_pad, false));
     }
     g->nblk_cap = cdiv(std::max<uint64_t>(C, nvl), CTILE) + 1;
-    for (int d = 0; d < 2; d++) A(dalloc(g, &g->blk[d], g->nblk_cap));
+    for (int t = 0; t < NPROB; t++) A(dalloc(g, &g->blk[t], g->nblk_cap));
+    g->task_cap = 1u << 19;
+    A(dalloc(g, &g->d_sched, 3));
+    A(dalloc(g, &g->d_tasks, g->task_cap));
     A(dalloc(g, &g->d_edges, g->max_batch, false));
     A(dalloc(g, &g->d_seqs, g->max_batch, false));
     A(dalloc(g, &g->d_queries, g->max_queries));
@@ -865,7 +888,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         ip.nq = (uint32_t)g->queries.size();
         ip.queries = g->d_queries;
         ip.debi = g->d_debi_ptrs;
-        for (int d = 0; d < 2; d++) { ip.dkey[d] = g->dkA[d]; ip.dval[d] = g->dvA[d]; }
+        for (int t = 0; t < NPROB; t++) { ip.sort.k[t] = g->dkA[t]; ip.sort.v[t] = g->dvA[t]; }
         ip.status = &g->d_ctrl->status;
         ip.last_ts_out = &g->d_ctrl->last_ts;
         stage_begin(g);
@@ -873,25 +896,31 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         CKL();
         stage_end(g, S_INGEST);
         stage_begin(g);
-        TRY(launch_adjacency_update(g, n, g->hi));
+        TRY(launch_adjacency_update(g, n, src, g->hi));
         stage_end(g, S_ADJ);
     }
+    // the adjacency enumerated holds seqs from `base` on: the new buffer was
+    // merged at lo; without new edges the current one was merged at merged_lo
     const int nbuf = n ? 1 - g->cur : g->cur;
-    int phases[2], bufs[2], nph = 0;
-    uint64_t blo[2], bhi[2];
+    const uint64_t nbase = n ? g->lo : g->merged_lo;
+    Phase ph[2];
+    int nph = 0;
     if (n && !g->queries.empty()) {
+        // dS+: query edges before the seed edge avoid the batch [hi, hi_new)
+        ph[nph] = Phase{0, nbuf, nbase, hi_new, g->lo, g->hi, false};
         TRY(launch_seeds_range(g, 0, g->hi, n, 0xffffffffu, 0xffffu));
-        TRY(launch_enumerate(g, 0, nbuf, hi_new, g->hi, hi_new, false, count_only));
-        phases[nph] = 0; bufs[nph] = nbuf; blo[nph] = g->hi; bhi[nph] = hi_new; nph++;
+        TRY(launch_enumerate(g, 0, nbuf, nbase, hi_new, g->lo, g->hi, false, count_only));
+        nph++;
     }
     if (x && !g->queries.empty()) {
+        // dS-: query edges before the seed edge avoid the expiring [lo, lo + x)
+        ph[nph] = Phase{1, nbuf, nbase, hi_new, g->lo + x, hi_new, false};
         TRY(launch_seeds_range(g, 1, g->lo, x, 0xffffffffu, 0xffffu));
-        TRY(launch_enumerate(g, 1, nbuf, hi_new, g->lo, g->lo + x, false, count_only));
-        phases[nph] = 1; bufs[nph] = nbuf; blo[nph] = g->lo; bhi[nph] = g->lo + x; nph++;
+        TRY(launch_enumerate(g, 1, nbuf, nbase, hi_new, g->lo + x, hi_new, false, count_only));
+        nph++;
     }
     bool over_budget = false;
-    const mn_status est = enumerate_phases(g, phases, bufs, nph, hi_new, blo, bhi, false, count_only,
-                                           &over_budget);
+    const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
     if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
     // commit (also after a timeout: the adjacency update ran; counts are partial)
     const std::string timeout_msg = g->err;
@@ -944,8 +973,8 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
                                                            g->r_dead, g->batch_flag, &g->d_ctrl->status);
         CKL();
     }
-    int phases[1] = {1}, bufs[1] = {g->cur}, nph = 0;
-    uint64_t blo[1] = {0}, bhi[1] = {0};
+    Phase ph[1] = {Phase{1, g->cur, g->merged_lo, g->hi, g->lo, g->hi, true}};
+    int nph = 0;
     if (n && nq) {
         uint64_t total_ne = 0;
         for (auto &Q : g->queries) total_ne += Q.ne;
@@ -955,12 +984,11 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
                                                                 &g->d_ctrl->nseeds[1],
                                                                 (uint32_t)g->seed_cap[1], &g->d_ctrl->status);
         CKL();
-        TRY(launch_enumerate(g, 1, g->cur, g->hi, g->lo, g->lo, true, count_only));
-        blo[0] = g->lo; bhi[0] = g->lo;
+        TRY(launch_enumerate(g, 1, g->cur, g->merged_lo, g->hi, g->lo, g->hi, true, count_only));
         nph = 1;
     }
     bool over_budget = false;
-    mn_status st = enumerate_phases(g, phases, bufs, nph, g->hi, blo, bhi, true, count_only, &over_budget);
+    mn_status st = enumerate_phases(g, ph, nph, count_only, &over_budget);
     if (n) {
         k_delete_apply<<<cdiv(n, 256), 256, 0, g->stream>>>(ds, (uint32_t)n, g->cap_mask, nq,
                                                             g->d_debi_ptrs, g->r_dead, g->batch_flag,
@@ -1022,7 +1050,7 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
     const uint64_t live = g->hi - g->lo;
     TRY(launch_seeds_range(g, 2, g->lo, live, query_id, 1u));
-    TRY(launch_enumerate(g, 2, g->cur, g->hi, g->lo, g->lo, false, true));
+    TRY(launch_enumerate(g, 2, g->cur, g->merged_lo, g->hi, g->lo, g->hi, false, true));
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     *count = g->h_ctrl->counts[query_id * 3 + 2];
@@ -1035,10 +1063,10 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
 
 namespace {
 
-// Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status, seed
-// count and seed cursor (u32 each), [4, 8) work counters, [8, 200) counts,
-// [256, 256 + MN_NOALLOC_MAX_SEEDS) seeds.
-constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SEEDS = 256;
+// Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status and seed
+// count (u32 each), [4, 8) work counters, [8, 200) counts, [200, 204)
+// scheduler words, [256, 256 + MN_NOALLOC_MAX_SEEDS) seeds.
+constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SCHED = 200, NA_SEEDS = 256;
 constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
 static __device__ __align__(256) unsigned long long mn_noalloc_scratch[NA_WORDS];
 
@@ -1090,11 +1118,11 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     }
     EnumParams p;
     memset(&p, 0, sizeof(p));
-    for (int d = 0; d < 2; d++) {
-        p.nbr[d] = g->base[g->cur][d].nbr;
-        p.s32[d] = g->base[g->cur][d].s32;
-        p.offs[d] = g->offs[d];
+    for (int t = 0; t < NPROB; t++) {
+        p.nbr[t] = g->base[g->cur][t].nbr;
+        p.s32[t] = g->base[g->cur][t].s32;
     }
+    for (int d = 0; d < 2; d++) p.offs[d] = g->offs[d];
     p.L = g->L;
     p.cap_mask = g->cap_mask;
     p.ring_src = g->r_src;
@@ -1104,10 +1132,13 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     p.seeds = seeds;
     p.nseeds = &ctl[1];
     p.seed_cap = MN_NOALLOC_MAX_SEEDS;
-    p.next_seed = &ctl[2];
-    p.lo32 = (uint32_t)g->lo;
-    p.vis_len = (uint32_t)live;
-    p.lo = g->lo;
+    p.sched = reinterpret_cast<Sched *>(base + NA_SCHED);   // no task queue: no splitting
+    p.base32 = (uint32_t)g->merged_lo;
+    p.base = g->merged_lo;
+    p.vis_lo = (uint32_t)(g->lo - g->merged_lo);
+    p.vis_hi = (uint32_t)(g->hi - g->merged_lo);
+    p.av_lo = p.vis_lo;
+    p.av_hi = p.vis_hi;
     p.sign = 2;
     p.counts = base + NA_COUNTS;
     p.count_only = 1;
