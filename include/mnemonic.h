@@ -175,6 +175,45 @@ mn_status mn_record_layout(const mn_graph *g, uint32_t query_id, uint32_t *nv, u
  * edge at query edge 0. */
 mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
 
+/* Matching-order policies (mn_set_order_policy).  Every candidate order is
+ * a connected order of the query, so the policy changes the work, never the
+ * result.  Candidate 0 is the paper's order (Sec. III preprocessing: most
+ * selective root, BFS tree; Sec. V: per-seed order, path to the root first);
+ * candidates 1-3 are greedy alternatives (most-connected vertex next,
+ * query edge nearest in declaration order next, highest query degree next). */
+#define MN_ORDER_PAPER   0   /* always candidate 0 (default) */
+#define MN_ORDER_EXPLORE 1   /* a pseudo-random candidate per seed; per-seed work is logged for training */
+#define MN_ORDER_LEARNED 2   /* the candidate with the smallest work predicted by the model */
+
+#define MN_MLP_FEATURES 16
+/* FP32 parameter block of the work model, in this order: W1[16][128],
+ * b1[128], W2[128][128], b2[128], w3[128], b3 (row-major, input-major). */
+#define MN_MLP_PARAMS 18817
+
+mn_status mn_set_order_policy(mn_graph *g, uint32_t policy);
+
+/* Train the work model on the samples logged under MN_ORDER_EXPLORE: full
+ * batch Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error
+ * of log2(1 + work), `epochs` steps; the loss before the first and after the
+ * last step go to *loss_first / *loss_last (either may be NULL).
+ * MN_ERR_STATE if nothing has been logged. */
+mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *loss_first,
+                               float *loss_last);
+
+/* Copy the model's MN_MLP_PARAMS parameters to host `get` (if not NULL),
+ * then replace them with host `set` (if not NULL). */
+mn_status mn_order_model_params(mn_graph *g, float *get, const float *set);
+
+/* Test hooks of the model's kernels, host pointers, on `device`: the
+ * tensor-core forward pass over n rows of 16 BF16 features (x holds raw BF16
+ * bit patterns) into y[n], and the gradient of the mean squared error against
+ * targets t[n] into grad[MN_MLP_PARAMS] with the loss in *loss.  Both use
+ * BF16 weights and BF16 layer-1 activations with FP32 accumulation. */
+mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x, uint64_t n,
+                         float *y);
+mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
+                          uint64_t n, float *grad, float *loss);
+
 /* Largest live window mn_count_static_noalloc accepts: its seed scratch
  * holds one 8-byte work unit per live edge. */
 #define MN_NOALLOC_MAX_SEEDS (1u << 22)

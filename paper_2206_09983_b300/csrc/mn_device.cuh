@@ -62,6 +62,11 @@ struct Step {
 };
 static_assert(sizeof(Step) == 16, "Step is 16 bytes");
 
+// Candidate matching orders compiled per (query, seed edge); 0 is the
+// paper's order (Sec. V), the others are greedy alternatives that a learned
+// model may pick per seed.
+constexpr int NCAND = 4;
+
 // 16-byte aligned: lanes load their step with one 16-byte vector load.
 struct alignas(16) Plan {
     Step step[MN_MAX_QE];   // step[0] is the seed edge
@@ -612,6 +617,7 @@ struct EnumParams {
     unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
     uint32_t *status;
     unsigned long long *work;           // [seeds, entries tested, binds, records]
+    unsigned long long *seed_work;      // optional: entries tested + binds per seed
 };
 
 __device__ __forceinline__ uint32_t vload(const uint32_t *p)
@@ -722,7 +728,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         }
 
         // ---------------------------------------------------------- set up the unit
-        uint32_t q, j, root, f = 0, g = 0, tbeg = 0, tend = 0;
+        uint32_t q, j, kc = 0, sid = 0, root, f = 0, g = 0, tbeg = 0, tend = 0;
         bool skip = false;
         if (kind == 1) {
             w_seeds++;
@@ -730,7 +736,9 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             const uint32_t seed32 = (uint32_t)(sd >> 32);
             q = (uint32_t)(sd >> 8) & 0xffffu;
             j = (uint32_t)sd & 0xffu;
-            const Plan *pl = &p.plans[q * MN_MAX_QE + j];
+            kc = (uint32_t)(sd >> 24) & (NCAND - 1);
+            sid = unit;
+            const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
             const uint32_t slot0 = seed32 & p.cap_mask;
             const uint32_t vs = p.ring_src[slot0], vd = p.ring_dst[slot0];
             if (pl->iso && vs == vd) skip = true;
@@ -760,11 +768,14 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             root = h >> 24;
             tbeg = __ldcg(&T->beg);
             tend = __ldcg(&T->end);
+            kc = __ldcg(&T->pad_[0]);
+            sid = __ldcg(&T->pad_[1]);
             f = __ldcg(&T->f[lane & 15]);
             g = __ldcg(&T->g[lane & 15]);
         }
-        const Plan *pl = &p.plans[q * MN_MAX_QE + j];
+        const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
         const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
+        const unsigned long long work0 = w_scanned + w_binds;
         const uint32_t rec_bytes = pl->rec_bytes, goff = pl->goff;
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
@@ -914,6 +925,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     T->qj_lvl = q | (j << 16) | (l << 24);
                     T->beg = mid;
                     T->end = e;
+                    T->pad_[0] = kc;
+                    T->pad_[1] = sid;
                 }
                 __threadfence();
                 __syncwarp();
@@ -1002,6 +1015,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         }
         if (p.count_only && lane == 0 && warp_count)
             atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
+        if (p.seed_work && lane == 0) {
+            const unsigned long long w = w_scanned + w_binds - work0;
+            atomicAdd(&p.seed_work[sid], w);
+        }
         if (lane == 0) {
             __threadfence();
             atomicSub(&sc->busy, 1u);

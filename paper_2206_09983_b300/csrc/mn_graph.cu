@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "mn_device.cuh"
+#include "mn_learned.cuh"
 
 using namespace mn;
 
@@ -50,7 +51,7 @@ struct QueryHost {
     std::vector<uint32_t> vmask;
     std::vector<mn_qedge> edges;
     std::vector<std::pair<uint32_t, uint32_t>> prec;
-    Plan plans[MN_MAX_QE];
+    Plan plans[MN_MAX_QE][NCAND];   // [seed edge][candidate order]
     QueryDev dev;
     uint32_t *debi = nullptr;
     uint8_t *out[2] = {nullptr, nullptr};
@@ -123,6 +124,22 @@ struct mn_graph {
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     mn_stats stats{};
     bool timing = false;
+    // learned matching order
+    uint32_t policy = 0;                 // MN_ORDER_*
+    float *d_P = nullptr, *d_G = nullptr, *d_M1 = nullptr, *d_M2 = nullptr, *d_loss = nullptr;
+    __nv_bfloat16 *d_w1t = nullptr, *d_w2t = nullptr;
+    uint64_t adam_step = 0;
+    bool packed = false;
+    __nv_bfloat16 *d_X = nullptr;        // features, seed_cap x NCAND rows
+    float *d_y = nullptr;
+    unsigned long long *d_seed_work = nullptr;
+    uint64_t learn_rows = 0;             // capacity of d_X / d_y / d_seed_work (rows)
+    __nv_bfloat16 *d_SX = nullptr;       // training ring
+    float *d_ST = nullptr;
+    uint32_t ring = 1u << 20;
+    uint64_t n_samples = 0, explore_round = 0;
+    uint32_t *d_temporal = nullptr;
+    unsigned long long *d_nsamples = nullptr;   // samples ever logged (ring position)
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
     cudaEvent_t ev_open = nullptr;
@@ -310,7 +327,8 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
         is_tree[tedge[bfs[h]]] = 1;
         bfs_edges.push_back(tedge[bfs[h]]);
     }
-    for (uint32_t j = 0; j < ne; j++) {
+    // candidate edge sequences per seed edge j; k = 0 is the paper's order
+    auto paper_order = [&](uint32_t j) {
         std::vector<int> order;
         const uint32_t a = Q.edges[j].src, b = Q.edges[j].dst;
         auto path_up = [&](int x) {
@@ -324,8 +342,43 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
             if (a != root) { order.push_back(tedge[a]); path_up(parent[a]); }
         }
         for (int e : bfs_edges) order.push_back(e);
-
-        Plan &P = Q.plans[j];
+        return order;
+    };
+    // greedy vertex orders: score(u) over unbound u adjacent to the bound set
+    auto greedy_order = [&](uint32_t j, int mode) {
+        std::vector<int> order;
+        std::vector<char> bnd(nv, 0);
+        bnd[Q.edges[j].src] = bnd[Q.edges[j].dst] = 1;
+        for (uint32_t step = 2; step < nv; step++) {
+            int best = -1, best_e = -1;
+            long best_score = 0;
+            for (uint32_t u = 0; u < nv; u++) {
+                if (bnd[u]) continue;
+                int links = 0, first_e = -1, near = 1 << 20;
+                for (uint32_t e = 0; e < ne; e++) {
+                    const uint32_t x = Q.edges[e].src, y = Q.edges[e].dst;
+                    if ((x == u && bnd[y]) || (y == u && bnd[x])) {
+                        links++;
+                        if (first_e < 0) first_e = (int)e;
+                        near = std::min(near, std::abs((int)e - (int)j));
+                    }
+                }
+                if (!links) continue;
+                long score = mode == 1 ? links * 64 - (long)u            // most connected
+                           : mode == 2 ? -(long)near * 64 - (long)u      // temporally nearest
+                                       : (long)deg[u] * 64 - (long)u;    // highest query degree
+                if (best < 0 || score > best_score) { best = (int)u; best_score = score; best_e = first_e; }
+            }
+            bnd[best] = 1;
+            order.push_back(best_e);
+        }
+        return order;
+    };
+    for (uint32_t j = 0; j < ne; j++) {
+      for (uint32_t kc = 0; kc < NCAND; kc++) {
+        const std::vector<int> order = kc == 0 ? paper_order(j) : greedy_order(j, (int)kc);
+        const uint32_t a = Q.edges[j].src, b = Q.edges[j].dst;
+        Plan &P = Q.plans[j][kc];
         memset(&P, 0, sizeof(P));
         std::vector<char> placed(ne, 0), bound(nv, 0);
         uint32_t bound_mask = 0;
@@ -371,6 +424,7 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
         P.nsteps = (uint8_t)ne; P.nv = (uint8_t)nv; P.ne = (uint8_t)ne; P.iso = (uint8_t)Q.iso;
         P.seed_src = (uint8_t)a; P.seed_dst = (uint8_t)b;
         P.rec_bytes = Q.rec_bytes; P.goff = Q.goff;
+      }
     }
     memset(&Q.dev, 0, sizeof(Q.dev));
     Q.dev.ne = ne;
@@ -382,6 +436,139 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
         p.attr_lo = Q.edges[e].attr_lo; p.attr_hi = Q.edges[e].attr_hi;
         p.ts_lo = Q.edges[e].ts_lo; p.ts_hi = Q.edges[e].ts_hi;
     }
+    return MN_OK;
+}
+
+// ---------------------------------------------------------------- learned order
+
+// He-uniform initial weights from a fixed splitmix64 stream, zero biases.
+void init_params(std::vector<float> &P)
+{
+    P.assign(P_COUNT, 0.f);
+    uint64_t z = 0x4D4E4C4541524EULL;
+    auto uni = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        x ^= x >> 31;
+        return (float)((x >> 11) * (1.0 / 9007199254740992.0)) * 2.f - 1.f;
+    };
+    const float a1 = std::sqrt(6.f / NF), a2 = std::sqrt(6.f / NH), a3 = std::sqrt(6.f / NH);
+    for (int i = 0; i < NF * NH; i++) P[P_W1 + i] = a1 * uni();
+    for (int i = 0; i < NH * NH; i++) P[P_W2 + i] = a2 * uni();
+    for (int i = 0; i < NH; i++) P[P_W3 + i] = 0.1f * a3 * uni();
+}
+
+mn_status ensure_model(mn_graph *g)
+{
+    if (g->d_P) return MN_OK;
+    TRY(dalloc(g, &g->d_P, P_COUNT, false));
+    TRY(dalloc(g, &g->d_G, P_COUNT));
+    TRY(dalloc(g, &g->d_M1, P_COUNT));
+    TRY(dalloc(g, &g->d_M2, P_COUNT));
+    TRY(dalloc(g, &g->d_loss, 1));
+    TRY(dalloc(g, &g->d_w1t, NF * NH, false));
+    TRY(dalloc(g, &g->d_w2t, NH * NH, false));
+    TRY(dalloc(g, &g->d_SX, (uint64_t)g->ring * NF, false));
+    TRY(dalloc(g, &g->d_ST, g->ring, false));
+    TRY(dalloc(g, &g->d_nsamples, 1));
+    std::vector<float> P;
+    init_params(P);
+    CK(cudaMemcpyAsync(g->d_P, P.data(), sizeof(float) * P_COUNT, cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->packed = false;
+    return MN_OK;
+}
+
+mn_status pack_model(mn_graph *g)
+{
+    if (g->packed) return MN_OK;
+    k_mlp_pack<<<cdiv(NH * NH, 256), 256, 0, g->stream>>>(g->d_P, g->d_w1t, g->d_w2t);
+    CKL();
+    g->packed = true;
+    return MN_OK;
+}
+
+mn_status ensure_learn_rows(mn_graph *g, uint64_t seeds)
+{
+    const uint64_t rows = seeds * NCAND;
+    if (rows <= g->learn_rows) return MN_OK;
+    const uint64_t old = g->learn_rows;
+    dfree(g, g->d_X, old * NF * sizeof(__nv_bfloat16));
+    dfree(g, g->d_y, old * sizeof(float));
+    dfree(g, g->d_seed_work, old / NCAND * sizeof(unsigned long long));
+    g->d_X = nullptr; g->d_y = nullptr; g->d_seed_work = nullptr; g->learn_rows = 0;
+    const uint64_t cap = next_pow2(rows);
+    TRY(dalloc(g, &g->d_X, cap * NF, false));
+    TRY(dalloc(g, &g->d_y, cap, false));
+    TRY(dalloc(g, &g->d_seed_work, cap / NCAND, false));
+    g->learn_rows = cap;
+    return MN_OK;
+}
+
+FeatParams feat_params(mn_graph *g, int phase, bool all)
+{
+    FeatParams f;
+    memset(&f, 0, sizeof(f));
+    f.seeds = g->d_seeds[phase];
+    f.nseeds = &g->d_ctrl->nseeds[phase];
+    f.seed_cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
+    f.all_candidates = all ? 1u : 0u;
+    f.ring_src = g->r_src;
+    f.ring_dst = g->r_dst;
+    f.r_label = g->r_label;
+    f.offs[0] = g->offs[0];
+    f.offs[1] = g->offs[1];
+    f.L = g->L;
+    f.cap_mask = g->cap_mask;
+    f.debi = g->d_debi_ptrs;
+    f.plans = g->d_plans;
+    f.temporal = g->d_temporal;
+    f.X = g->d_X;
+    return f;
+}
+
+// Before enumerating `phase`: pick each seed's matching order by policy.
+mn_status choose_orders(mn_graph *g, int phase)
+{
+    if (g->policy == MN_ORDER_PAPER || g->queries.empty()) return MN_OK;
+    TRY(ensure_model(g));
+    TRY(ensure_learn_rows(g, g->seed_cap[phase]));
+    const uint32_t grid = (uint32_t)g->enum_grid;
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
+    if (g->policy == MN_ORDER_EXPLORE) {
+        k_explore<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap,
+                                               ++g->explore_round);
+        CKL();
+    } else {
+        TRY(pack_model(g));
+        k_features<<<grid, 256, 0, g->stream>>>(feat_params(g, phase, true));
+        CKL();
+        k_mlp_forward<<<grid, MLP_WARPS * 32, 0, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND,
+                                                              0, g->d_w1t, g->d_w2t, g->d_P, g->d_y);
+        CKL();
+        k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y);
+        CKL();
+    }
+    if (g->policy == MN_ORDER_EXPLORE)
+        CK(cudaMemsetAsync(g->d_seed_work, 0, sizeof(unsigned long long) * cap, g->stream));
+    return MN_OK;
+}
+
+// After enumerating `phase` under exploration: log features and work.
+mn_status log_samples(mn_graph *g, int phase)
+{
+    if (g->policy != MN_ORDER_EXPLORE || g->queries.empty()) return MN_OK;
+    const uint32_t grid = (uint32_t)g->enum_grid;
+    const uint32_t cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
+    k_features<<<grid, 256, 0, g->stream>>>(feat_params(g, phase, false));
+    CKL();
+    k_log_samples<<<grid, 256, 0, g->stream>>>(g->d_X, g->d_seed_work, &g->d_ctrl->nseeds[phase], cap,
+                                                g->d_SX, g->d_ST, g->d_nsamples, g->ring);
+    CKL();
+    k_advance<<<1, 1, 0, g->stream>>>(g->d_nsamples, &g->d_ctrl->nseeds[phase], cap);
+    CKL();
     return MN_OK;
 }
 
@@ -442,6 +629,7 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.max_iters = g->max_iters;
     p.status = &g->d_ctrl->status;
     p.work = g->d_ctrl->work;
+    p.seed_work = g->policy == MN_ORDER_EXPLORE && phase < 2 ? g->d_seed_work : nullptr;
     CK(cudaMemsetAsync(g->d_sched + phase, 0, sizeof(Sched), g->stream));
     stage_begin(g);
     k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
@@ -739,11 +927,12 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
     A(dalloc(g, &g->d_edges, g->max_batch, false));
     A(dalloc(g, &g->d_seqs, g->max_batch, false));
     A(dalloc(g, &g->d_queries, g->max_queries));
-    A(dalloc(g, &g->d_plans, (uint64_t)g->max_queries * MN_MAX_QE));
+    A(dalloc(g, &g->d_plans, (uint64_t)g->max_queries * MN_MAX_QE * NCAND));
     A(dalloc(g, &g->d_debi_ptrs, g->max_queries));
     A(dalloc(g, &g->d_out_ptrs, (uint64_t)g->max_queries * 2));
     A(dalloc(g, &g->d_out_cap, (uint64_t)g->max_queries * 2));
     A(dalloc(g, &g->d_ctrl, 1));
+    A(dalloc(g, &g->d_temporal, g->max_queries));
 #undef A
     {
         int nsm = 0, per_sm = 0;
@@ -835,9 +1024,11 @@ mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query
         Q.out_cap[s] = g->default_out_cap;
     }
     CK(cudaMemcpyAsync(g->d_queries + qid, &Q.dev, sizeof(QueryDev), cudaMemcpyHostToDevice, g->stream));
-    CK(cudaMemcpyAsync(g->d_plans + (uint64_t)qid * MN_MAX_QE, Q.plans, sizeof(Q.plans),
+    CK(cudaMemcpyAsync(g->d_plans + (uint64_t)qid * MN_MAX_QE * NCAND, Q.plans, sizeof(Q.plans),
                        cudaMemcpyHostToDevice, g->stream));
     CK(cudaMemcpyAsync(g->d_debi_ptrs + qid, &Q.debi, sizeof(uint32_t *), cudaMemcpyHostToDevice, g->stream));
+    const uint32_t tflag = Q.prec.empty() ? 0u : 1u;
+    CK(cudaMemcpyAsync(g->d_temporal + qid, &tflag, sizeof(uint32_t), cudaMemcpyHostToDevice, g->stream));
     CK(cudaMemcpyAsync(g->d_out_ptrs + 2 * qid, Q.out, 2 * sizeof(uint8_t *), cudaMemcpyHostToDevice,
                        g->stream));
     CK(cudaMemcpyAsync(g->d_out_cap + 2 * qid, Q.out_cap, 2 * sizeof(unsigned long long),
@@ -909,14 +1100,18 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         // dS+: query edges before the seed edge avoid the batch [hi, hi_new)
         ph[nph] = Phase{0, nbuf, nbase, hi_new, g->lo, g->hi, false};
         TRY(launch_seeds_range(g, 0, g->hi, n, 0xffffffffu, 0xffffu));
+        TRY(choose_orders(g, 0));
         TRY(launch_enumerate(g, 0, nbuf, nbase, hi_new, g->lo, g->hi, false, count_only));
+        TRY(log_samples(g, 0));
         nph++;
     }
     if (x && !g->queries.empty()) {
         // dS-: query edges before the seed edge avoid the expiring [lo, lo + x)
         ph[nph] = Phase{1, nbuf, nbase, hi_new, g->lo + x, hi_new, false};
         TRY(launch_seeds_range(g, 1, g->lo, x, 0xffffffffu, 0xffffu));
+        TRY(choose_orders(g, 1));
         TRY(launch_enumerate(g, 1, nbuf, nbase, hi_new, g->lo + x, hi_new, false, count_only));
+        TRY(log_samples(g, 1));
         nph++;
     }
     bool over_budget = false;
@@ -924,6 +1119,8 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
     // commit (also after a timeout: the adjacency update ran; counts are partial)
     const std::string timeout_msg = g->err;
+    if (g->policy == MN_ORDER_EXPLORE)
+        for (int k = 0; k < nph; k++) g->n_samples += g->h_ctrl->nseeds[ph[k].phase];
     CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
     const uint64_t seq_lo = g->hi;
     if (n) {
@@ -1245,12 +1442,154 @@ mn_status mn_reset_stats(mn_graph *g)
     return MN_OK;
 }
 
+mn_status mn_set_order_policy(mn_graph *g, uint32_t policy)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (policy > MN_ORDER_LEARNED) return fail(g, MN_ERR_INVALID_ARG, "unknown order policy");
+    CK(cudaSetDevice(g->device));
+    if (policy != MN_ORDER_PAPER) TRY(ensure_model(g));
+    g->policy = policy;
+    return MN_OK;
+}
+
+mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *loss_first,
+                               float *loss_last)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    CK(cudaSetDevice(g->device));
+    TRY(ensure_model(g));
+    unsigned long long total = 0;
+    CK(cudaMemcpyAsync(&total, g->d_nsamples, sizeof(total), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (total == 0) return fail(g, MN_ERR_STATE, "no logged samples: run batches under MN_ORDER_EXPLORE");
+    const uint32_t n = (uint32_t)std::min<unsigned long long>(total, g->ring);
+    static bool attr = false;
+    if (!attr) {
+        CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
+        attr = true;
+    }
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
+    float l0 = 0.f, l1 = 0.f;
+    for (uint32_t e = 0; e <= epochs; e++) {
+        CK(cudaMemsetAsync(g->d_G, 0, sizeof(float) * P_COUNT, g->stream));
+        CK(cudaMemsetAsync(g->d_loss, 0, sizeof(float), g->stream));
+        k_mlp_grad<<<nsm, TR_THREADS, TR_SMEM, g->stream>>>(g->d_SX, g->d_ST, n, g->d_P, g->d_G, g->d_loss);
+        CKL();
+        if (e == 0 || e == epochs) {
+            float l = 0.f;
+            CK(cudaMemcpyAsync(&l, g->d_loss, sizeof(float), cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            if (e == 0) l0 = l; else l1 = l;
+        }
+        if (e == epochs) break;
+        g->adam_step++;
+        const float c1 = 1.f - std::pow(0.9f, (float)g->adam_step);
+        const float c2 = 1.f - std::pow(0.999f, (float)g->adam_step);
+        k_adam<<<cdiv(P_COUNT, 256), 256, 0, g->stream>>>(g->d_P, g->d_G, g->d_M1, g->d_M2, P_COUNT, lr,
+                                                          0.9f, 0.999f, 1e-8f, c1, c2);
+        CKL();
+    }
+    g->packed = false;
+    if (loss_first) *loss_first = l0;
+    if (loss_last) *loss_last = l1;
+    return MN_OK;
+}
+
+mn_status mn_order_model_params(mn_graph *g, float *get, const float *set)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    CK(cudaSetDevice(g->device));
+    TRY(ensure_model(g));
+    if (get) {
+        CK(cudaMemcpyAsync(get, g->d_P, sizeof(float) * P_COUNT, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    if (set) {
+        CK(cudaMemcpyAsync(g->d_P, set, sizeof(float) * P_COUNT, cudaMemcpyHostToDevice, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        g->packed = false;
+    }
+    return MN_OK;
+}
+
 // Test hook: per-warp loop budget of the enumerator (0 restores no limit).
 // A tiny budget makes a bounded device loop give up and report MN_ERR_TIMEOUT.
 mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters)
 {
     if (!g) return MN_ERR_INVALID_ARG;
     g->max_iters = max_iters ? max_iters : ~0ull;
+    return MN_OK;
+}
+
+}  // extern "C"
+
+// ====================================================================== model test hooks
+
+namespace {
+struct DevBuf {
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+}  // namespace
+
+extern "C" {
+
+mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x, uint64_t n, float *y)
+{
+    mn_graph *g = nullptr;
+    if (!params || (n && (!x || !y))) return fail(nullptr, MN_ERR_INVALID_ARG, "NULL argument");
+    if (n > (1ull << 28)) return fail(nullptr, MN_ERR_INVALID_ARG, "too many rows");
+    CK(cudaSetDevice(device));
+    DevBuf P, X, Y, W1, W2;
+    CK(cudaMalloc(&P.p, sizeof(float) * P_COUNT));
+    CK(cudaMalloc(&X.p, 2 * NF * std::max<uint64_t>(n, 1)));
+    CK(cudaMalloc(&Y.p, sizeof(float) * std::max<uint64_t>(n, 1)));
+    CK(cudaMalloc(&W1.p, 2 * NF * NH));
+    CK(cudaMalloc(&W2.p, 2 * NH * NH));
+    CK(cudaMemcpy(P.p, params, sizeof(float) * P_COUNT, cudaMemcpyHostToDevice));
+    if (n) CK(cudaMemcpy(X.p, x, 2 * NF * n, cudaMemcpyHostToDevice));
+    k_mlp_pack<<<cdiv(NH * NH, 256), 256>>>((float *)P.p, (__nv_bfloat16 *)W1.p, (__nv_bfloat16 *)W2.p);
+    CK(cudaGetLastError());
+    if (n) {
+        k_mlp_forward<<<cdiv(n, 16 * MLP_WARPS), MLP_WARPS * 32>>>(
+            (const __nv_bfloat16 *)X.p, nullptr, 1, (uint32_t)n, (const __nv_bfloat16 *)W1.p,
+            (const __nv_bfloat16 *)W2.p, (const float *)P.p, (float *)Y.p);
+        CK(cudaGetLastError());
+        CK(cudaMemcpy(y, Y.p, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    }
+    CK(cudaDeviceSynchronize());
+    return MN_OK;
+}
+
+mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
+                          uint64_t n, float *grad, float *loss)
+{
+    mn_graph *g = nullptr;
+    if (!params || !grad || !loss || (n && (!x || !t))) return fail(nullptr, MN_ERR_INVALID_ARG, "NULL argument");
+    if (n > (1ull << 28)) return fail(nullptr, MN_ERR_INVALID_ARG, "too many rows");
+    CK(cudaSetDevice(device));
+    CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
+    DevBuf P, X, T, G, L;
+    CK(cudaMalloc(&P.p, sizeof(float) * P_COUNT));
+    CK(cudaMalloc(&G.p, sizeof(float) * P_COUNT));
+    CK(cudaMalloc(&L.p, sizeof(float)));
+    CK(cudaMalloc(&X.p, 2 * NF * std::max<uint64_t>(n, 1)));
+    CK(cudaMalloc(&T.p, sizeof(float) * std::max<uint64_t>(n, 1)));
+    CK(cudaMemcpy(P.p, params, sizeof(float) * P_COUNT, cudaMemcpyHostToDevice));
+    if (n) {
+        CK(cudaMemcpy(X.p, x, 2 * NF * n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(T.p, t, sizeof(float) * n, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemset(G.p, 0, sizeof(float) * P_COUNT));
+    CK(cudaMemset(L.p, 0, sizeof(float)));
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+    k_mlp_grad<<<nsm, TR_THREADS, TR_SMEM>>>((const __nv_bfloat16 *)X.p, (const float *)T.p,
+                                             (uint32_t)n, (const float *)P.p, (float *)G.p, (float *)L.p);
+    CK(cudaGetLastError());
+    CK(cudaMemcpy(grad, G.p, sizeof(float) * P_COUNT, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(loss, L.p, sizeof(float), cudaMemcpyDeviceToHost));
     return MN_OK;
 }
 

@@ -37,8 +37,11 @@ EXPORTS = [
     "mn_delete_batch", "mn_fetch_embeddings", "mn_record_layout", "mn_count_static",
     "mn_read_debi", "mn_read_adjacency", "mn_graph_info", "mn_set_work_budget",
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
-    "mn_last_error",
+    "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
+    "mn_mlp_gradient", "mn_last_error",
 ]
+MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
+MLP_PARAMS = 18817
 
 
 class MnError(RuntimeError):
@@ -116,6 +119,12 @@ def load(path: str | None = None):
                                  C.POINTER(C.c_uint32)]),
         "mn_count_static": (S, [P, C.c_uint32, C.POINTER(U64)]),
         "mn_count_static_noalloc": (S, [P, C.c_uint32, C.POINTER(U64)]),
+        "mn_set_order_policy": (S, [P, C.c_uint32]),
+        "mn_train_order_model": (S, [P, C.c_uint32, C.c_float, C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float)]),
+        "mn_order_model_params": (S, [P, P, P]),
+        "mn_mlp_forward": (S, [C.c_int32, P, P, U64, P]),
+        "mn_mlp_gradient": (S, [C.c_int32, P, P, P, U64, P, C.POINTER(C.c_float)]),
         "mn_read_debi": (S, [P, C.c_uint32, U64, U64, P]),
         "mn_read_adjacency": (S, [P, C.c_uint32, U64, P, P, P, C.POINTER(U64)]),
         "mn_graph_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(C.c_uint32)]),
@@ -335,5 +344,48 @@ class Graph:
         self._check(self._lib.mn_get_stats(self._h, C.byref(st)))
         return st.as_dict()
 
+    def set_order_policy(self, policy: str):
+        self._check(self._lib.mn_set_order_policy(self._h, MN_ORDER[policy]))
+
+    def train_order_model(self, epochs: int = 200, lr: float = 1e-3):
+        l0, l1 = C.c_float(), C.c_float()
+        self._check(self._lib.mn_train_order_model(self._h, epochs, lr, C.byref(l0), C.byref(l1)))
+        return l0.value, l1.value
+
+    def model_params(self, new=None) -> np.ndarray:
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        src = None if new is None else np.ascontiguousarray(new, dtype=np.float32)
+        self._check(self._lib.mn_order_model_params(self._h, out.ctypes.data,
+                                                    None if src is None else src.ctypes.data))
+        return out
+
     def reset_stats(self):
         self._check(self._lib.mn_reset_stats(self._h))
+
+
+def mlp_forward(params: np.ndarray, x_bf16_bits: np.ndarray, device: int = 0) -> np.ndarray:
+    """Tensor-core forward pass of the work model (test hook)."""
+    lib = load()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x_bf16_bits, dtype=np.uint16)
+    n = x.shape[0]
+    y = np.zeros(n, dtype=np.float32)
+    st = lib.mn_mlp_forward(device, p.ctypes.data, x.ctypes.data, n, y.ctypes.data)
+    if st != MN_OK:
+        raise MnError(st, lib.mn_last_error(None).decode())
+    return y
+
+
+def mlp_gradient(params, x_bf16_bits, targets, device: int = 0):
+    """Loss and FP32 gradient of the work model on the device (test hook)."""
+    lib = load()
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x_bf16_bits, dtype=np.uint16)
+    t = np.ascontiguousarray(targets, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = C.c_float()
+    st = lib.mn_mlp_gradient(device, p.ctypes.data, x.ctypes.data, t.ctypes.data, len(t),
+                             g.ctypes.data, C.byref(loss))
+    if st != MN_OK:
+        raise MnError(st, lib.mn_last_error(None).decode())
+    return loss.value, g

@@ -16,6 +16,8 @@ draws, the largest estimate below 2^20), so every batch's lists stay
 listable on the device and the oracle can still check samples.
 
 Usage: python tests/golden/calibrate_rmat20_queries.py  (prints the labels)
+       python tests/golden/calibrate_rmat20_queries.py --check NAME '[labels]' '[vlabels]'
+           exact |dS+| of the first batch for one candidate (large node budget)
 """
 import os
 import sys
@@ -82,5 +84,22 @@ def main():
     print("RMAT20_LABELS =", out)
 
 
+def check(name, el, vl):
+    import json
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    s = workloads.rmat20_stream()
+    q = workloads.rmat20_queries({**workloads.RMAT20_LABELS, name: (json.loads(el), json.loads(vl))})[
+        list(SHAPES).index(name)]
+    mask = np.zeros(W + B, dtype=np.uint8)
+    mask[W:] = 1
+    t = time.time()
+    cnt, complete = oracle.delta_count_budget(s, 0, W + B, q, mask, 2 * 10**10)
+    print(f"{name} {el} {vl}: exact |dS+| of batch 0 = {cnt} (complete={complete}, {time.time() - t:.0f}s)")
+
+
 if __name__ == "__main__":
-    main()
+    if len(sys.argv) > 1 and sys.argv[1] == "--check":
+        check(sys.argv[2], sys.argv[3], sys.argv[4])
+    else:
+        main()
