@@ -161,6 +161,9 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=512)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--train-epochs", type=int, default=300)
+    ap.add_argument("--plain-only", action="store_true", help="time only the plain arm (diagnostics)")
+    ap.add_argument("--tuning", default="", help="blocks_per_sm,split_min,split_depth for both arms")
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -186,7 +189,7 @@ def main():
     w = workloads.RMAT20
     W, B = w["window"], w["batch"]
     K, WU = args.steps, max(3, args.warmup)
-    need = W + B * (2 * (WU + K) + 2)
+    need = W + B * (2 * (WU + K) + 2)   # warm-up + timed + end-to-end batches
     stream = workloads.rmat20_stream()
     n = len(stream["src"])
     assert n >= need, "stream too short for the requested steps"
@@ -195,74 +198,93 @@ def main():
     base_ptr = d_edges.data_ptr()
     qs = workloads.rmat20_queries()
     cur_stream = torch.cuda.current_stream(dev)
-    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
-                window=W, max_batch=B, max_queries=len(qs), device=local,
-                stream=cur_stream.cuda_stream, out_capacity=1 << 21)
-    for lo in range(0, W, B):                                   # preload the window
-        g.insert(None, device_ptr=base_ptr + 24 * lo, n=B, count_only=True)
-    for q in qs:
-        g.register_query(q)
-    pos = W
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # ---- device-resident run (value)
-    for _ in range(WU):
-        g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
-        pos += B
-    g.set_timing(True)
-    g.reset_stats()
-    barrier()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lat, counts, per_q = [], [], []
-    ev0.record(cur_stream)
-    for _ in range(K):
-        t0 = time.perf_counter()
-        r = g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
-        lat.append(time.perf_counter() - t0)
-        counts.append((sum(r.count_pos), sum(r.count_neg)))
-        per_q.append((list(r.count_pos), list(r.count_neg)))
-        pos += B
-    ev1.record(cur_stream)
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    barrier()
-    dev_ms = ev0.elapsed_time(ev1)
-    st = g.stats()
-    g.set_timing(False)
-
-    # ---- end-to-end run through the public API from pinned host memory
-    e2e = None
-    if not args.no_e2e:
-        host = torch.from_numpy(packed.view(np.uint8)[24 * pos: 24 * (pos + B * (WU + K))].copy())
-        host = host.pin_memory()
-        hp = host.data_ptr()
-        for k in range(WU):
-            g.insert_ptr(hp + 24 * B * k, B)
-        st0 = g.stats()
+    def arm(policy: str, with_e2e: bool):
+        """One arm on the same stream batches: preload, register, WU warm-up
+        batches (under exploration for the learned arm, then training), K
+        timed batches, then the end-to-end run."""
+        g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
+                    window=W, max_batch=B, max_queries=len(qs), device=local,
+                    stream=cur_stream.cuda_stream, out_capacity=1 << 21)
+        res = {}
+        if args.tuning:
+            g.set_tuning(*[int(x) for x in args.tuning.split(",")])
+        res["tuning"] = g.get_tuning()
+        for lo in range(0, W, B):                               # preload the window
+            g.insert(None, device_ptr=base_ptr + 24 * lo, n=B, count_only=True)
+        for q in qs:
+            g.register_query(q)
+        pos = W
+        g.set_order_policy("explore" if policy == "learned" else "paper")
+        for _ in range(WU):
+            g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+            pos += B
+        if policy == "learned":
+            t0 = time.perf_counter()
+            l0, l1 = g.train_order_model(epochs=args.train_epochs, lr=2e-3)
+            res["train"] = {"loss_first": l0, "loss_last": l1, "epochs": args.train_epochs,
+                            "seconds": time.perf_counter() - t0}
+            g.set_order_policy("learned")
+        g.set_timing(True)
+        g.reset_stats()
         barrier()
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        elat = []
-        for k in range(WU, WU + K):
-            t1 = time.perf_counter()
-            g.insert_ptr(hp + 24 * B * k, B)
-            elat.append(time.perf_counter() - t1)
+        clk = ClockSampler(local)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lat, counts, per_q = [], [], []
+        ev0.record(cur_stream)
+        for _ in range(K):
+            t0 = time.perf_counter()
+            r = g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+            lat.append(time.perf_counter() - t0)
+            counts.append((sum(r.count_pos), sum(r.count_neg)))
+            per_q.append((list(r.count_pos), list(r.count_neg)))
+            pos += B
+        ev1.record(cur_stream)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        st1 = g.stats()
-        e2e = {"value": K * B / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // K,
-               "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // K,
-               "p50_ms": 1e3 * statistics.median(elat),
-               "p99_ms": 1e3 * float(np.percentile(elat, 99))}
-        pos += B * (WU + K)
-    g.close()
+        res["clocks"] = clk.stop()
+        barrier()
+        res.update(dev_ms=ev0.elapsed_time(ev1), lat=lat, counts=counts, per_q=per_q, st=g.stats())
+        g.set_timing(False)
+        res["e2e"] = None
+        if with_e2e:
+            host = torch.from_numpy(packed.view(np.uint8)[24 * pos: 24 * (pos + B * (WU + K))].copy())
+            host = host.pin_memory()
+            hp = host.data_ptr()
+            for k in range(WU):
+                g.insert_ptr(hp + 24 * B * k, B)
+            st0 = g.stats()
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            elat = []
+            for k in range(WU, WU + K):
+                t1 = time.perf_counter()
+                g.insert_ptr(hp + 24 * B * k, B)
+                elat.append(time.perf_counter() - t1)
+            torch.cuda.synchronize()
+            e2e_s = time.perf_counter() - t0
+            st1 = g.stats()
+            res["e2e"] = {"value": world * K * B / e2e_s, "unit": UNIT,
+                          "h2d_bytes_per_step": (st1["h2d_bytes"] - st0["h2d_bytes"]) // K,
+                          "d2h_bytes_per_step": (st1["d2h_bytes"] - st0["d2h_bytes"]) // K,
+                          "p50_ms": 1e3 * statistics.median(elat),
+                          "p99_ms": 1e3 * float(np.percentile(elat, 99))}
+        res["pos"] = pos
+        g.close()
+        return res
+
+    plain = arm("paper", with_e2e=args.plain_only and not args.no_e2e)
+    learned = plain if args.plain_only else arm("learned", with_e2e=not args.no_e2e)
+    for k in range(K):                                  # exact counts: both arms agree
+        assert plain["per_q"][k] == learned["per_q"][k], "learned and plain counts differ"
+    dev_ms, lat, counts, per_q, st = (learned[k] for k in ("dev_ms", "lat", "counts", "per_q", "st"))
+    clocks, e2e, pos = learned["clocks"], learned["e2e"], learned["pos"]
 
     # ---- aggregate over ranks (max time)
     dev_s = dev_ms / 1e3
@@ -302,7 +324,17 @@ def main():
         "config": {"workload": w["name"], "vertices": 1 << w["scale"], "edges": w["num_edges"],
                    "window": W, "batch": B, "queries": workloads.QUERY_NAMES,
                    "semantics": "isomorphism, increasing timestamps", "l2": CTRL_NOTE,
-                   "path": "plain GPU path (per-batch launches, paper matching order)"},
+                   "path": "learned matching order (value) vs plain GPU path with the paper's order"},
+        "plain": {"value": world * K * B / (plain["dev_ms"] / 1e3), "unit": UNIT,
+                  "ms_per_step": plain["dev_ms"] / K,
+                  "latency_ms": {"p50": 1e3 * statistics.median(plain["lat"]),
+                                 "p99": 1e3 * float(np.percentile(plain["lat"], 99))},
+                  "work_per_step": {k: plain["st"][k] / K for k in ("entries_scanned", "binds")},
+                  "stage_ms_per_step": {"enumerate": plain["st"]["ms_enumerate"] / K,
+                                        "adjacency": plain["st"]["ms_adjacency"] / K},
+                  "clocks": plain["clocks"]},
+        "learned_vs_plain": (plain["dev_ms"] / dev_ms) if dev_ms else None,
+        "train": learned.get("train"),
         "latency_ms": {"p50": 1e3 * statistics.median(lat), "p99": 1e3 * float(np.percentile(lat, 99)),
                        "max": 1e3 * max(lat)},
         "embeddings_per_step": {"new": float(np.mean([c[0] for c in counts])),

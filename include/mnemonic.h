@@ -182,8 +182,9 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
  * candidates 1-3 are greedy alternatives (most-connected vertex next,
  * query edge nearest in declaration order next, highest query degree next). */
 #define MN_ORDER_PAPER   0   /* always candidate 0 (default) */
-#define MN_ORDER_EXPLORE 1   /* a pseudo-random candidate per seed; per-seed work is logged for training */
-#define MN_ORDER_LEARNED 2   /* the candidate with the smallest work predicted by the model */
+#define MN_ORDER_EXPLORE 1   /* a pseudo-random candidate per seed; per-seed SM cycles are logged for training */
+#define MN_ORDER_LEARNED 2   /* the candidate with the smallest predicted cost, if it beats the
+                                paper's order by at least 2x; otherwise the paper's order */
 
 #define MN_MLP_FEATURES 16
 /* FP32 parameter block of the work model, in this order: W1[16][128],
@@ -194,7 +195,7 @@ mn_status mn_set_order_policy(mn_graph *g, uint32_t policy);
 
 /* Train the work model on the samples logged under MN_ORDER_EXPLORE: full
  * batch Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error
- * of log2(1 + work), `epochs` steps; the loss before the first and after the
+ * of log2(1 + cycles) (the SM cycles the enumerator spent per seed), `epochs` steps; the loss before the first and after the
  * last step go to *loss_first / *loss_last (either may be NULL).
  * MN_ERR_STATE if nothing has been logged. */
 mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *loss_first,
@@ -214,6 +215,19 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
                           uint64_t n, float *grad, float *loss);
 
+/* Launch parameters of the enumerator (none changes any result): resident
+ * blocks of 8 warps per SM in its persistent grid (0 = the occupancy limit),
+ * the smallest candidate range a busy warp hands to an idle one (0 = 40; at
+ * least 33), the deepest search depth that may be split (0 = any), and the
+ * preferred shared-memory carve-out in percent of the SM's unified L1/shared
+ * storage (-1 = the driver's choice; less shared memory leaves more L1 for
+ * the adjacency and DEBI reads).  mn_get_tuning reads them back with the
+ * occupancy limit. */
+mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min, uint32_t split_depth,
+                        int32_t smem_carveout);
+mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *max_blocks_per_sm,
+                        uint32_t *split_min, uint32_t *split_depth, int32_t *smem_carveout);
+
 /* Largest live window mn_count_static_noalloc accepts: its seed scratch
  * holds one 8-byte work unit per live edge. */
 #define MN_NOALLOC_MAX_SEEDS (1u << 22)
@@ -225,7 +239,7 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
  * audited.  mn_count_static grows its seed buffer with cudaMalloc when the
  * window grows; this variant never calls cudaMalloc, cudaFree or any
  * allocating routine.  Its scratch is one fixed array in the library's
- * device memory (32 MiB plus 2 KiB; every GPU that loads the library holds it
+ * device memory (32 MiB plus 3 KiB; every GPU that loads the library holds it
  * until the process exits).  The paper has no counterpart.
  *   - The first call on a device looks up the array's device address with
  *     that device current and caches it; make that first call before any

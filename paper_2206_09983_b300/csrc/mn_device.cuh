@@ -575,20 +575,25 @@ struct alignas(16) Task {
 };
 static_assert(sizeof(Task) == 160, "Task is 160 bytes");
 
-// Scheduler words of one enumerator launch (zeroed before the launch).
+// Scheduler words of one enumerator launch (zeroed before the launch), each
+// on its own 128-byte line: the idle count is read by every busy warp and
+// must not share a line with the counters that take atomics.
+struct alignas(128) SchedWord {
+    uint32_t v;
+    uint32_t pad_[31];
+};
 struct Sched {
-    uint32_t next_seed;         // seed cursor
-    uint32_t q_head, q_tail;    // task queue: taken / reserved slots
-    uint32_t idle;              // warps waiting for work
-    uint32_t busy;              // warps running a seed or a task
-    uint32_t pad_[3];
+    SchedWord next_seed;        // seed cursor
+    SchedWord q_head, q_tail;   // task queue: taken / reserved slots
+    SchedWord idle;             // warps waiting for work
+    SchedWord busy;             // warps running a seed or a task
 };
 
 constexpr int ENUM_WARPS = 8;              // warps per block
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
 constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 4 us per poll)
 constexpr uint32_t READY_SPINS = 1u << 22; // bound on waiting for a reserved task
-constexpr uint32_t SPLIT_MIN = 64;         // split a depth's range only above this many entries
+constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
 
 struct EnumParams {
     const uint32_t *nbr[NPROB];         // 0,1: by neighbour (out, in); 2,3: by arrival
@@ -617,7 +622,9 @@ struct EnumParams {
     unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
     uint32_t *status;
     unsigned long long *work;           // [seeds, entries tested, binds, records]
-    unsigned long long *seed_work;      // optional: entries tested + binds per seed
+    unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
+    uint32_t split_min;                 // smallest range handed to an idle warp
+    uint32_t split_depth;               // deepest search depth that may be split
 };
 
 __device__ __forceinline__ uint32_t vload(const uint32_t *p)
@@ -667,6 +674,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
     const uint32_t nseeds = min(*p.nseeds, p.seed_cap);
     Sched *sc = p.sched;
     unsigned long long iters = 0;
+    uint32_t poll = 0;                       // chunk counter: check for idle warps every 4th
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0;
     uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0;
 
@@ -692,19 +700,19 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         uint32_t kind = 0, unit = 0;
         if (lane == 0) {
             if (p.tasks) {
-                uint32_t h = vload(&sc->q_head);
-                const uint32_t t = min(vload(&sc->q_tail), p.task_cap);
+                uint32_t h = vload(&sc->q_head.v);
+                const uint32_t t = min(vload(&sc->q_tail.v), p.task_cap);
                 while (h < t) {
-                    const uint32_t prev = atomicCAS(&sc->q_head, h, h + 1);
+                    const uint32_t prev = atomicCAS(&sc->q_head.v, h, h + 1);
                     if (prev == h) { kind = 2; unit = h; break; }
                     h = prev;
                 }
             }
             if (!kind) {
-                const uint32_t s = atomicAdd(&sc->next_seed, 1u);
+                const uint32_t s = atomicAdd(&sc->next_seed.v, 1u);
                 if (s < nseeds) { kind = 1; unit = s; }
             }
-            if (kind) atomicAdd(&sc->busy, 1u);
+            if (kind) atomicAdd(&sc->busy.v, 1u);
         }
         kind = __shfl_sync(FULL, kind, 0);
         unit = __shfl_sync(FULL, unit, 0);
@@ -712,16 +720,16 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             // idle: wait (bounded) until a task appears or no warp is busy
             uint32_t more = 0;
             if (lane == 0 && p.tasks) {
-                atomicAdd(&sc->idle, 1u);
+                atomicAdd(&sc->idle.v, 1u);
                 uint32_t nap = 128;
                 for (uint32_t it = 0; it < IDLE_SPINS; it++) {
                     __threadfence();
-                    if (vload(&sc->q_head) < min(vload(&sc->q_tail), p.task_cap)) { more = 1; break; }
-                    if (vload(&sc->busy) == 0) break;
+                    if (vload(&sc->q_head.v) < min(vload(&sc->q_tail.v), p.task_cap)) { more = 1; break; }
+                    if (vload(&sc->busy.v) == 0) break;
                     __nanosleep(nap);
                     nap = min(nap * 2, 4096u);
                 }
-                atomicSub(&sc->idle, 1u);
+                atomicSub(&sc->idle.v, 1u);
             }
             if (__shfl_sync(FULL, more, 0)) continue;
             break;
@@ -759,7 +767,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             }
             ok = __shfl_sync(FULL, ok, 0);
             if (!ok) {
-                if (lane == 0) atomicSub(&sc->busy, 1u);
+                if (lane == 0) atomicSub(&sc->busy.v, 1u);
                 break;
             }
             const uint32_t h = __ldcg(&T->qj_lvl);
@@ -775,7 +783,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         }
         const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
         const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
-        const unsigned long long work0 = w_scanned + w_binds;
+        long long t_unit = 0;
+        if (p.seed_work && lane == 0) t_unit = clock64();
         const uint32_t rec_bytes = pl->rec_bytes, goff = pl->goff;
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
@@ -915,7 +924,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             // hand [mid, e) of depth l to the queue; false if the queue is full
             auto push = [&](uint32_t l, uint32_t mid, uint32_t e) -> bool {
                 uint32_t slot = 0;
-                if (lane == 0) slot = atomicAdd(&sc->q_tail, 1u);
+                if (lane == 0) slot = atomicAdd(&sc->q_tail.v, 1u);
                 slot = __shfl_sync(FULL, slot, 0);
                 if (slot >= p.task_cap) return false;
                 Task *T = &p.tasks[slot];
@@ -948,9 +957,9 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     }
                     // when some warp is idle, hand it half of the shallowest
                     // depth that still has a large unexplored range
-                    if (p.tasks) {
+                    if (p.tasks && (++poll & 3) == 0) {
                         uint32_t idle = 0;
-                        if (lane == 0) idle = vload(&sc->idle);
+                        if (lane == 0) idle = vload(&sc->idle.v);
                         idle = __shfl_sync(FULL, idle, 0);
                         if (idle) {
                             // unexplored range per depth: lanes root..lvl-1 hold
@@ -958,7 +967,9 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                             uint32_t rb = 0, re = 0;
                             if ((uint32_t)lane >= root && (uint32_t)lane < lvl) { rb = Lcur; re = Lend; }
                             if ((uint32_t)lane == lvl) { rb = min(cur + 32, end); re = end; }
-                            const uint32_t big = __ballot_sync(FULL, re > rb && re - rb >= SPLIT_MIN);
+                            const bool can = (uint32_t)lane <= p.split_depth && re > rb &&
+                                             re - rb >= p.split_min;
+                            const uint32_t big = __ballot_sync(FULL, can);
                             if (big) {
                                 const uint32_t l = __ffs(big) - 1;
                                 const uint32_t b0 = __shfl_sync(FULL, rb, l);
@@ -1015,13 +1026,11 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         }
         if (p.count_only && lane == 0 && warp_count)
             atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
-        if (p.seed_work && lane == 0) {
-            const unsigned long long w = w_scanned + w_binds - work0;
-            atomicAdd(&p.seed_work[sid], w);
-        }
+        if (p.seed_work && lane == 0)                // measured SM cycles of this unit
+            atomicAdd(&p.seed_work[sid], (unsigned long long)(clock64() - t_unit));
         if (lane == 0) {
             __threadfence();
-            atomicSub(&sc->busy, 1u);
+            atomicSub(&sc->busy.v, 1u);
         }
         uint32_t stop = 0;
         if (lane == 0) stop = vload(p.status) & ST_TIMEOUT;

@@ -122,6 +122,9 @@ struct mn_graph {
     std::vector<uint64_t> count_pos, count_neg;
     unsigned long long max_iters = ~0ull;
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
+    int nsm = 0, enum_max_per_sm = 0;
+    uint32_t split_min = SPLIT_MIN, split_depth = MN_MAX_QE;
+    int smem_carveout = -1;     // preferred shared-memory carve-out of the enumerator (%), -1 = driver
     mn_stats stats{};
     bool timing = false;
     // learned matching order
@@ -548,7 +551,8 @@ mn_status choose_orders(mn_graph *g, int phase)
         k_mlp_forward<<<grid, MLP_WARPS * 32, 0, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND,
                                                               0, g->d_w1t, g->d_w2t, g->d_P, g->d_y);
         CKL();
-        k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y);
+        k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
+                                            1.0f);
         CKL();
     }
     if (g->policy == MN_ORDER_EXPLORE)
@@ -630,7 +634,10 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.status = &g->d_ctrl->status;
     p.work = g->d_ctrl->work;
     p.seed_work = g->policy == MN_ORDER_EXPLORE && phase < 2 ? g->d_seed_work : nullptr;
+    p.split_min = g->split_min;
+    p.split_depth = g->split_depth;
     CK(cudaMemsetAsync(g->d_sched + phase, 0, sizeof(Sched), g->stream));
+    CK(cudaFuncSetAttribute(k_enumerate, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
     stage_begin(g);
     k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
@@ -940,7 +947,9 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         if (e == cudaSuccess)
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, 256, 0);
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
-        g->enum_grid = nsm * std::max(per_sm, 1);
+        g->nsm = nsm;
+        g->enum_max_per_sm = std::max(per_sm, 1);
+        g->enum_grid = nsm * g->enum_max_per_sm;
     }
     e = cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_OOM); }
@@ -1261,9 +1270,11 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
 namespace {
 
 // Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status and seed
-// count (u32 each), [4, 8) work counters, [8, 200) counts, [200, 204)
-// scheduler words, [256, 256 + MN_NOALLOC_MAX_SEEDS) seeds.
-constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SCHED = 200, NA_SEEDS = 256;
+// count (u32 each), [4, 8) work counters, [8, 200) counts, [256, 336)
+// scheduler words (one 128-byte line each), [384, 384 + MN_NOALLOC_MAX_SEEDS)
+// seeds.
+constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SCHED = 256, NA_SEEDS = 384;
+static_assert(NA_SCHED * 8 + sizeof(Sched) <= NA_SEEDS * 8, "scheduler words overlap the seeds");
 constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
 static __device__ __align__(256) unsigned long long mn_noalloc_scratch[NA_WORDS];
 
@@ -1510,6 +1521,33 @@ mn_status mn_order_model_params(mn_graph *g, float *get, const float *set)
         CK(cudaStreamSynchronize(g->stream));
         g->packed = false;
     }
+    return MN_OK;
+}
+
+mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min, uint32_t split_depth,
+                        int32_t smem_carveout)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (smem_carveout < -1 || smem_carveout > 100)
+        return fail(g, MN_ERR_INVALID_ARG, "smem_carveout must be -1 or 0..100");
+    g->smem_carveout = smem_carveout;
+    if (blocks_per_sm > (uint32_t)g->enum_max_per_sm)
+        return fail(g, MN_ERR_INVALID_ARG, "blocks_per_sm above the enumerator's occupancy limit");
+    g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm : (uint32_t)g->enum_max_per_sm);
+    g->split_min = split_min ? std::max<uint32_t>(split_min, 33) : SPLIT_MIN;
+    g->split_depth = split_depth ? split_depth : MN_MAX_QE;
+    return MN_OK;
+}
+
+mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *max_blocks_per_sm,
+                        uint32_t *split_min, uint32_t *split_depth, int32_t *smem_carveout)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    if (smem_carveout) *smem_carveout = g->smem_carveout;
+    if (blocks_per_sm) *blocks_per_sm = (uint32_t)(g->enum_grid / std::max(g->nsm, 1));
+    if (max_blocks_per_sm) *max_blocks_per_sm = (uint32_t)g->enum_max_per_sm;
+    if (split_min) *split_min = g->split_min;
+    if (split_depth) *split_depth = g->split_depth;
     return MN_OK;
 }
 

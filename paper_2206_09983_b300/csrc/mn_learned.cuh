@@ -10,7 +10,8 @@
 // BF16 with FP32 accumulation (inference: mma.sync m16n8k16 on the tensor
 // cores), FP32 master weights, mean squared error on log2(1 + work), Adam
 // (Kingma & Ba, 2015).  Training data are logged by the enumerator itself:
-// per seed the adjacency entries it tested plus the candidates it bound.
+// per seed the SM cycles spent on it (summed over the seed's own unit and
+// every subtree split off from it).
 #pragma once
 #include <cuda_bf16.h>
 #include "mn_device.cuh"
@@ -312,18 +313,22 @@ __global__ void k_adam(float *P, const float *G, float *M1, float *M2, int n, fl
 
 // ------------------------------------------------------------------ order choice
 
-// Per seed: the candidate order with the smallest predicted work.
+// Per seed: the candidate order with the smallest predicted cost, but the
+// paper's order (candidate 0) unless the best prediction beats it by at least
+// `margin` (log2 units): the paper's order is the fallback.
 __global__ void k_pick(unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
-                       const float *y)
+                       const float *y, float margin)
 {
     const uint32_t n = min(*nseeds, seed_cap);
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         uint32_t best = 0;
-        float bv = y[(size_t)s * NCAND];
+        const float y0 = y[(size_t)s * NCAND];
+        float bv = y0;
         for (uint32_t k = 1; k < NCAND; k++) {
             const float v = y[(size_t)s * NCAND + k];
             if (v < bv) { bv = v; best = k; }
         }
+        if (bv > y0 - margin) best = 0;
         seeds[s] = (seeds[s] & ~(0xffull << 24)) | ((unsigned long long)best << 24);
     }
 }
@@ -344,7 +349,7 @@ __global__ void k_explore(unsigned long long *seeds, const uint32_t *nseeds, uin
     }
 }
 
-// Append (features of the seed's own order, log2(1 + logged work)) to the
+// Append (features of the seed's own order, log2(1 + logged cycles)) to the
 // training ring at position *pos (advanced afterwards by k_advance).
 __global__ void k_log_samples(const __nv_bfloat16 *X, const unsigned long long *work,
                               const uint32_t *nseeds, uint32_t seed_cap, __nv_bfloat16 *SX,

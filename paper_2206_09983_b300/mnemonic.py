@@ -38,7 +38,7 @@ EXPORTS = [
     "mn_read_debi", "mn_read_adjacency", "mn_graph_info", "mn_set_work_budget",
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
-    "mn_mlp_gradient", "mn_last_error",
+    "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -124,6 +124,9 @@ def load(path: str | None = None):
                                      C.POINTER(C.c_float)]),
         "mn_order_model_params": (S, [P, P, P]),
         "mn_mlp_forward": (S, [C.c_int32, P, P, U64, P]),
+        "mn_set_tuning": (S, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32]),
+        "mn_get_tuning": (S, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
+                              C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]),
         "mn_mlp_gradient": (S, [C.c_int32, P, P, P, U64, P, C.POINTER(C.c_float)]),
         "mn_read_debi": (S, [P, C.c_uint32, U64, U64, P]),
         "mn_read_adjacency": (S, [P, C.c_uint32, U64, P, P, P, C.POINTER(U64)]),
@@ -358,6 +361,17 @@ class Graph:
         self._check(self._lib.mn_order_model_params(self._h, out.ctypes.data,
                                                     None if src is None else src.ctypes.data))
         return out
+
+    def set_tuning(self, blocks_per_sm: int = 0, split_min: int = 0, split_depth: int = 0,
+                   smem_carveout: int = -1):
+        self._check(self._lib.mn_set_tuning(self._h, blocks_per_sm, split_min, split_depth,
+                                            smem_carveout))
+
+    def get_tuning(self) -> dict:
+        v = [C.c_uint32() for _ in range(4)] + [C.c_int32()]
+        self._check(self._lib.mn_get_tuning(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(("blocks_per_sm", "max_blocks_per_sm", "split_min", "split_depth",
+                         "smem_carveout"), [x.value for x in v]))
 
     def reset_stats(self):
         self._check(self._lib.mn_reset_stats(self._h))

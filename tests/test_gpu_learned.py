@@ -82,7 +82,7 @@ def run(policy_schedule, s, qs, W=8000, B=3000, keep=()):
     rows, work, losses = {}, {}, []
     try:
         for lo in range(0, W, B):
-            g.insert(M.edges_from_stream(s, lo, lo + B), count_only=True)
+            g.insert(M.edges_from_stream(s, lo, min(W, lo + B)), count_only=True)
         for q in qs:
             g.register_query(q)
         k = 0
