@@ -149,6 +149,70 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ serving mode
+
+def run_serve(args, local):
+    """Continuous-batching request loop on the window stream: Poisson arrivals
+    of log-uniform batches in [1K, 64K] edges at a fraction of the plain
+    path's measured throughput; queued requests are merged into one device
+    batch when the GPU frees up.  Reports per-request latency (arrival ->
+    counts on the host) and sustained edges/s."""
+    import threading
+    import torch
+    from paper_2206_09983_b300 import build, workloads
+    from paper_2206_09983_b300 import mnemonic as M
+    from paper_2206_09983_b300.serve import Server, poisson_batches
+
+    build.build()
+    torch.cuda.set_device(local)
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    stream = workloads.rmat20_stream()
+    packed = M.edges_from_stream(stream, 0, len(stream["src"]))
+    qs = workloads.rmat20_queries()
+    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
+                window=W, max_batch=B, max_queries=len(qs), device=local, out_capacity=1 << 21)
+    for lo in range(0, W, B):
+        g.insert(packed[lo:lo + B], count_only=True)
+    for q in qs:
+        g.register_query(q)
+    for k in range(3):                                          # warm-up
+        g.insert(packed[W + k * B: W + (k + 1) * B])
+    pos = W + 3 * B
+    rate = args.serve_rate
+    rng = np.random.default_rng(0x5E4E)
+    sched = poisson_batches(rng, args.serve_edges, 1024, B, rate)
+    srv = Server(mem_budget_bytes=8 << 30, merge=True, max_batch=B)
+    srv.add_tenant("rmat20", g, count_only=False)
+    reqs = []
+    t0 = time.perf_counter()
+    for t, size in sched:
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        reqs.append(srv.submit("rmat20", packed[pos:pos + size], t_arrival=t0 + t))
+        pos += size
+    srv.drain(timeout=3600)
+    t_end = max(r.t_done for r in reqs)
+    srv.close()
+    g.close()
+    lat = np.array([1e3 * r.latency for r in reqs])
+    edges = sum(len(r.edges) for r in reqs)
+    merged = np.array([r.merged_with for r in reqs])
+    return {
+        "mode": "serve", "metric": METRIC, "unit": UNIT,
+        "value": edges / (t_end - t0),
+        "offered_edges_per_s": rate, "requests": len(reqs), "edges": edges,
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "max": float(lat.max())},
+        "mean_requests_per_batch": float(np.mean(merged)),
+        "errors": sum(1 for r in reqs if r.error),
+        "config": {"workload": w["name"], "window": W, "max_batch": B,
+                   "arrivals": "Poisson, batch sizes log-uniform in [1024, 65536]",
+                   "path": "plain GPU path, continuous batching (queued requests merged)"},
+    }
+
+
 # ------------------------------------------------------------------ GPU arm
 
 def main():
@@ -164,6 +228,9 @@ def main():
     ap.add_argument("--train-epochs", type=int, default=300)
     ap.add_argument("--plain-only", action="store_true", help="time only the plain arm (diagnostics)")
     ap.add_argument("--tuning", default="", help="blocks_per_sm,split_min,split_depth for both arms")
+    ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
+    ap.add_argument("--serve-rate", type=float, default=4.0e5, help="offered load, edges/s")
+    ap.add_argument("--serve-edges", type=int, default=6_000_000)
     args = ap.parse_args()
     rank, world, local = env_rank()
 
@@ -179,6 +246,11 @@ def main():
             dist.destroy_process_group()
         return rc
 
+    if args.mode == "serve":
+        if rank == 0:
+            print(json.dumps(run_serve(args, local)), flush=True)
+        return 0
+
     import torch
     from paper_2206_09983_b300 import build, workloads
     from paper_2206_09983_b300 import mnemonic as M
@@ -189,7 +261,7 @@ def main():
     w = workloads.RMAT20
     W, B = w["window"], w["batch"]
     K, WU = args.steps, max(3, args.warmup)
-    need = W + B * (2 * (WU + K) + 2)   # warm-up + timed + end-to-end batches
+    need = W + B * (2 * (WU + K) + 2 + 16)   # warm-up, autotuning, timed, end-to-end batches
     stream = workloads.rmat20_stream()
     n = len(stream["src"])
     assert n >= need, "stream too short for the requested steps"
@@ -204,7 +276,7 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    def arm(policy: str, with_e2e: bool):
+    def arm(policy: str, with_e2e: bool, skip: int = 0):
         """One arm on the same stream batches: preload, register, WU warm-up
         batches (under exploration for the learned arm, then training), K
         timed batches, then the end-to-end run."""
@@ -230,6 +302,16 @@ def main():
             res["train"] = {"loss_first": l0, "loss_last": l1, "epochs": args.train_epochs,
                             "seconds": time.perf_counter() - t0}
             g.set_order_policy("learned")
+            if not args.tuning:                                  # online autotuning on live batches
+                g.autotune(1)
+                res["tune_batches"] = g.autotune_state()[1]
+                while g.autotune_state()[0]:
+                    g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+                    pos += B
+        else:
+            for _ in range(skip):                                # same batches as the learned arm
+                g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
+                pos += B
         g.set_timing(True)
         g.reset_stats()
         barrier()
@@ -276,11 +358,15 @@ def main():
                           "p50_ms": 1e3 * statistics.median(elat),
                           "p99_ms": 1e3 * float(np.percentile(elat, 99))}
         res["pos"] = pos
+        res["tuning_used"] = g.get_tuning()
         g.close()
         return res
 
-    plain = arm("paper", with_e2e=args.plain_only and not args.no_e2e)
-    learned = plain if args.plain_only else arm("learned", with_e2e=not args.no_e2e)
+    if args.plain_only:
+        plain = learned = arm("paper", with_e2e=not args.no_e2e)
+    else:
+        learned = arm("learned", with_e2e=not args.no_e2e)
+        plain = arm("paper", with_e2e=False, skip=learned.get("tune_batches", 0))
     for k in range(K):                                  # exact counts: both arms agree
         assert plain["per_q"][k] == learned["per_q"][k], "learned and plain counts differ"
     dev_ms, lat, counts, per_q, st = (learned[k] for k in ("dev_ms", "lat", "counts", "per_q", "st"))
@@ -335,6 +421,7 @@ def main():
                   "clocks": plain["clocks"]},
         "learned_vs_plain": (plain["dev_ms"] / dev_ms) if dev_ms else None,
         "train": learned.get("train"),
+        "tuning": {"plain": plain.get("tuning_used"), "learned": learned.get("tuning_used")},
         "latency_ms": {"p50": 1e3 * statistics.median(lat), "p99": 1e3 * float(np.percentile(lat, 99)),
                        "max": 1e3 * max(lat)},
         "embeddings_per_step": {"new": float(np.mean([c[0] for c in counts])),

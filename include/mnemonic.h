@@ -228,6 +228,16 @@ mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min,
 mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *max_blocks_per_sm,
                         uint32_t *split_min, uint32_t *split_depth, int32_t *smem_carveout);
 
+/* Online autotuning of the launch parameters above: each of the next
+ * insert batches that enumerates runs under one candidate configuration
+ * (blocks per SM x split threshold x split depth), `batches_per_config` batches
+ * each; then the configuration with the least enumeration time per unit of
+ * work (adjacency entries tested + candidates bound) is kept.  Results are
+ * unaffected.  mn_autotune_state reports whether tuning is still running and
+ * how many configurations are left. */
+mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config);
+mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left);
+
 /* Largest live window mn_count_static_noalloc accepts: its seed scratch
  * holds one 8-byte work unit per live edge. */
 #define MN_NOALLOC_MAX_SEEDS (1u << 22)

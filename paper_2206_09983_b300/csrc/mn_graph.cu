@@ -125,6 +125,13 @@ struct mn_graph {
     int nsm = 0, enum_max_per_sm = 0;
     uint32_t split_min = SPLIT_MIN, split_depth = MN_MAX_QE;
     int smem_carveout = -1;     // preferred shared-memory carve-out of the enumerator (%), -1 = driver
+    // online autotuner: candidate launch configurations tried on live batches
+    struct TuneCfg { uint32_t bps, split_min, split_depth; };
+    bool tuning = false;
+    std::vector<TuneCfg> tune_cfgs;
+    std::vector<double> tune_ms, tune_work;
+    uint32_t tune_per = 1, tune_idx = 0, tune_in = 0;
+    cudaEvent_t tune_e0 = nullptr, tune_e1 = nullptr;
     mn_stats stats{};
     bool timing = false;
     // learned matching order
@@ -972,6 +979,8 @@ void mn_destroy_graph(mn_graph *g)
     for (auto &p : g->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
     for (auto e : g->ev_pool) cudaEventDestroy(e);
     if (g->ev_open) cudaEventDestroy(g->ev_open);
+    if (g->tune_e0) cudaEventDestroy(g->tune_e0);
+    if (g->tune_e1) cudaEventDestroy(g->tune_e1);
     if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
@@ -1099,6 +1108,15 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         TRY(launch_adjacency_update(g, n, src, g->hi));
         stage_end(g, S_ADJ);
     }
+    // autotuning: run this batch's enumeration under the next candidate
+    const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
+    if (tune_now) {
+        const auto &c = g->tune_cfgs[g->tune_idx];
+        g->enum_grid = g->nsm * (int)c.bps;
+        g->split_min = c.split_min;
+        g->split_depth = c.split_depth;
+        CK(cudaEventRecord(g->tune_e0, g->stream));
+    }
     // the adjacency enumerated holds seqs from `base` on: the new buffer was
     // merged at lo; without new edges the current one was merged at merged_lo
     const int nbuf = n ? 1 - g->cur : g->cur;
@@ -1123,8 +1141,28 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         TRY(log_samples(g, 1));
         nph++;
     }
+    if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
     bool over_budget = false;
     const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
+    if (tune_now && est == MN_OK) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
+        g->tune_ms[g->tune_idx] += ms;
+        g->tune_work[g->tune_idx] += (double)(g->h_ctrl->work[1] + g->h_ctrl->work[2]) + 1.0;
+        if (++g->tune_in >= g->tune_per) {
+            g->tune_in = 0;
+            if (++g->tune_idx == g->tune_cfgs.size()) {       // keep the fastest per unit of work
+                size_t best = 0;
+                for (size_t k = 1; k < g->tune_cfgs.size(); k++)
+                    if (g->tune_ms[k] / g->tune_work[k] < g->tune_ms[best] / g->tune_work[best]) best = k;
+                const auto &c = g->tune_cfgs[best];
+                g->enum_grid = g->nsm * (int)c.bps;
+                g->split_min = c.split_min;
+                g->split_depth = c.split_depth;
+                g->tuning = false;
+            }
+        }
+    }
     if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
     // commit (also after a timeout: the adjacency update ran; counts are partial)
     const std::string timeout_msg = g->err;
@@ -1536,6 +1574,35 @@ mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min,
     g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm : (uint32_t)g->enum_max_per_sm);
     g->split_min = split_min ? std::max<uint32_t>(split_min, 33) : SPLIT_MIN;
     g->split_depth = split_depth ? split_depth : MN_MAX_QE;
+    return MN_OK;
+}
+
+mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    CK(cudaSetDevice(g->device));
+    if (!g->tune_e0) CK(cudaEventCreate(&g->tune_e0));
+    if (!g->tune_e1) CK(cudaEventCreate(&g->tune_e1));
+    g->tune_cfgs.clear();
+    std::vector<uint32_t> bps = {1u};
+    if (g->enum_max_per_sm > 1) bps.push_back((uint32_t)g->enum_max_per_sm);
+    for (uint32_t b : bps)
+        for (uint32_t sm : {33u, 40u, 64u, 128u})
+            for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE}) g->tune_cfgs.push_back({b, sm, sd});
+    g->tune_ms.assign(g->tune_cfgs.size(), 0.0);
+    g->tune_work.assign(g->tune_cfgs.size(), 0.0);
+    g->tune_per = std::max<uint32_t>(batches_per_config, 1);
+    g->tune_idx = 0;
+    g->tune_in = 0;
+    g->tuning = true;
+    return MN_OK;
+}
+
+mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    if (active) *active = g->tuning ? 1 : 0;
+    if (configs_left) *configs_left = g->tuning ? (uint32_t)(g->tune_cfgs.size() - g->tune_idx) : 0u;
     return MN_OK;
 }
 

@@ -38,7 +38,8 @@ EXPORTS = [
     "mn_read_debi", "mn_read_adjacency", "mn_graph_info", "mn_set_work_budget",
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
-    "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_last_error",
+    "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
+    "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -125,6 +126,8 @@ def load(path: str | None = None):
         "mn_order_model_params": (S, [P, P, P]),
         "mn_mlp_forward": (S, [C.c_int32, P, P, U64, P]),
         "mn_set_tuning": (S, [P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int32]),
+        "mn_autotune": (S, [P, C.c_uint32]),
+        "mn_autotune_state": (S, [P, C.POINTER(C.c_int32), C.POINTER(C.c_uint32)]),
         "mn_get_tuning": (S, [P, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32),
                               C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_int32)]),
         "mn_mlp_gradient": (S, [C.c_int32, P, P, P, U64, P, C.POINTER(C.c_float)]),
@@ -366,6 +369,14 @@ class Graph:
                    smem_carveout: int = -1):
         self._check(self._lib.mn_set_tuning(self._h, blocks_per_sm, split_min, split_depth,
                                             smem_carveout))
+
+    def autotune(self, batches_per_config: int = 1):
+        self._check(self._lib.mn_autotune(self._h, batches_per_config))
+
+    def autotune_state(self):
+        a, left = C.c_int32(), C.c_uint32()
+        self._check(self._lib.mn_autotune_state(self._h, C.byref(a), C.byref(left)))
+        return bool(a.value), left.value
 
     def get_tuning(self) -> dict:
         v = [C.c_uint32() for _ in range(4)] + [C.c_int32()]
