@@ -654,6 +654,38 @@ __device__ __forceinline__ uint32_t warp_lower_bound_by(KeyFn key, uint32_t lo, 
     return lo + __popc(__ballot_sync(FULL, less));
 }
 
+// First i in [lo, hi) with key(i) >= t, searched by one lane alone.
+template <class KeyFn>
+__device__ __forceinline__ uint32_t lane_lower_bound(KeyFn key, uint32_t lo, uint32_t hi, uint32_t t)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (key(mid) < t) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// [r1, r2) = [first i with key(i) >= t1, first i with key(i) >= t2) in
+// [lo, hi) for t1 <= t2 and a non-decreasing key; ranges of at most 32 entries
+// take one probe round for both bounds.
+template <class KeyFn>
+__device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi, uint32_t t1,
+                                            uint32_t t2, int lane, uint32_t &r1, uint32_t &r2)
+{
+    if (hi - lo <= 32) {
+        const uint32_t pos = lo + (uint32_t)lane;
+        uint32_t kv = 0;
+        const bool in = pos < hi;
+        if (in) kv = key(pos);
+        r1 = lo + __popc(__ballot_sync(FULL, in && kv < t1));
+        r2 = t1 < t2 ? lo + __popc(__ballot_sync(FULL, in && kv < t2)) : r1;
+        return;
+    }
+    r1 = warp_lower_bound_by(key, lo, hi, t1, lane);
+    r2 = t1 < t2 ? warp_lower_bound_by(key, r1, hi, t2, lane) : r1;
+}
+
 // Warp-per-unit backtracking enumerator (Sec. III enumerator, Sec. V work
 // units, matching orders and masks).  Persistent: warps take split-off
 // subtrees from a global task queue first, then seeds (pull-based
@@ -793,7 +825,11 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         const bool direct = rec_bytes * 32 > STAGE_BYTES;
 
         // emit the embeddings completed by the valid lanes of one chunk
-        auto emit = [&](bool ok, uint32_t to_new, uint32_t nb, uint32_t qe_new, uint32_t rel) {
+        // per-lane overrides: vertex to_new -> nb and edge qe_new -> rel (this
+        // lane's candidate); optionally also vertex to2 -> nb2, edge qe2 -> rel2
+        auto emit = [&](bool ok, uint32_t to_new, uint32_t nb, uint32_t qe_new, uint32_t rel,
+                        uint32_t to2 = 0xffu, uint32_t nb2 = 0, uint32_t qe2 = 0xffu,
+                        uint32_t rel2 = 0) {
             const uint32_t m = __ballot_sync(FULL, ok);
             if (!m) return;
             const uint32_t cnt = __popc(m);
@@ -818,12 +854,14 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             }
             for (uint32_t u = 0; u < nv; u++) {
                 uint32_t fu = __shfl_sync(FULL, f, u);
+                if (u == to2) fu = nb2;
                 if (u == to_new) fu = nb;
                 if (wr) reinterpret_cast<uint32_t *>(rec)[u] = fu;
             }
             if ((nv & 1) && wr) reinterpret_cast<uint32_t *>(rec)[nv] = 0;
             for (uint32_t e = 0; e < ne; e++) {
                 uint32_t ge = __shfl_sync(FULL, g, e);
+                if (e == qe2) ge = rel2;
                 if (e == qe_new) ge = rel;
                 if (wr) reinterpret_cast<unsigned long long *>(rec + goff)[e] = p.base + ge;
             }
@@ -874,9 +912,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                         const uint32_t *sq = p.s32[dsel];
                         const uint32_t b32 = p.base32;
                         auto key = [&](uint32_t i) { return sq[i] - b32; };
-                        const uint32_t nb0 = warp_lower_bound_by(key, beg, end, tlo, lane);
-                        end = tlo < thi ? warp_lower_bound_by(key, nb0, end, thi, lane) : nb0;
-                        beg = nb0;
+                        uint32_t r1, r2;
+                        warp_bounds(key, beg, end, tlo, thi, lane, r1, r2);
+                        beg = r1;
+                        end = r2;
                     }
                 } else {
                     const uint32_t tv = __shfl_sync(FULL, f, to);
@@ -894,15 +933,13 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     if (label >= 0 && !from_task && beg < end) {
                         const uint32_t *nbv = p.nbr[dsel];
                         auto keyn = [&](uint32_t i) { return nbv[i]; };
-                        uint32_t lb = warp_lower_bound_by(keyn, beg, end, tgt, lane);
-                        uint32_t ub = warp_lower_bound_by(keyn, lb, end, tgt + 1, lane);
+                        uint32_t lb, ub;
+                        warp_bounds(keyn, beg, end, tgt, tgt + 1, lane, lb, ub);
                         if (lb < ub) {
                             const uint32_t *sq = p.s32[dsel];
                             const uint32_t b32 = p.base32;
                             auto key = [&](uint32_t i) { return sq[i] - b32; };
-                            const uint32_t nb0 = warp_lower_bound_by(key, lb, ub, tlo, lane);
-                            ub = tlo < thi ? warp_lower_bound_by(key, nb0, ub, thi, lane) : nb0;
-                            lb = nb0;
+                            warp_bounds(key, lb, ub, tlo, thi, lane, lb, ub);
                         }
                         beg = lb; end = ub;
                     }
@@ -941,6 +978,123 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 __syncwarp();
                 if (lane == 0) *reinterpret_cast<volatile uint32_t *>(&T->ready) = p.epoch;
                 return true;
+            };
+
+            // The last two depths fused: every valid candidate of a chunk at
+            // depth last-1 computes its own last-depth range (lane-local
+            // searches, all candidates at once); the warp then sweeps the
+            // concatenated ranges 32 entries at a time, each entry tested with
+            // its owner candidate's binding (owner found by a search over the
+            // lanes' prefix sums) and emitted with both bindings.
+            auto expand_last = [&](bool okc, uint32_t nb_c, uint32_t rel_c) {
+                const uint32_t qe_p = qe, to_p = kind_s == K_EXTEND ? to : 0xffu;
+                const uint32_t w0 = __shfl_sync(FULL, sw.x, last), w1 = __shfl_sync(FULL, sw.y, last);
+                const uint32_t w2 = __shfl_sync(FULL, sw.z, last), w3 = __shfl_sync(FULL, sw.w, last);
+                const uint32_t qe_l = w0 & 0xff, kind_l = (w0 >> 8) & 0xff;
+                const uint32_t from_l = (w0 >> 16) & 0xff, to_l = w0 >> 24;
+                const uint32_t dir_l = w1 & 0xff, avoid_l = (w1 >> 8) & 0xff;
+                const int32_t label_l = (int32_t)(int16_t)(w1 >> 16);
+                const uint32_t pred_l = w2 & 0xffff, succ_l = w2 >> 16, bv_l = w3 & 0xffff;
+                // temporal bounds from edges bound above, then this lane's candidate
+                const uint32_t others = ~(1u << qe_p);
+                const uint32_t pe = ((pred_l & others) >> lane) & 1u, se = ((succ_l & others) >> lane) & 1u;
+                uint32_t tl = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
+                uint32_t th = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
+                tl = max(tl, avoid_l ? p.av_lo : p.vis_lo);
+                th = min(th, avoid_l ? p.av_hi : p.vis_hi);
+                if ((pred_l >> qe_p) & 1u) tl = max(tl, rel_c + 1);
+                if ((succ_l >> qe_p) & 1u) th = min(th, rel_c);
+                const uint32_t f_from = __shfl_sync(FULL, f, from_l), f_to = __shfl_sync(FULL, f, to_l);
+                const uint32_t fv = from_l == to_p ? nb_c : f_from;
+                const uint32_t tv = to_l == to_p ? nb_c : f_to;
+                const uint32_t L = p.L, b32 = p.base32;
+                uint32_t beg = 0, end2 = 0, dsl = dir_l + 2, tg = 0;
+                if (okc) {
+                    if (kind_l == K_EXTEND) {
+                        const uint32_t *o = p.offs[dir_l];
+                        if (label_l >= 0) { beg = o[fv * L + label_l]; end2 = o[fv * L + label_l + 1]; }
+                        else              { beg = o[fv * L];           end2 = o[fv * L + L]; }
+                        if (label_l >= 0 && beg < end2) {
+                            const uint32_t *sq = p.s32[dsl];
+                            auto key = [&](uint32_t i) { return sq[i] - b32; };
+                            const uint32_t r1 = lane_lower_bound(key, beg, end2, tl);
+                            end2 = tl < th ? lane_lower_bound(key, r1, end2, th) : r1;
+                            beg = r1;
+                        }
+                    } else {
+                        const uint32_t *oa = p.offs[dir_l], *ob = p.offs[dir_l ^ 1u];
+                        uint32_t a0, a1, c0, c1;
+                        if (label_l >= 0) {
+                            a0 = oa[fv * L + label_l]; a1 = oa[fv * L + label_l + 1];
+                            c0 = ob[tv * L + label_l]; c1 = ob[tv * L + label_l + 1];
+                        } else {
+                            a0 = oa[fv * L]; a1 = oa[fv * L + L];
+                            c0 = ob[tv * L]; c1 = ob[tv * L + L];
+                        }
+                        if (a1 - a0 <= c1 - c0) { dsl = dir_l; tg = tv; beg = a0; end2 = a1; }
+                        else                    { dsl = dir_l ^ 1u; tg = fv; beg = c0; end2 = c1; }
+                        if (label_l >= 0 && beg < end2) {
+                            const uint32_t *nbv = p.nbr[dsl];
+                            auto keyn = [&](uint32_t i) { return nbv[i]; };
+                            const uint32_t lb = lane_lower_bound(keyn, beg, end2, tg);
+                            const uint32_t ub = lane_lower_bound(keyn, lb, end2, tg + 1);
+                            const uint32_t *sq = p.s32[dsl];
+                            auto key = [&](uint32_t i) { return sq[i] - b32; };
+                            const uint32_t r1 = lane_lower_bound(key, lb, ub, tl);
+                            end2 = tl < th ? lane_lower_bound(key, r1, ub, th) : r1;
+                            beg = r1;
+                        }
+                    }
+                }
+                const uint32_t len = end2 > beg ? end2 - beg : 0u;
+                uint32_t inc = len;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, inc, d);
+                    if (lane >= d) inc += y;
+                }
+                const uint32_t total = __shfl_sync(FULL, inc, 31);
+                const uint32_t exc = inc - len;
+                w_binds += __popc(__ballot_sync(FULL, okc));
+                for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+                    if (++iters > p.max_iters) {
+                        if (lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                        break;
+                    }
+                    const uint32_t t = t0 + (uint32_t)lane;
+                    uint32_t o = 0;                  // first lane whose inclusive prefix exceeds t
+#pragma unroll
+                    for (uint32_t st = 16; st; st >>= 1) {
+                        const uint32_t ip = __shfl_sync(FULL, inc, o + st - 1);
+                        if (ip <= t) o += st;
+                    }
+                    const uint32_t obeg = __shfl_sync(FULL, beg, o), oexc = __shfl_sync(FULL, exc, o);
+                    const uint32_t otl = __shfl_sync(FULL, tl, o), oth = __shfl_sync(FULL, th, o);
+                    const uint32_t onb = __shfl_sync(FULL, nb_c, o), orel = __shfl_sync(FULL, rel_c, o);
+                    const uint32_t otg = __shfl_sync(FULL, tg, o), odsl = __shfl_sync(FULL, dsl, o);
+                    bool ok2 = false;
+                    uint32_t nb2 = 0, rel2 = 0;
+                    if (t < total) {
+                        const uint32_t idx = obeg + (t - oexc);
+                        nb2 = p.nbr[odsl][idx];
+                        const uint32_t sv = p.s32[odsl][idx];
+                        rel2 = sv - b32;
+                        ok2 = rel2 >= otl && rel2 < oth;
+                        if (ok2) ok2 = (debi[sv & p.cap_mask] >> qe_l) & 1u;
+                        if (ok2 && avoid_l && p.batch_flag) ok2 = p.batch_flag[sv & p.cap_mask] == 0;
+                        if (kind_l == K_CLOSE) ok2 = ok2 && nb2 == otg;
+                    }
+                    if (kind_l == K_EXTEND && iso) {
+                        for (uint32_t bv = bv_l; bv; bv &= bv - 1) {
+                            const uint32_t wv = __ffs(bv) - 1;
+                            uint32_t fw = __shfl_sync(FULL, f, wv);
+                            if (wv == to_p) fw = onb;
+                            ok2 = ok2 && nb2 != fw;
+                        }
+                    }
+                    w_scanned += min(32u, total - t0);
+                    emit(ok2, kind_l == K_EXTEND ? to_l : 0xffu, nb2, qe_l, rel2, to_p, onb, qe_p, orel);
+                }
             };
 
             open(lvl, kind == 2);
@@ -1005,6 +1159,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     cur += 32;
                     if (lvl == last) {
                         emit(ok, kind_s == K_EXTEND ? to : 0xffu, nb, qe, rel);
+                        continue;
+                    }
+                    if (lvl + 1 == last) {           // candidates' last depths, all at once
+                        expand_last(ok, nb, rel);
                         continue;
                     }
                     mask = __ballot_sync(FULL, ok);

@@ -956,7 +956,9 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
         g->nsm = nsm;
         g->enum_max_per_sm = std::max(per_sm, 1);
-        g->enum_grid = nsm * g->enum_max_per_sm;
+        // 16 warps per SM: more resident warps measured slower (L1 pressure
+        // and contention on the scheduler words outweigh the extra latency hiding)
+        g->enum_grid = nsm * std::min(g->enum_max_per_sm, 2);
     }
     e = cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_OOM); }
@@ -1571,7 +1573,8 @@ mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min,
     g->smem_carveout = smem_carveout;
     if (blocks_per_sm > (uint32_t)g->enum_max_per_sm)
         return fail(g, MN_ERR_INVALID_ARG, "blocks_per_sm above the enumerator's occupancy limit");
-    g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm : (uint32_t)g->enum_max_per_sm);
+    g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm
+                                               : (uint32_t)std::min(g->enum_max_per_sm, 2));
     g->split_min = split_min ? std::max<uint32_t>(split_min, 33) : SPLIT_MIN;
     g->split_depth = split_depth ? split_depth : MN_MAX_QE;
     return MN_OK;
@@ -1585,7 +1588,7 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     if (!g->tune_e1) CK(cudaEventCreate(&g->tune_e1));
     g->tune_cfgs.clear();
     std::vector<uint32_t> bps = {1u};
-    if (g->enum_max_per_sm > 1) bps.push_back((uint32_t)g->enum_max_per_sm);
+    if (g->enum_max_per_sm > 1) bps.push_back(2u);
     for (uint32_t b : bps)
         for (uint32_t sm : {33u, 40u, 64u, 128u})
             for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE}) g->tune_cfgs.push_back({b, sm, sd});
