@@ -397,6 +397,9 @@ def main():
             "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per}
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
     nq = len(qs)
+    tu = learned.get("tuning_used") or {}
+    enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * 8
+                  * max(1, tu.get("blocks_per_sm", 2)))
     adj_bytes_per_batch = 2 * (2 * (W + B) * 12)     # read + write of both directions' entries
     adj = {"kernel": "adjacency update (sort+compact+merge+offsets)",
            "ms_per_batch": st["ms_adjacency"] / K,
@@ -431,7 +434,13 @@ def main():
                    "removed": float(np.mean([c[1][i] for c in per_q]))}
             for i, name in enumerate(workloads.QUERY_NAMES)},
         "stage_ms_per_step": {k: v / K for k, v in stage_ms.items()},
-        "work_per_step": {k: st[k] / K for k in ("seeds", "entries_scanned", "binds", "records")},
+        "work_per_step": {k: st[k] / K for k in ("seeds", "entries_scanned", "binds", "records",
+                                                  "tasks_split")},
+        # share of the enumerator's warp-time spent inside work units (the rest
+        # is waiting for work at the end of a launch: load imbalance)
+        "enum_warp_utilization": (st["busy_cycles"] / (st["ms_enumerate"] * 1e-3 * clocks["sm_mhz"] * 1e6
+                                                        * enum_warps)
+                                  if st["ms_enumerate"] and clocks.get("sm_mhz") else None),
         "gpu_launches": st["kernel_launches"],
         "roofline": roof,
         "adjacency_roofline": adj,

@@ -305,6 +305,8 @@ typedef struct {
     uint64_t entries_scanned;
     uint64_t binds;
     uint64_t records;
+    uint64_t busy_cycles;          /* SM cycles enumerator warps spent inside work units */
+    uint64_t tasks_split;          /* subtrees handed from busy to idle warps */
     uint64_t h2d_bytes;            /* bytes the library copied host -> device */
     uint64_t d2h_bytes;            /* bytes copied device -> host (counts, status) */
 } mn_stats;

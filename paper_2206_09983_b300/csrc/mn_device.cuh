@@ -568,7 +568,7 @@ __global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_
 struct alignas(16) Task {
     uint32_t qj_lvl;            // query | seed edge << 16 | depth << 24
     uint32_t beg, end;
-    uint32_t ready;             // epoch of the launch that published the task
+    uint32_t ready;             // slot state: epoch published, epoch|SLOT_ABANDONED given up
     uint32_t pad_[4];
     uint32_t f[MN_MAX_QV];      // data vertex per query vertex
     uint32_t g[MN_MAX_QE];      // seq (relative to the adjacency base) per query edge
@@ -584,7 +584,7 @@ struct alignas(128) SchedWord {
 };
 struct Sched {
     SchedWord next_seed;        // seed cursor
-    SchedWord q_head, q_tail;   // task queue: taken / reserved slots
+    SchedWord q_head, q_tail;   // task queue: tickets drawn by waiters / slots used by publishers
     SchedWord idle;             // warps waiting for work
     SchedWord busy;             // warps running a seed or a task
 };
@@ -592,7 +592,6 @@ struct Sched {
 constexpr int ENUM_WARPS = 8;              // warps per block
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
 constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 4 us per poll)
-constexpr uint32_t READY_SPINS = 1u << 22; // bound on waiting for a reserved task
 constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
 
 struct EnumParams {
@@ -621,7 +620,7 @@ struct EnumParams {
     uint32_t count_only;
     unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
     uint32_t *status;
-    unsigned long long *work;           // [seeds, entries tested, binds, records]
+    unsigned long long *work;           // [seeds, entries tested, binds, records, busy cycles, tasks]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
     uint32_t split_min;                 // smallest range handed to an idle warp
     uint32_t split_depth;               // deepest search depth that may be split
@@ -630,6 +629,24 @@ struct EnumParams {
 __device__ __forceinline__ uint32_t vload(const uint32_t *p)
 {
     return *reinterpret_cast<const volatile uint32_t *>(p);
+}
+
+// A task slot's state word holds the epoch of the launch that decided it:
+// `epoch` once a task is published there, `epoch | SLOT_ABANDONED` once its
+// ticket holder gave up; any other value is left over from an earlier launch
+// and means undecided.  The first of publisher and waiter to CAS it wins.
+constexpr uint32_t SLOT_ABANDONED = 0x80000000u;
+
+__device__ __forceinline__ bool claim_slot(uint32_t *st, uint32_t epoch, uint32_t value)
+{
+    uint32_t cur = vload(st);
+    for (int i = 0; i < 64; i++) {
+        if ((cur & ~SLOT_ABANDONED) == epoch) return false;       // decided in this launch
+        const uint32_t prev = atomicCAS(st, cur, value);
+        if (prev == cur) return true;
+        cur = prev;
+    }
+    return false;
 }
 
 // First i in [lo, hi) with key(i) >= t (hi if none) for a key that is
@@ -707,7 +724,9 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
     Sched *sc = p.sched;
     unsigned long long iters = 0;
     uint32_t poll = 0;                       // chunk counter: check for idle warps every 4th
-    unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0;
+    bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
+    unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
+    unsigned long long w_tasks = 0;
     uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0;
 
     // write the staged records of query st_q to its list
@@ -729,43 +748,42 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
 
     for (;;) {
         // ---------------------------------------------------------- take a unit
+        // Seeds first.  Then a ticket of the task queue: the warp waits on
+        // its own slot until a busy warp publishes a task there; when no warp
+        // has been busy for a few polls it abandons the slot (a CAS that the
+        // publisher loses, keeping its work) and leaves.
         uint32_t kind = 0, unit = 0;
         if (lane == 0) {
-            if (p.tasks) {
-                uint32_t h = vload(&sc->q_head.v);
-                const uint32_t t = min(vload(&sc->q_tail.v), p.task_cap);
-                while (h < t) {
-                    const uint32_t prev = atomicCAS(&sc->q_head.v, h, h + 1);
-                    if (prev == h) { kind = 2; unit = h; break; }
-                    h = prev;
+            const uint32_t s0 = seeds_left ? atomicAdd(&sc->next_seed.v, 1u) : nseeds;
+            if (s0 < nseeds) {
+                kind = 1;
+                unit = s0;
+            } else if (p.tasks) {
+                seeds_left = false;
+                const uint32_t t = atomicAdd(&sc->q_head.v, 1u);
+                if (t < p.task_cap) {
+                    uint32_t *st = &p.tasks[t].ready;
+                    atomicAdd(&sc->idle.v, 1u);
+                    uint32_t nap = 64, quiet = 0;
+                    for (uint32_t it = 0; it < IDLE_SPINS; it++) {
+                        if (vload(st) == p.epoch) { kind = 2; unit = t; break; }
+                        if (vload(&sc->busy.v) == 0) { if (++quiet >= 4) break; }
+                        else quiet = 0;
+                        __nanosleep(nap);
+                        nap = min(nap * 2, 2048u);
+                    }
+                    atomicSub(&sc->idle.v, 1u);
+                    if (!kind && !claim_slot(st, p.epoch, p.epoch | SLOT_ABANDONED)) {
+                        kind = 2;                       // published just now
+                        unit = t;
+                    }
                 }
-            }
-            if (!kind) {
-                const uint32_t s = atomicAdd(&sc->next_seed.v, 1u);
-                if (s < nseeds) { kind = 1; unit = s; }
             }
             if (kind) atomicAdd(&sc->busy.v, 1u);
         }
         kind = __shfl_sync(FULL, kind, 0);
         unit = __shfl_sync(FULL, unit, 0);
-        if (!kind) {
-            // idle: wait (bounded) until a task appears or no warp is busy
-            uint32_t more = 0;
-            if (lane == 0 && p.tasks) {
-                atomicAdd(&sc->idle.v, 1u);
-                uint32_t nap = 128;
-                for (uint32_t it = 0; it < IDLE_SPINS; it++) {
-                    __threadfence();
-                    if (vload(&sc->q_head.v) < min(vload(&sc->q_tail.v), p.task_cap)) { more = 1; break; }
-                    if (vload(&sc->busy.v) == 0) break;
-                    __nanosleep(nap);
-                    nap = min(nap * 2, 4096u);
-                }
-                atomicSub(&sc->idle.v, 1u);
-            }
-            if (__shfl_sync(FULL, more, 0)) continue;
-            break;
-        }
+        if (!kind) break;
 
         // ---------------------------------------------------------- set up the unit
         uint32_t q, j, kc = 0, sid = 0, root, f = 0, g = 0, tbeg = 0, tend = 0;
@@ -788,20 +806,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             root = 1;
         } else {
             Task *T = &p.tasks[unit];
-            uint32_t ok = 1;
-            if (lane == 0) {
-                uint32_t it = 0;
-                while (vload(&T->ready) != p.epoch) {
-                    if (++it > READY_SPINS) { ok = 0; atomicOr(p.status, ST_TIMEOUT); break; }
-                    __nanosleep(64);
-                }
-                __threadfence();
-            }
-            ok = __shfl_sync(FULL, ok, 0);
-            if (!ok) {
-                if (lane == 0) atomicSub(&sc->busy.v, 1u);
-                break;
-            }
+            __threadfence();                       // the slot was seen published
+            __syncwarp();
             const uint32_t h = __ldcg(&T->qj_lvl);
             q = h & 0xffffu;
             j = (h >> 16) & 0xffu;
@@ -816,7 +822,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
         const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
         long long t_unit = 0;
-        if (p.seed_work && lane == 0) t_unit = clock64();
+        if (lane == 0) t_unit = clock64();
         const uint32_t rec_bytes = pl->rec_bytes, goff = pl->goff;
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
@@ -958,15 +964,20 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 tgt = __shfl_sync(FULL, Ltgt, s);
                 dsel = __shfl_sync(FULL, Ldsel, s);
             };
-            // hand [mid, e) of depth l to the queue; false if the queue is full
-            auto push = [&](uint32_t l, uint32_t mid, uint32_t e) -> bool {
+            // hand [mid, e) of depth l to the queue, optionally with vertex
+            // fo_lane bound to fo_val and edge go_lane to go_val; false if the
+            // queue is full
+            auto push = [&](uint32_t l, uint32_t mid, uint32_t e, uint32_t fo_lane = 0xffu,
+                            uint32_t fo_val = 0, uint32_t go_lane = 0xffu, uint32_t go_val = 0) -> bool {
                 uint32_t slot = 0;
-                if (lane == 0) slot = atomicAdd(&sc->q_tail.v, 1u);
+                if (lane == 0) slot = atomicAdd(&sc->q_tail.v, 1u);     // slots in ticket order
                 slot = __shfl_sync(FULL, slot, 0);
                 if (slot >= p.task_cap) return false;
                 Task *T = &p.tasks[slot];
-                const uint32_t gg = __shfl_sync(FULL, g, lane & 15);
-                reinterpret_cast<uint32_t *>(T)[8 + lane] = lane < 16 ? f : gg;
+                uint32_t gg = __shfl_sync(FULL, g, lane & 15);
+                if ((uint32_t)(lane & 15) == go_lane) gg = go_val;
+                const uint32_t fl = (uint32_t)lane == fo_lane ? fo_val : f;
+                reinterpret_cast<uint32_t *>(T)[8 + lane] = lane < 16 ? fl : gg;
                 if (lane == 0) {
                     T->qj_lvl = q | (j << 16) | (l << 24);
                     T->beg = mid;
@@ -976,8 +987,11 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 }
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) *reinterpret_cast<volatile uint32_t *>(&T->ready) = p.epoch;
-                return true;
+                uint32_t ok = 0;
+                if (lane == 0) ok = claim_slot(&T->ready, p.epoch, p.epoch) ? 1u : 0u;
+                ok = __shfl_sync(FULL, ok, 0);
+                if (ok) w_tasks++;
+                return ok != 0;                    // false: its waiter left; keep the work
             };
 
             // The last two depths fused: every valid candidate of a chunk at
@@ -1046,7 +1060,24 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                         }
                     }
                 }
-                const uint32_t len = end2 > beg ? end2 - beg : 0u;
+                uint32_t len = end2 > beg ? end2 - beg : 0u;
+                // idle warps: hand them the large last-depth ranges, each as a
+                // task at the last depth carrying its candidate's binding
+                if (p.tasks) {
+                    uint32_t idle = 0;
+                    if (lane == 0) idle = vload(&sc->idle.v);
+                    idle = __shfl_sync(FULL, idle, 0);
+                    uint32_t big = idle ? __ballot_sync(FULL, len >= p.split_min) : 0u;
+                    while (big && idle) {
+                        const uint32_t b = __ffs(big) - 1;
+                        big &= big - 1;
+                        const uint32_t bb = __shfl_sync(FULL, beg, b), be = __shfl_sync(FULL, end2, b);
+                        const uint32_t bn = __shfl_sync(FULL, nb_c, b), br = __shfl_sync(FULL, rel_c, b);
+                        if (!push(last, bb, be, to_p, bn, qe_p, br)) break;
+                        if ((uint32_t)lane == b) len = 0;
+                        idle--;
+                    }
+                }
                 uint32_t inc = len;
 #pragma unroll
                 for (int d = 1; d < 32; d <<= 1) {
@@ -1184,8 +1215,11 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         }
         if (p.count_only && lane == 0 && warp_count)
             atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
-        if (p.seed_work && lane == 0)                // measured SM cycles of this unit
-            atomicAdd(&p.seed_work[sid], (unsigned long long)(clock64() - t_unit));
+        if (lane == 0) {                             // measured SM cycles of this unit
+            const unsigned long long cyc = (unsigned long long)(clock64() - t_unit);
+            w_busy += cyc;
+            if (p.seed_work) atomicAdd(&p.seed_work[sid], cyc);
+        }
         if (lane == 0) {
             __threadfence();
             atomicSub(&sc->busy.v, 1u);
@@ -1200,6 +1234,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         atomicAdd(&p.work[1], w_scanned);
         atomicAdd(&p.work[2], w_binds);
         atomicAdd(&p.work[3], w_records);
+        atomicAdd(&p.work[4], w_busy);
+        atomicAdd(&p.work[5], w_tasks);
     }
 }
 

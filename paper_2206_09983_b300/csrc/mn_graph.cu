@@ -39,7 +39,7 @@ struct Ctrl {
     uint32_t next_seed[3];
     uint32_t pad_;
     long long last_ts;
-    unsigned long long work[4];
+    unsigned long long work[6];
     unsigned long long counts[64 * 3];
 };
 
@@ -284,6 +284,8 @@ void collect_work(mn_graph *g)
     g->stats.entries_scanned += g->h_ctrl->work[1];
     g->stats.binds += g->h_ctrl->work[2];
     g->stats.records += g->h_ctrl->work[3];
+    g->stats.busy_cycles += g->h_ctrl->work[4];
+    g->stats.tasks_split += g->h_ctrl->work[5];
     collect_timing(g);
 }
 
@@ -624,7 +626,9 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.sched = g->d_sched + phase;
     p.tasks = g->d_tasks;
     p.task_cap = g->task_cap;
-    p.epoch = ++g->epoch;
+    g->epoch = (g->epoch + 1) & 0x7fffffffu;              // 31 bits: bit 31 marks abandoned slots
+    if (g->epoch == 0) g->epoch = 1;                       // 0 is the zeroed slots' state
+    p.epoch = g->epoch;
     p.base32 = (uint32_t)base;
     p.base = base;
     p.vis_lo = (uint32_t)(g->lo - base);

@@ -77,7 +77,7 @@ class Stats(C.Structure):
                 ("ms_adjacency", C.c_double), ("ms_seeds", C.c_double),
                 ("ms_enumerate", C.c_double), ("ms_expire", C.c_double),
                 ("seeds", C.c_uint64), ("entries_scanned", C.c_uint64),
-                ("binds", C.c_uint64), ("records", C.c_uint64),
+                ("binds", C.c_uint64), ("records", C.c_uint64), ("busy_cycles", C.c_uint64), ("tasks_split", C.c_uint64),
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
 
     def as_dict(self):
