@@ -568,8 +568,9 @@ __global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_
 struct alignas(16) Task {
     uint32_t qj_lvl;            // query | seed edge << 16 | depth << 24
     uint32_t beg, end;
-    uint32_t ready;             // slot state: epoch published, epoch|SLOT_ABANDONED given up
-    uint32_t pad_[4];
+    uint32_t kc;                // candidate matching order of the seed
+    unsigned long long state;   // slot state (slot_key)
+    uint32_t sid, pad_;         // seed index (work log)
     uint32_t f[MN_MAX_QV];      // data vertex per query vertex
     uint32_t g[MN_MAX_QE];      // seq (relative to the adjacency base) per query edge
 };
@@ -607,7 +608,7 @@ struct EnumParams {
     uint32_t seed_cap;
     Sched *sched;
     Task *tasks;                        // NULL: no splitting
-    uint32_t task_cap, epoch;
+    uint32_t task_cap, task_log2, epoch;   // task ring: slots (a power of two), log2
     uint32_t base32;                    // lowest seq held by the adjacency (low 32 bits)
     unsigned long long base;
     uint32_t vis_lo, vis_hi;            // visible seqs, relative to base
@@ -631,22 +632,28 @@ __device__ __forceinline__ uint32_t vload(const uint32_t *p)
     return *reinterpret_cast<const volatile uint32_t *>(p);
 }
 
-// A task slot's state word holds the epoch of the launch that decided it:
-// `epoch` once a task is published there, `epoch | SLOT_ABANDONED` once its
-// ticket holder gave up; any other value is left over from an earlier launch
-// and means undecided.  The first of publisher and waiter to CAS it wins.
-constexpr uint32_t SLOT_ABANDONED = 0x80000000u;
-
-__device__ __forceinline__ bool claim_slot(uint32_t *st, uint32_t epoch, uint32_t value)
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long *p)
 {
-    uint32_t cur = vload(st);
-    for (int i = 0; i < 64; i++) {
-        if ((cur & ~SLOT_ABANDONED) == epoch) return false;       // decided in this launch
-        const uint32_t prev = atomicCAS(st, cur, value);
-        if (prev == cur) return true;
-        cur = prev;
-    }
-    return false;
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+// The task queue is a ring of task_cap slots.  Ticket (and slot number) t
+// uses slot t mod task_cap in lap t / task_cap.  A slot's 64-bit state only
+// grows: slot_key(epoch, lap) + phase, with phase RESERVED (a publisher is
+// writing the task), PUBLISHED, ABANDONED (the ticket holder left first) or
+// CONSUMED.  States of earlier launches are smaller than any of this launch.
+constexpr uint32_t SLOT_RESERVED = 0, SLOT_PUBLISHED = 1, SLOT_ABANDONED = 2, SLOT_CONSUMED = 3;
+
+__device__ __forceinline__ unsigned long long slot_key(uint32_t epoch, uint32_t lap)
+{
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)lap << 2);
+}
+
+// A slot holds no live task: it was abandoned or consumed, or it was last
+// used by an earlier launch.
+__device__ __forceinline__ bool slot_free(unsigned long long st, uint32_t epoch)
+{
+    return (uint32_t)(st >> 32) != epoch || (st & 3) >= SLOT_ABANDONED;
 }
 
 // First i in [lo, hi) with key(i) >= t (hi if none) for a key that is
@@ -759,25 +766,40 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 kind = 1;
                 unit = s0;
             } else if (p.tasks) {
+                // Ticket holder of slot t in lap L: take the task once it is
+                // published; a later lap found on the slot means the ticket
+                // was skipped (draw again); when no warp is busy for a few
+                // polls, mark a free slot abandoned and leave.
                 seeds_left = false;
-                const uint32_t t = atomicAdd(&sc->q_head.v, 1u);
-                if (t < p.task_cap) {
-                    uint32_t *st = &p.tasks[t].ready;
-                    atomicAdd(&sc->idle.v, 1u);
+                atomicAdd(&sc->idle.v, 1u);
+                for (uint32_t draws = 0; draws < 64 && !kind; draws++) {
+                    const uint32_t t = atomicAdd(&sc->q_head.v, 1u);
+                    unsigned long long *st = &p.tasks[t & (p.task_cap - 1)].state;
+                    const unsigned long long key = slot_key(p.epoch, t >> p.task_log2);
                     uint32_t nap = 64, quiet = 0;
-                    for (uint32_t it = 0; it < IDLE_SPINS; it++) {
-                        if (vload(st) == p.epoch) { kind = 2; unit = t; break; }
-                        if (vload(&sc->busy.v) == 0) { if (++quiet >= 4) break; }
+                    bool leave = false;
+                    for (uint32_t it = 0;; it++) {
+                        const unsigned long long v = vload64(st);
+                        if (v == key + SLOT_PUBLISHED) { kind = 2; unit = t; break; }
+                        if (v >= key + 4) break;        // skipped by a later lap
+                        if (v != key + SLOT_RESERVED && slot_free(v, p.epoch) &&
+                            (it >= IDLE_SPINS || quiet >= 4)) {
+                            if (atomicCAS(st, v, key + SLOT_ABANDONED) == v) { leave = true; break; }
+                            continue;                   // state moved on: look again
+                        }
+                        if (it >= 2 * IDLE_SPINS) {     // a reserved slot never published
+                            atomicOr(p.status, ST_TIMEOUT);
+                            leave = true;
+                            break;
+                        }
+                        if (vload(&sc->busy.v) == 0) quiet++;
                         else quiet = 0;
                         __nanosleep(nap);
                         nap = min(nap * 2, 2048u);
                     }
-                    atomicSub(&sc->idle.v, 1u);
-                    if (!kind && !claim_slot(st, p.epoch, p.epoch | SLOT_ABANDONED)) {
-                        kind = 2;                       // published just now
-                        unit = t;
-                    }
+                    if (leave) break;
                 }
+                atomicSub(&sc->idle.v, 1u);
             }
             if (kind) atomicAdd(&sc->busy.v, 1u);
         }
@@ -805,7 +827,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             if (lane == (int)j) g = seed32 - p.base32;
             root = 1;
         } else {
-            Task *T = &p.tasks[unit];
+            Task *T = &p.tasks[unit & (p.task_cap - 1)];
             __threadfence();                       // the slot was seen published
             __syncwarp();
             const uint32_t h = __ldcg(&T->qj_lvl);
@@ -814,10 +836,15 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             root = h >> 24;
             tbeg = __ldcg(&T->beg);
             tend = __ldcg(&T->end);
-            kc = __ldcg(&T->pad_[0]);
-            sid = __ldcg(&T->pad_[1]);
+            kc = __ldcg(&T->kc);
+            sid = __ldcg(&T->sid);
             f = __ldcg(&T->f[lane & 15]);
             g = __ldcg(&T->g[lane & 15]);
+            __syncwarp();                          // every lane has read the task
+            if (lane == 0) {
+                __threadfence();
+                atomicExch(&T->state, slot_key(p.epoch, unit >> p.task_log2) + SLOT_CONSUMED);
+            }
         }
         const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
         const uint32_t nsteps = pl->nsteps, nv = pl->nv, ne = pl->ne, iso = pl->iso;
@@ -969,11 +996,25 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             // queue is full
             auto push = [&](uint32_t l, uint32_t mid, uint32_t e, uint32_t fo_lane = 0xffu,
                             uint32_t fo_val = 0, uint32_t go_lane = 0xffu, uint32_t go_val = 0) -> bool {
-                uint32_t slot = 0;
-                if (lane == 0) slot = atomicAdd(&sc->q_tail.v, 1u);     // slots in ticket order
+                // Publish into the next slot: reserve it (it must hold no
+                // live task), write, publish.  false: the work stays here.
+                uint32_t ok = 0, slot = 0;
+                if (lane == 0 && (int32_t)(vload(&sc->q_tail.v) - vload(&sc->q_head.v)) <
+                                     (int32_t)(p.task_cap >> 1)) {
+                    slot = atomicAdd(&sc->q_tail.v, 1u);          // slots in ticket order
+                    unsigned long long *st = &p.tasks[slot & (p.task_cap - 1)].state;
+                    const unsigned long long key = slot_key(p.epoch, slot >> p.task_log2);
+                    unsigned long long v = vload64(st);
+                    for (int i = 0; i < 8 && v < key && slot_free(v, p.epoch); i++) {
+                        const unsigned long long prev = atomicCAS(st, v, key + SLOT_RESERVED);
+                        if (prev == v) { ok = 1; break; }
+                        v = prev;
+                    }
+                }
+                ok = __shfl_sync(FULL, ok, 0);
+                if (!ok) return false;
                 slot = __shfl_sync(FULL, slot, 0);
-                if (slot >= p.task_cap) return false;
-                Task *T = &p.tasks[slot];
+                Task *T = &p.tasks[slot & (p.task_cap - 1)];
                 uint32_t gg = __shfl_sync(FULL, g, lane & 15);
                 if ((uint32_t)(lane & 15) == go_lane) gg = go_val;
                 const uint32_t fl = (uint32_t)lane == fo_lane ? fo_val : f;
@@ -982,16 +1023,15 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     T->qj_lvl = q | (j << 16) | (l << 24);
                     T->beg = mid;
                     T->end = e;
-                    T->pad_[0] = kc;
-                    T->pad_[1] = sid;
+                    T->kc = kc;
+                    T->sid = sid;
                 }
                 __threadfence();
                 __syncwarp();
-                uint32_t ok = 0;
-                if (lane == 0) ok = claim_slot(&T->ready, p.epoch, p.epoch) ? 1u : 0u;
-                ok = __shfl_sync(FULL, ok, 0);
-                if (ok) w_tasks++;
-                return ok != 0;                    // false: its waiter left; keep the work
+                if (lane == 0)                     // only the reserver moves a reserved slot on
+                    atomicExch(&T->state, slot_key(p.epoch, slot >> p.task_log2) + SLOT_PUBLISHED);
+                w_tasks++;
+                return true;
             };
 
             // The last two depths fused: every valid candidate of a chunk at

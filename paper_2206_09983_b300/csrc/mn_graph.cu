@@ -626,6 +626,7 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.sched = g->d_sched + phase;
     p.tasks = g->d_tasks;
     p.task_cap = g->task_cap;
+    p.task_log2 = (uint32_t)__builtin_ctz(g->task_cap);
     g->epoch = (g->epoch + 1) & 0x7fffffffu;              // 31 bits: bit 31 marks abandoned slots
     if (g->epoch == 0) g->epoch = 1;                       // 0 is the zeroed slots' state
     p.epoch = g->epoch;
