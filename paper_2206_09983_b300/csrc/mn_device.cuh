@@ -1180,29 +1180,53 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                         if (lvl >= root) restore(lvl);
                         continue;
                     }
-                    // when some warp is idle, hand it half of the shallowest
-                    // depth that still has a large unexplored range
+                    // when some warp is idle, hand it work of the shallowest
+                    // depth that has some left: half of a large unexplored
+                    // range, else the upper half of the candidates still
+                    // pending from the chunk in progress there (entries from
+                    // the first of them on; the receiver tests them again)
                     if (p.tasks && (++poll & 3) == 0) {
                         uint32_t idle = 0;
                         if (lane == 0) idle = vload(&sc->idle.v);
                         idle = __shfl_sync(FULL, idle, 0);
                         if (idle) {
-                            // unexplored range per depth: lanes root..lvl-1 hold
-                            // [Lcur, Lend); this depth keeps its next chunk
-                            uint32_t rb = 0, re = 0;
-                            if ((uint32_t)lane >= root && (uint32_t)lane < lvl) { rb = Lcur; re = Lend; }
-                            if ((uint32_t)lane == lvl) { rb = min(cur + 32, end); re = end; }
-                            const bool can = (uint32_t)lane <= p.split_depth && re > rb &&
-                                             re - rb >= p.split_min;
+                            // lanes root..lvl-1: chunk [Lcur - 32, Lcur) with
+                            // pending bits Lmask, unexplored [Lcur, Lend) (Lend
+                            // below Lcur after a split of pending bits); this
+                            // depth keeps its next chunk
+                            uint32_t rb = 0, re = 0, keep = 0;
+                            if ((uint32_t)lane >= root && (uint32_t)lane < lvl) {
+                                keep = Lmask;
+                                if (Lend > Lcur && Lend - Lcur >= p.split_min) {
+                                    rb = Lcur + (Lend - Lcur) / 2;
+                                    re = Lend;
+                                } else if (Lmask) {
+                                    uint32_t give = Lmask;
+                                    for (uint32_t k = __popc(Lmask) / 2; k; k--) give &= give - 1;
+                                    const uint32_t b = __ffs(give) - 1;
+                                    rb = Lcur - 32 + b;
+                                    re = Lend;
+                                    keep = Lmask & ((1u << b) - 1u);
+                                }
+                            }
+                            if ((uint32_t)lane == lvl && end > cur + 32 && end - (cur + 32) >= p.split_min) {
+                                rb = cur + 32 + (end - cur - 32) / 2;
+                                re = end;
+                            }
+                            const bool can = (uint32_t)lane <= p.split_depth && re > rb;
                             const uint32_t big = __ballot_sync(FULL, can);
                             if (big) {
                                 const uint32_t l = __ffs(big) - 1;
                                 const uint32_t b0 = __shfl_sync(FULL, rb, l);
                                 const uint32_t e0 = __shfl_sync(FULL, re, l);
-                                const uint32_t mid = b0 + (e0 - b0) / 2;
-                                if (push(l, mid, e0)) {
-                                    if (lane == (int)l) Lend = mid;
-                                    if (l == lvl) end = mid;
+                                if (push(l, b0, e0)) {
+                                    // the donor's depth l now ends at b0 (a later
+                                    // split there hands out entries below b0 only)
+                                    if (lane == (int)l) {
+                                        Lend = b0;
+                                        if (l < lvl) Lmask = keep;
+                                    }
+                                    if (l == lvl) end = b0;
                                 }
                             }
                         }
