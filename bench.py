@@ -18,6 +18,7 @@ N > 1 (under torchrun): every rank runs an independent replica of the stream
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -85,6 +86,19 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per k_enumerate
+# launch, the mean of the two launches of the learned arm's first timed batch in
+# one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
+# enumerator source it was taken on: reported as null once that has changed.
+ENUM_TRAFFIC = {"source_sha1": "b8521eee32c34bdc6c1a22bdfcad8729c82201a5", "bytes_per_launch": 476.1e6}
+
+
+def enum_traffic():
+    src = os.path.join(ROOT, "paper_2206_09983_b300", "csrc", "mn_device.cuh")
+    h = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    return ENUM_TRAFFIC["bytes_per_launch"] if h == ENUM_TRAFFIC["source_sha1"] else None
 
 
 def measured_peaks():
@@ -319,6 +333,7 @@ def main():
         clk = ClockSampler(local)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         lat, counts, per_q = [], [], []
+        torch.cuda.profiler.start()                  # ncu --profile-from-start off: timed batches only
         ev0.record(cur_stream)
         for _ in range(K):
             t0 = time.perf_counter()
@@ -328,6 +343,7 @@ def main():
             per_q.append((list(r.count_pos), list(r.count_neg)))
             pos += B
         ev1.record(cur_stream)
+        torch.cuda.profiler.stop()
         torch.cuda.synchronize()
         res["clocks"] = clk.stop()
         barrier()
@@ -392,7 +408,7 @@ def main():
     enum_ms_per = st["ms_enumerate"] / launches
     roof = {"kernel": "k_enumerate", "bound": "hbm",
             "achieved": (enum_bytes / launches) / (enum_ms_per / 1e3) / 1e9 if enum_ms_per else None,
-            "peak": peak, "unit": "GB/s", "traffic": None,
+            "peak": peak, "unit": "GB/s", "traffic": enum_traffic(),
             "peak_source": f"{peak_kind} HBM copy bandwidth",
             "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per}
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
