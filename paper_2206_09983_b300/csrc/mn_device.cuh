@@ -570,7 +570,7 @@ struct alignas(16) Task {
     uint32_t beg, end;
     uint32_t kc;                // candidate matching order of the seed
     unsigned long long state;   // slot state (slot_key)
-    uint32_t sid, pad_;         // seed index (work log)
+    uint32_t sid, set;          // seed index (work log), seed set
     uint32_t f[MN_MAX_QV];      // data vertex per query vertex
     uint32_t g[MN_MAX_QE];      // seq (relative to the adjacency base) per query edge
 };
@@ -623,6 +623,14 @@ struct EnumParams {
     uint32_t *status;
     unsigned long long *work;           // [seeds, entries tested, binds, records, busy cycles, tasks]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
+    // optional second seed set, enumerated in the same launch after the first
+    // (the other phase of the same batch): its seeds, avoid interval, sign and
+    // work log; seeds1 == NULL: one set
+    const unsigned long long *seeds1;
+    const uint32_t *nseeds1;
+    uint32_t seed_cap1;
+    uint32_t av_lo1, av_hi1, sign1;
+    unsigned long long *seed_work1;
     uint32_t split_min;                 // smallest range handed to an idle warp
     uint32_t split_depth;               // deepest search depth that may be split
 };
@@ -727,25 +735,26 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
     if (*p.status) return;
     const int lane = threadIdx.x & 31;
     unsigned char *stage = stage_all[threadIdx.x >> 5];
-    const uint32_t nseeds = min(*p.nseeds, p.seed_cap);
+    const uint32_t nseeds0 = min(*p.nseeds, p.seed_cap);
+    const uint32_t nseeds = nseeds0 + (p.seeds1 ? min(*p.nseeds1, p.seed_cap1) : 0u);
     Sched *sc = p.sched;
     unsigned long long iters = 0;
     uint32_t poll = 0;                       // chunk counter: check for idle warps every 4th
     bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
     unsigned long long w_tasks = 0;
-    uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0;
+    uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0, st_sign = 0;
 
     // write the staged records of query st_q to its list
     auto flush = [&]() {
         if (st_n == 0) return;
         unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(&p.counts[st_q * 3 + p.sign], (unsigned long long)st_n);
+        if (lane == 0) base = atomicAdd(&p.counts[st_q * 3 + st_sign], (unsigned long long)st_n);
         base = __shfl_sync(FULL, base, 0);
-        const unsigned long long cap = p.out_cap[st_q * 2 + p.sign];
+        const unsigned long long cap = p.out_cap[st_q * 2 + st_sign];
         const unsigned long long nw = base >= cap ? 0ull : min((unsigned long long)st_n, cap - base);
         unsigned long long *dst =
-            reinterpret_cast<unsigned long long *>(p.out[st_q * 2 + p.sign] + base * st_rb);
+            reinterpret_cast<unsigned long long *>(p.out[st_q * 2 + st_sign] + base * st_rb);
         const unsigned long long *src = reinterpret_cast<const unsigned long long *>(stage);
         const uint32_t words = (uint32_t)(nw * st_rb / 8);
         for (uint32_t w = lane; w < words; w += 32) dst[w] = src[w];
@@ -808,11 +817,13 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         if (!kind) break;
 
         // ---------------------------------------------------------- set up the unit
-        uint32_t q, j, kc = 0, sid = 0, root, f = 0, g = 0, tbeg = 0, tend = 0;
+        uint32_t q, j, kc = 0, sid = 0, set = 0, root, f = 0, g = 0, tbeg = 0, tend = 0;
         bool skip = false;
         if (kind == 1) {
             w_seeds++;
-            const unsigned long long sd = p.seeds[unit];
+            set = unit >= nseeds0 ? 1u : 0u;
+            if (set) unit -= nseeds0;
+            const unsigned long long sd = (set ? p.seeds1 : p.seeds)[unit];
             const uint32_t seed32 = (uint32_t)(sd >> 32);
             q = (uint32_t)(sd >> 8) & 0xffffu;
             j = (uint32_t)sd & 0xffu;
@@ -838,6 +849,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             tend = __ldcg(&T->end);
             kc = __ldcg(&T->kc);
             sid = __ldcg(&T->sid);
+            set = __ldcg(&T->set);
             f = __ldcg(&T->f[lane & 15]);
             g = __ldcg(&T->g[lane & 15]);
             __syncwarp();                          // every lane has read the task
@@ -854,6 +866,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
         const uint32_t *__restrict__ debi = p.debi[q];
+        const uint32_t sign = set ? p.sign1 : p.sign;       // this unit's output lists
+        const uint32_t av_lo = set ? p.av_lo1 : p.av_lo, av_hi = set ? p.av_hi1 : p.av_hi;
         unsigned long long warp_count = 0;
         const bool direct = rec_bytes * 32 > STAGE_BYTES;
 
@@ -873,14 +887,15 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             unsigned long long gbase = 0;
             bool wr = ok;
             if (direct) {
-                if (lane == 0) gbase = atomicAdd(&p.counts[q * 3 + p.sign], (unsigned long long)cnt);
+                if (lane == 0) gbase = atomicAdd(&p.counts[q * 3 + sign], (unsigned long long)cnt);
                 gbase = __shfl_sync(FULL, gbase, 0) + rank;
-                wr = ok && gbase < p.out_cap[q * 2 + p.sign];
-                rec = p.out[q * 2 + p.sign] + gbase * rec_bytes;
+                wr = ok && gbase < p.out_cap[q * 2 + sign];
+                rec = p.out[q * 2 + sign] + gbase * rec_bytes;
             } else {
-                if (st_q != q || (st_n + cnt) * rec_bytes > STAGE_BYTES) {
+                if (st_q != q || st_sign != sign || (st_n + cnt) * rec_bytes > STAGE_BYTES) {
                     flush();
                     st_q = q;
+                    st_sign = sign;
                     st_rb = rec_bytes;
                 }
                 rec = stage + (st_n + rank) * rec_bytes;
@@ -930,8 +945,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 const uint32_t pe = (pred >> lane) & 1u, se = (succ >> lane) & 1u;
                 tlo = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
                 thi = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
-                tlo = max(tlo, avoid ? p.av_lo : p.vis_lo);
-                thi = min(thi, avoid ? p.av_hi : p.vis_hi);
+                tlo = max(tlo, avoid ? av_lo : p.vis_lo);
+                thi = min(thi, avoid ? av_hi : p.vis_hi);
                 const uint32_t fv = __shfl_sync(FULL, f, from);
                 const uint32_t L = p.L;
                 uint32_t beg;
@@ -1025,6 +1040,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                     T->end = e;
                     T->kc = kc;
                     T->sid = sid;
+                    T->set = set;
                 }
                 __threadfence();
                 __syncwarp();
@@ -1054,8 +1070,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                 const uint32_t pe = ((pred_l & others) >> lane) & 1u, se = ((succ_l & others) >> lane) & 1u;
                 uint32_t tl = __reduce_max_sync(FULL, pe ? g + 1 : 0u);
                 uint32_t th = __reduce_min_sync(FULL, se ? g : 0xffffffffu);
-                tl = max(tl, avoid_l ? p.av_lo : p.vis_lo);
-                th = min(th, avoid_l ? p.av_hi : p.vis_hi);
+                tl = max(tl, avoid_l ? av_lo : p.vis_lo);
+                th = min(th, avoid_l ? av_hi : p.vis_hi);
                 if ((pred_l >> qe_p) & 1u) tl = max(tl, rel_c + 1);
                 if ((succ_l >> qe_p) & 1u) th = min(th, rel_c);
                 const uint32_t f_from = __shfl_sync(FULL, f, from_l), f_to = __shfl_sync(FULL, f, to_l);
@@ -1278,11 +1294,12 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
             }
         }
         if (p.count_only && lane == 0 && warp_count)
-            atomicAdd(&p.counts[q * 3 + p.sign], warp_count);
+            atomicAdd(&p.counts[q * 3 + sign], warp_count);
         if (lane == 0) {                             // measured SM cycles of this unit
             const unsigned long long cyc = (unsigned long long)(clock64() - t_unit);
             w_busy += cyc;
-            if (p.seed_work) atomicAdd(&p.seed_work[sid], cyc);
+            unsigned long long *sw_log = set ? p.seed_work1 : p.seed_work;
+            if (sw_log) atomicAdd(&sw_log[sid], cyc);
         }
         if (lane == 0) {
             __threadfence();

@@ -509,12 +509,12 @@ mn_status ensure_learn_rows(mn_graph *g, uint64_t seeds)
     const uint64_t old = g->learn_rows;
     dfree(g, g->d_X, old * NF * sizeof(__nv_bfloat16));
     dfree(g, g->d_y, old * sizeof(float));
-    dfree(g, g->d_seed_work, old / NCAND * sizeof(unsigned long long));
+    dfree(g, g->d_seed_work, 2 * (old / NCAND) * sizeof(unsigned long long));
     g->d_X = nullptr; g->d_y = nullptr; g->d_seed_work = nullptr; g->learn_rows = 0;
     const uint64_t cap = next_pow2(rows);
     TRY(dalloc(g, &g->d_X, cap * NF, false));
     TRY(dalloc(g, &g->d_y, cap, false));
-    TRY(dalloc(g, &g->d_seed_work, cap / NCAND, false));
+    TRY(dalloc(g, &g->d_seed_work, 2 * (cap / NCAND), false));     // one half per phase
     g->learn_rows = cap;
     return MN_OK;
 }
@@ -541,6 +541,13 @@ FeatParams feat_params(mn_graph *g, int phase, bool all)
     return f;
 }
 
+// Per-seed work log of `phase` under exploration (dS+ and dS- of one batch
+// are enumerated in one launch, so each has its own half).
+unsigned long long *seed_work_of(mn_graph *g, int phase)
+{
+    return g->d_seed_work + (phase == 1 ? g->learn_rows / NCAND : 0);
+}
+
 // Before enumerating `phase`: pick each seed's matching order by policy.
 mn_status choose_orders(mn_graph *g, int phase)
 {
@@ -565,7 +572,7 @@ mn_status choose_orders(mn_graph *g, int phase)
         CKL();
     }
     if (g->policy == MN_ORDER_EXPLORE)
-        CK(cudaMemsetAsync(g->d_seed_work, 0, sizeof(unsigned long long) * cap, g->stream));
+        CK(cudaMemsetAsync(seed_work_of(g, phase), 0, sizeof(unsigned long long) * cap, g->stream));
     return MN_OK;
 }
 
@@ -577,7 +584,7 @@ mn_status log_samples(mn_graph *g, int phase)
     const uint32_t cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
     k_features<<<grid, 256, 0, g->stream>>>(feat_params(g, phase, false));
     CKL();
-    k_log_samples<<<grid, 256, 0, g->stream>>>(g->d_X, g->d_seed_work, &g->d_ctrl->nseeds[phase], cap,
+    k_log_samples<<<grid, 256, 0, g->stream>>>(g->d_X, seed_work_of(g, phase), &g->d_ctrl->nseeds[phase], cap,
                                                 g->d_SX, g->d_ST, g->d_nsamples, g->ring);
     CKL();
     k_advance<<<1, 1, 0, g->stream>>>(g->d_nsamples, &g->d_ctrl->nseeds[phase], cap);
@@ -599,19 +606,27 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
     return MN_OK;
 }
 
-// Enumeration over seeds of `phase` (0 = new, 1 = removed, 2 = static) on
-// adjacency buffer `buf` whose lowest seq is `base`; visible seqs
-// [g->lo, vis_hi); query edges before the seed edge may use seqs
-// [av_lo, av_hi) only (the batch's complement), or, with use_flags, any
-// visible seq whose slot is not flagged.
-mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint64_t vis_hi,
-                           uint64_t av_lo, uint64_t av_hi, bool use_flags, bool count_only)
+// One enumeration phase: seeds of d_seeds[phase] on adjacency buffer `buf`
+// whose lowest seq is `base`; visible seqs [g->lo, vis_hi); query edges before
+// the seed edge may use seqs [av_lo, av_hi) only (the batch's complement), or,
+// with flags, any visible seq whose slot is not flagged.
+struct Phase {
+    int phase, buf;
+    uint64_t base, vis_hi, av_lo, av_hi;
+    bool flags;
+};
+
+// One enumerator launch over the seeds of one or two phases (dS+ and dS- of
+// one batch share the adjacency buffer and visibility; a single launch has
+// one tail instead of two).  The first phase's seeds are taken first.
+mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_only)
 {
+    const Phase &a = ph[0];
     EnumParams p;
     memset(&p, 0, sizeof(p));
     for (int t = 0; t < NPROB; t++) {
-        p.nbr[t] = g->base[buf][t].nbr;
-        p.s32[t] = g->base[buf][t].s32;
+        p.nbr[t] = g->base[a.buf][t].nbr;
+        p.s32[t] = g->base[a.buf][t].s32;
     }
     for (int d = 0; d < 2; d++) p.offs[d] = g->offs[d];
     p.L = g->L;
@@ -620,24 +635,24 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.ring_dst = g->r_dst;
     p.debi = g->d_debi_ptrs;
     p.plans = g->d_plans;
-    p.seeds = g->d_seeds[phase];
-    p.nseeds = &g->d_ctrl->nseeds[phase];
-    p.seed_cap = (uint32_t)std::min<uint64_t>(g->seed_cap[phase], 0xffffffffull);
-    p.sched = g->d_sched + phase;
+    p.seeds = g->d_seeds[a.phase];
+    p.nseeds = &g->d_ctrl->nseeds[a.phase];
+    p.seed_cap = (uint32_t)std::min<uint64_t>(g->seed_cap[a.phase], 0xffffffffull);
+    p.sched = g->d_sched + a.phase;
     p.tasks = g->d_tasks;
     p.task_cap = g->task_cap;
     p.task_log2 = (uint32_t)__builtin_ctz(g->task_cap);
     g->epoch = (g->epoch + 1) & 0x7fffffffu;              // 31 bits: bit 31 marks abandoned slots
     if (g->epoch == 0) g->epoch = 1;                       // 0 is the zeroed slots' state
     p.epoch = g->epoch;
-    p.base32 = (uint32_t)base;
-    p.base = base;
-    p.vis_lo = (uint32_t)(g->lo - base);
-    p.vis_hi = (uint32_t)(vis_hi - base);
-    p.av_lo = (uint32_t)(av_lo - base);
-    p.av_hi = (uint32_t)(av_hi - base);
-    p.batch_flag = use_flags ? g->batch_flag : nullptr;
-    p.sign = (uint32_t)phase;
+    p.base32 = (uint32_t)a.base;
+    p.base = a.base;
+    p.vis_lo = (uint32_t)(g->lo - a.base);
+    p.vis_hi = (uint32_t)(a.vis_hi - a.base);
+    p.av_lo = (uint32_t)(a.av_lo - a.base);
+    p.av_hi = (uint32_t)(a.av_hi - a.base);
+    p.batch_flag = a.flags ? g->batch_flag : nullptr;
+    p.sign = (uint32_t)a.phase;
     p.counts = g->d_ctrl->counts;
     p.out = g->d_out_ptrs;
     p.out_cap = g->d_out_cap;
@@ -645,10 +660,23 @@ mn_status launch_enumerate(mn_graph *g, int phase, int buf, uint64_t base, uint6
     p.max_iters = g->max_iters;
     p.status = &g->d_ctrl->status;
     p.work = g->d_ctrl->work;
-    p.seed_work = g->policy == MN_ORDER_EXPLORE && phase < 2 ? g->d_seed_work : nullptr;
+    const bool explore = g->policy == MN_ORDER_EXPLORE;
+    p.seed_work = explore && a.phase < 2 ? seed_work_of(g, a.phase) : nullptr;
+    if (nph > 1) {
+        const Phase &b = ph[1];
+        if (b.buf != a.buf || b.base != a.base || b.vis_hi != a.vis_hi || b.flags != a.flags)
+            return fail(g, MN_ERR_STATE, "phases of one launch must share the adjacency view");
+        p.seeds1 = g->d_seeds[b.phase];
+        p.nseeds1 = &g->d_ctrl->nseeds[b.phase];
+        p.seed_cap1 = (uint32_t)std::min<uint64_t>(g->seed_cap[b.phase], 0xffffffffull);
+        p.av_lo1 = (uint32_t)(b.av_lo - b.base);
+        p.av_hi1 = (uint32_t)(b.av_hi - b.base);
+        p.sign1 = (uint32_t)b.phase;
+        p.seed_work1 = explore && b.phase < 2 ? seed_work_of(g, b.phase) : nullptr;
+    }
     p.split_min = g->split_min;
     p.split_depth = g->split_depth;
-    CK(cudaMemsetAsync(g->d_sched + phase, 0, sizeof(Sched), g->stream));
+    CK(cudaMemsetAsync(g->d_sched + a.phase, 0, sizeof(Sched), g->stream));
     CK(cudaFuncSetAttribute(k_enumerate, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
     stage_begin(g);
     k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
@@ -818,12 +846,6 @@ void fill_result(mn_graph *g, mn_batch_result *out, uint64_t seq_lo, uint64_t se
 }
 
 // One enumeration phase as launched (kept to re-run it after growing lists).
-struct Phase {
-    int phase, buf;
-    uint64_t base, vis_hi, av_lo, av_hi;
-    bool flags;
-};
-
 // Check the phases' status, re-running any whose lists overflowed after
 // growing them to the exact counts.
 mn_status enumerate_phases(mn_graph *g, const Phase *ph, int nph, bool count_only, bool *over_budget)
@@ -831,15 +853,17 @@ mn_status enumerate_phases(mn_graph *g, const Phase *ph, int nph, bool count_onl
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     if (count_only) return MN_OK;
-    for (int k = 0; k < nph; k++) {
-        bool regrown = false;
-        TRY(grow_outputs(g, ph[k].phase, &regrown, over_budget));
-        if (!regrown) continue;
+    for (int round = 0; round < 2; round++) {
+        bool any = false;
+        for (int k = 0; k < nph; k++) {
+            bool regrown = false;
+            TRY(grow_outputs(g, ph[k].phase, &regrown, over_budget));
+            any = any || regrown;
+        }
+        if (!any) break;
+        // the phases share a launch and the counters: re-run them together
         CK(cudaMemsetAsync(&g->d_ctrl->counts[0], 0, sizeof(g->h_ctrl->counts), g->stream));
-        // counts of the other phase must survive: re-run every phase
-        for (int r = 0; r < nph; r++)
-            TRY(launch_enumerate(g, ph[r].phase, ph[r].buf, ph[r].base, ph[r].vis_hi, ph[r].av_lo,
-                                 ph[r].av_hi, ph[r].flags, false));
+        TRY(launch_enumerate(g, ph, nph, false));
         TRY(read_ctrl(g));
         if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     }
@@ -1128,26 +1152,24 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     // merged at lo; without new edges the current one was merged at merged_lo
     const int nbuf = n ? 1 - g->cur : g->cur;
     const uint64_t nbase = n ? g->lo : g->merged_lo;
+    // dS- first: its seeds (the oldest edges) start the longest searches
     Phase ph[2];
     int nph = 0;
-    if (n && !g->queries.empty()) {
-        // dS+: query edges before the seed edge avoid the batch [hi, hi_new)
-        ph[nph] = Phase{0, nbuf, nbase, hi_new, g->lo, g->hi, false};
-        TRY(launch_seeds_range(g, 0, g->hi, n, 0xffffffffu, 0xffffu));
-        TRY(choose_orders(g, 0));
-        TRY(launch_enumerate(g, 0, nbuf, nbase, hi_new, g->lo, g->hi, false, count_only));
-        TRY(log_samples(g, 0));
-        nph++;
-    }
     if (x && !g->queries.empty()) {
         // dS-: query edges before the seed edge avoid the expiring [lo, lo + x)
-        ph[nph] = Phase{1, nbuf, nbase, hi_new, g->lo + x, hi_new, false};
+        ph[nph++] = Phase{1, nbuf, nbase, hi_new, g->lo + x, hi_new, false};
         TRY(launch_seeds_range(g, 1, g->lo, x, 0xffffffffu, 0xffffu));
-        TRY(choose_orders(g, 1));
-        TRY(launch_enumerate(g, 1, nbuf, nbase, hi_new, g->lo + x, hi_new, false, count_only));
-        TRY(log_samples(g, 1));
-        nph++;
     }
+    if (n && !g->queries.empty()) {
+        // dS+: query edges before the seed edge avoid the batch [hi, hi_new)
+        ph[nph++] = Phase{0, nbuf, nbase, hi_new, g->lo, g->hi, false};
+        TRY(launch_seeds_range(g, 0, g->hi, n, 0xffffffffu, 0xffffu));
+    }
+    if (nph && g->policy != MN_ORDER_PAPER)
+        TRY(ensure_learn_rows(g, std::max(g->seed_cap[0], g->seed_cap[1])));
+    for (int k = 0; k < nph; k++) TRY(choose_orders(g, ph[k].phase));
+    if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
+    for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
     if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
     bool over_budget = false;
     const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
@@ -1235,7 +1257,7 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
                                                                 &g->d_ctrl->nseeds[1],
                                                                 (uint32_t)g->seed_cap[1], &g->d_ctrl->status);
         CKL();
-        TRY(launch_enumerate(g, 1, g->cur, g->merged_lo, g->hi, g->lo, g->hi, true, count_only));
+        TRY(launch_enumerate(g, ph, 1, count_only));
         nph = 1;
     }
     bool over_budget = false;
@@ -1301,7 +1323,8 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
     const uint64_t live = g->hi - g->lo;
     TRY(launch_seeds_range(g, 2, g->lo, live, query_id, 1u));
-    TRY(launch_enumerate(g, 2, g->cur, g->merged_lo, g->hi, g->lo, g->hi, false, true));
+    const Phase ps{2, g->cur, g->merged_lo, g->hi, g->lo, g->hi, false};
+    TRY(launch_enumerate(g, &ps, 1, true));
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     *count = g->h_ctrl->counts[query_id * 3 + 2];
