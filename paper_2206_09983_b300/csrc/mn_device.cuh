@@ -686,16 +686,35 @@ __device__ __forceinline__ uint32_t warp_lower_bound_by(KeyFn key, uint32_t lo, 
     return lo + __popc(__ballot_sync(FULL, less));
 }
 
-// First i in [lo, hi) with key(i) >= t, searched by one lane alone.
-template <class KeyFn>
-__device__ __forceinline__ uint32_t lane_lower_bound(KeyFn key, uint32_t lo, uint32_t hi, uint32_t t)
+// One lane's [r1, r2) = [first i with key(i) >= t1, first i with key(i) >= t2)
+// in [lo, hi) for t1 <= t2 and a non-decreasing key: both binary searches in
+// lock step, so each step has two independent loads in flight; each search
+// also narrows the other (r1 <= r2).  With ENDS, the first and last keys are
+// read first (one round of two loads): an interval entirely before or after
+// the keys, or a bound at an end, needs no search.
+template <bool ENDS, class KeyFn>
+__device__ __forceinline__ void lane_bounds2(KeyFn key, uint32_t lo, uint32_t hi, uint32_t t1,
+                                             uint32_t t2, uint32_t &r1, uint32_t &r2)
 {
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (key(mid) < t) lo = mid + 1;
-        else hi = mid;
+    uint32_t l1 = lo, h1 = hi, l2 = lo, h2 = hi;
+    if (ENDS && lo < hi) {
+        const uint32_t kf = key(lo), kl = key(hi - 1);
+        if (kf >= t1) h1 = lo; else l1 = lo + 1;          // key(lo) decides bound 1 or drops lo
+        if (kf >= t2) h2 = lo; else l2 = lo + 1;
+        if (kl < t1) l1 = hi; else h1 = min(h1, hi - 1);  // key(hi - 1) likewise at the top
+        if (kl < t2) l2 = hi; else h2 = min(h2, hi - 1);
     }
-    return lo;
+    while (l1 < h1 || l2 < h2) {
+        const bool a = l1 < h1, b = l2 < h2;
+        const uint32_t m1 = (l1 + h1) >> 1, m2 = (l2 + h2) >> 1;
+        const uint32_t k1 = a ? key(m1) : 0u, k2 = b ? key(m2) : 0u;
+        if (a) { if (k1 < t1) l1 = m1 + 1; else h1 = m1; }
+        if (b) { if (k2 < t2) l2 = m2 + 1; else h2 = m2; }
+        l2 = max(l2, l1);
+        h1 = min(h1, h2);
+    }
+    r1 = l1;
+    r2 = l2;
 }
 
 // [r1, r2) = [first i with key(i) >= t1, first i with key(i) >= t2) in
@@ -1087,9 +1106,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                         if (label_l >= 0 && beg < end2) {
                             const uint32_t *sq = p.s32[dsl];
                             auto key = [&](uint32_t i) { return sq[i] - b32; };
-                            const uint32_t r1 = lane_lower_bound(key, beg, end2, tl);
-                            end2 = tl < th ? lane_lower_bound(key, r1, end2, th) : r1;
+                            uint32_t r1, r2;
+                            lane_bounds2<true>(key, beg, end2, tl, max(tl, th), r1, r2);
                             beg = r1;
+                            end2 = r2;
                         }
                     } else {
                         const uint32_t *oa = p.offs[dir_l], *ob = p.offs[dir_l ^ 1u];
@@ -1106,13 +1126,14 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
                         if (label_l >= 0 && beg < end2) {
                             const uint32_t *nbv = p.nbr[dsl];
                             auto keyn = [&](uint32_t i) { return nbv[i]; };
-                            const uint32_t lb = lane_lower_bound(keyn, beg, end2, tg);
-                            const uint32_t ub = lane_lower_bound(keyn, lb, end2, tg + 1);
+                            uint32_t lb, ub;
+                            lane_bounds2<false>(keyn, beg, end2, tg, tg + 1, lb, ub);
                             const uint32_t *sq = p.s32[dsl];
                             auto key = [&](uint32_t i) { return sq[i] - b32; };
-                            const uint32_t r1 = lane_lower_bound(key, lb, ub, tl);
-                            end2 = tl < th ? lane_lower_bound(key, r1, ub, th) : r1;
+                            uint32_t r1, r2;
+                            lane_bounds2<false>(key, lb, ub, tl, max(tl, th), r1, r2);
                             beg = r1;
+                            end2 = r2;
                         }
                     }
                 }
