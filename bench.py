@@ -101,6 +101,9 @@ def enum_traffic():
     return ENUM_TRAFFIC["bytes_per_launch"] if h == ENUM_TRAFFIC["source_sha1"] else None
 
 
+ENUM_WARPS_PER_BLOCK = 4           # k_enumerate's block: 128 threads
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -414,7 +417,7 @@ def main():
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
     nq = len(qs)
     tu = learned.get("tuning_used") or {}
-    enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * ENUM_WARPS_PER_BLOCK
                   * max(1, tu.get("blocks_per_sm", 2)))
     adj_bytes_per_batch = 2 * (2 * (W + B) * 12)     # read + write of both directions' entries
     adj = {"kernel": "adjacency update (sort+compact+merge+offsets)",

@@ -216,7 +216,7 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
                           uint64_t n, float *grad, float *loss);
 
 /* Launch parameters of the enumerator (none changes any result): resident
- * blocks of 8 warps per SM in its persistent grid (0 = 2, or the occupancy limit if lower),
+ * blocks of 4 warps per SM in its persistent grid (0 = the occupancy limit, 5 on B300),
  * the smallest candidate range a busy warp hands to an idle one (0 = 40; at
  * least 33), the deepest search depth that may be split (0 = any), and the
  * preferred shared-memory carve-out in percent of the SM's unified L1/shared

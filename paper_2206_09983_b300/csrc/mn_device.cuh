@@ -590,7 +590,11 @@ struct Sched {
     SchedWord busy;             // warps running a seed or a task
 };
 
-constexpr int ENUM_WARPS = 8;              // warps per block
+constexpr int ENUM_WARPS = 4;              // warps per block
+// Resident blocks per SM the enumerator is compiled for (registers capped at
+// 96 per thread): 20 warps per SM hide more of the dependent-load latency than
+// 16 warps at 122 registers (the few spilled bytes stay in L1).
+constexpr int ENUM_MIN_BLOCKS = 5;
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
 constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 4 us per poll)
 constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
@@ -748,7 +752,7 @@ __device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi,
 // injectivity.  When other warps are idle, a warp hands the upper half of a
 // large range to the queue.  Embeddings are staged per warp in shared memory
 // and written out in contiguous blocks.
-__global__ void __launch_bounds__(ENUM_WARPS * 32) k_enumerate(EnumParams p)
+__global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(EnumParams p)
 {
     __shared__ __align__(16) unsigned char stage_all[ENUM_WARPS][STAGE_BYTES];
     if (*p.status) return;

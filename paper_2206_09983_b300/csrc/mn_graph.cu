@@ -981,13 +981,12 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, 256, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, ENUM_WARPS * 32, 0);
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
         g->nsm = nsm;
         g->enum_max_per_sm = std::max(per_sm, 1);
-        // 16 warps per SM: more resident warps measured slower (L1 pressure
-        // and contention on the scheduler words outweigh the extra latency hiding)
-        g->enum_grid = nsm * std::min(g->enum_max_per_sm, 2);
+        // as many resident blocks as fit (the kernel is latency-bound)
+        g->enum_grid = nsm * g->enum_max_per_sm;
     }
     e = cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_OOM); }
@@ -1421,7 +1420,7 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     p.max_iters = g->max_iters;
     p.status = &ctl[0];
     p.work = base + NA_WORK;
-    k_enumerate<<<g->enum_grid, 256, 0, g->stream>>>(p);
+    k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     uint32_t st = 0;
     unsigned long long c = 0;
@@ -1601,8 +1600,7 @@ mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min,
     g->smem_carveout = smem_carveout;
     if (blocks_per_sm > (uint32_t)g->enum_max_per_sm)
         return fail(g, MN_ERR_INVALID_ARG, "blocks_per_sm above the enumerator's occupancy limit");
-    g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm
-                                               : (uint32_t)std::min(g->enum_max_per_sm, 2));
+    g->enum_grid = g->nsm * (int)(blocks_per_sm ? blocks_per_sm : (uint32_t)g->enum_max_per_sm);
     g->split_min = split_min ? std::max<uint32_t>(split_min, 33) : SPLIT_MIN;
     g->split_depth = split_depth ? split_depth : MN_MAX_QE;
     return MN_OK;
@@ -1615,8 +1613,8 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     if (!g->tune_e0) CK(cudaEventCreate(&g->tune_e0));
     if (!g->tune_e1) CK(cudaEventCreate(&g->tune_e1));
     g->tune_cfgs.clear();
-    std::vector<uint32_t> bps = {1u};
-    if (g->enum_max_per_sm > 1) bps.push_back(2u);
+    std::vector<uint32_t> bps = {(uint32_t)g->enum_max_per_sm};
+    if (g->enum_max_per_sm > 1) bps.push_back((uint32_t)g->enum_max_per_sm - 1u);
     for (uint32_t b : bps)
         for (uint32_t sm : {33u, 40u, 64u, 128u})
             for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE}) g->tune_cfgs.push_back({b, sm, sd});
