@@ -762,7 +762,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
     const uint32_t nseeds = nseeds0 + (p.seeds1 ? min(*p.nseeds1, p.seed_cap1) : 0u);
     Sched *sc = p.sched;
     unsigned long long iters = 0;
-    uint32_t poll = 0;                       // chunk counter: check for idle warps every 4th
+    uint32_t poll = 0;                       // chunk counter: check for idle warps every 8th
+    // lane 0: the idle-warp count read at the previous check; each check uses
+    // it and issues the next read, so the read's latency is not waited on
+    uint32_t idle_seen = 0;
     bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
     unsigned long long w_tasks = 0;
@@ -1146,7 +1149,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                 // task at the last depth carrying its candidate's binding
                 if (p.tasks) {
                     uint32_t idle = 0;
-                    if (lane == 0) idle = vload(&sc->idle.v);
+                    if (lane == 0) { idle = idle_seen; idle_seen = vload(&sc->idle.v); }
                     idle = __shfl_sync(FULL, idle, 0);
                     uint32_t big = idle ? __ballot_sync(FULL, len >= p.split_min) : 0u;
                     while (big && idle) {
@@ -1226,9 +1229,9 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                     // range, else the upper half of the candidates still
                     // pending from the chunk in progress there (entries from
                     // the first of them on; the receiver tests them again)
-                    if (p.tasks && (++poll & 3) == 0) {
+                    if (p.tasks && (++poll & 7) == 0) {
                         uint32_t idle = 0;
-                        if (lane == 0) idle = vload(&sc->idle.v);
+                        if (lane == 0) { idle = idle_seen; idle_seen = vload(&sc->idle.v); }
                         idle = __shfl_sync(FULL, idle, 0);
                         if (idle) {
                             // lanes root..lvl-1: chunk [Lcur - 32, Lcur) with
