@@ -766,6 +766,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
     // lane 0: the idle-warp count read at the previous check; each check uses
     // it and issues the next read, so the read's latency is not waited on
     uint32_t idle_seen = 0;
+    uint32_t poll_mask = 7;                  // check every 8th chunk; every 2nd while many warps idle
+    const uint32_t many_idle = gridDim.x * ENUM_WARPS / 4;
     bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
     unsigned long long w_tasks = 0;
@@ -1229,10 +1231,11 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                     // range, else the upper half of the candidates still
                     // pending from the chunk in progress there (entries from
                     // the first of them on; the receiver tests them again)
-                    if (p.tasks && (++poll & 7) == 0) {
+                    if (p.tasks && (++poll & poll_mask) == 0) {
                         uint32_t idle = 0;
                         if (lane == 0) { idle = idle_seen; idle_seen = vload(&sc->idle.v); }
                         idle = __shfl_sync(FULL, idle, 0);
+                        poll_mask = idle > many_idle ? 1u : 7u;
                         if (idle) {
                             // lanes root..lvl-1: chunk [Lcur - 32, Lcur) with
                             // pending bits Lmask, unexplored [Lcur, Lend) (Lend
