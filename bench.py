@@ -89,10 +89,10 @@ class ClockSampler:
 
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per k_enumerate
-# launch, the mean of the two launches of the learned arm's first timed batch in
+# launch, the mean of the learned arm's first two timed launches (one per batch) in
 # one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
 # enumerator source it was taken on: reported as null once that has changed.
-ENUM_TRAFFIC = {"source_sha1": "b8521eee32c34bdc6c1a22bdfcad8729c82201a5", "bytes_per_launch": 476.1e6}
+ENUM_TRAFFIC = {"source_sha1": "9dea82bc57b5f3f2fb97c68cdd5dd1375f2a00e1", "bytes_per_launch": 1085.8e6}
 
 
 def enum_traffic():
