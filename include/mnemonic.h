@@ -73,6 +73,7 @@ typedef int32_t mn_status;
 /* insert/delete flags */
 #define MN_DEVICE_PTR 0x1u     /* the edge (or seq) array is device memory */
 #define MN_COUNT_ONLY 0x2u     /* count embeddings, keep no lists */
+#define MN_ASYNC      0x4u     /* mn_insert_batch only queues the batch; mn_batch_wait completes it */
 
 /* fetch destination flags */
 #define MN_DST_HOST   0x0u
@@ -149,9 +150,26 @@ mn_status mn_register_query(mn_graph *g, const mn_query_desc *q, uint32_t *query
  * edges (host array, or device array with MN_DEVICE_PTR), report dS+ for
  * every query, then, with a window, expire the oldest edges beyond
  * window_edges and report dS- computed before their removal.  n may be 0.
- * `out` may be NULL. */
+ * `out` may be NULL.  With MN_ASYNC the call only queues the batch (see
+ * mn_batch_wait). */
 mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags,
                           mn_batch_result *out);
+
+/* Complete the batch that mn_insert_batch queued with MN_ASYNC (Sec. V-A:
+ * one snapshot's work runs on the GPU while the host prepares the next).
+ * With MN_ASYNC, mn_insert_batch returns once every kernel of the snapshot is
+ * queued on the graph's stream; its `out` gets the batch id, seq ranges and
+ * count arrays whose values are valid only after mn_batch_wait returns.  The
+ * host edge array must stay valid until then.  mn_batch_wait waits for the
+ * enumeration, grows and re-runs result lists that overflowed, commits the
+ * batch (or, on a validation error such as MN_ERR_TS_ORDER, applies nothing)
+ * and fills `out` (may be NULL) as a synchronous insert would; it returns
+ * what that insert would have returned.  While a batch is pending, the calls
+ * that read or change the graph (insert, delete, fetch, register, static
+ * counts, DEBI and adjacency reads, training) return MN_ERR_STATE.  A
+ * batch_id that was already completed gives MN_OK; an unknown one
+ * MN_ERR_INVALID_ARG. */
+mn_status mn_batch_wait(mn_graph *g, uint64_t batch_id, mn_batch_result *out);
 
 /* Explicit deletion of live edges by seq (Alg. 2 batchDeletes): report dS-
  * on the graph before removal, then remove them.  Every seq must be live and

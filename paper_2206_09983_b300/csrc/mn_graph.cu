@@ -69,6 +69,25 @@ uint32_t cdiv(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
 
 }  // namespace
 
+// One enumeration phase: seeds of d_seeds[phase] on adjacency buffer `buf`
+// whose lowest seq is `base`; visible seqs [g->lo, vis_hi); query edges before
+// the seed edge may use seqs [av_lo, av_hi) only (the batch's complement), or,
+// with flags, any visible seq whose slot is not flagged.
+struct Phase {
+    int phase, buf;
+    uint64_t base, vis_hi, av_lo, av_hi;
+    bool flags;
+};
+
+// A batch queued by mn_insert_batch with MN_ASYNC: what its completion needs.
+struct PendingBatch {
+    bool active = false;
+    uint64_t id = 0, n = 0, x = 0, hi_new = 0;
+    bool count_only = false, tune_now = false;
+    int nph = 0;
+    Phase ph[2] = {};
+};
+
 struct mn_graph {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -120,6 +139,7 @@ struct mn_graph {
 
     Ctrl *d_ctrl = nullptr, *h_ctrl = nullptr;
     std::vector<uint64_t> count_pos, count_neg;
+    PendingBatch pending;       // MN_ASYNC batch not yet completed by mn_batch_wait
     unsigned long long max_iters = ~0ull;
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     int nsm = 0, enum_max_per_sm = 0;
@@ -606,16 +626,6 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
     return MN_OK;
 }
 
-// One enumeration phase: seeds of d_seeds[phase] on adjacency buffer `buf`
-// whose lowest seq is `base`; visible seqs [g->lo, vis_hi); query edges before
-// the seed edge may use seqs [av_lo, av_hi) only (the batch's complement), or,
-// with flags, any visible seq whose slot is not flagged.
-struct Phase {
-    int phase, buf;
-    uint64_t base, vis_hi, av_lo, av_hi;
-    bool flags;
-};
-
 // One enumerator launch over the seeds of one or two phases (dS+ and dS- of
 // one batch share the adjacency buffer and visibility; a single launch has
 // one tail instead of two).  The first phase's seeds are taken first.
@@ -872,6 +882,80 @@ mn_status enumerate_phases(mn_graph *g, const Phase *ph, int nph, bool count_onl
 
 }  // namespace
 
+// Complete the queued batch g->pending: wait for its enumeration, grow and
+// re-run overflowed lists, then commit (or, on a validation error, apply
+// nothing) and report.
+static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
+{
+    const PendingBatch pd = g->pending;
+    g->pending.active = false;
+    const uint64_t n = pd.n, x = pd.x, hi_new = pd.hi_new;
+    const bool count_only = pd.count_only, tune_now = pd.tune_now;
+    const int nph = pd.nph;
+    const Phase *ph = pd.ph;
+    bool over_budget = false;
+    const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
+    if (tune_now && est == MN_OK) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
+        g->tune_ms[g->tune_idx] += ms;
+        g->tune_work[g->tune_idx] += (double)(g->h_ctrl->work[1] + g->h_ctrl->work[2]) + 1.0;
+        if (++g->tune_in >= g->tune_per) {
+            g->tune_in = 0;
+            if (++g->tune_idx == g->tune_cfgs.size()) {       // keep the fastest per unit of work
+                size_t best = 0;
+                for (size_t k = 1; k < g->tune_cfgs.size(); k++)
+                    if (g->tune_ms[k] / g->tune_work[k] < g->tune_ms[best] / g->tune_work[best]) best = k;
+                const auto &c = g->tune_cfgs[best];
+                g->enum_grid = g->nsm * (int)c.bps;
+                g->split_min = c.split_min;
+                g->split_depth = c.split_depth;
+                g->tuning = false;
+            }
+        }
+    }
+    if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
+    // commit (also after a timeout: the adjacency update ran; counts are partial)
+    const std::string timeout_msg = g->err;
+    if (g->policy == MN_ORDER_EXPLORE)
+        for (int k = 0; k < nph; k++) g->n_samples += g->h_ctrl->nseeds[ph[k].phase];
+    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+    const uint64_t seq_lo = g->hi;
+    if (n) {
+        g->cur = 1 - g->cur;
+        g->merged_lo = g->lo;
+        g->last_ts = g->h_ctrl->last_ts;
+        g->have_ts = true;
+    }
+    g->hi = hi_new;
+    const uint64_t ex_lo = g->lo;
+    if (x) {
+        stage_begin(g);
+        k_expire<<<cdiv(x, 256), 256, 0, g->stream>>>(g->lo, (uint32_t)x, g->cap_mask, g->L,
+                                                      (uint32_t)g->queries.size(), g->d_debi_ptrs,
+                                                      g->r_src, g->r_dst, g->r_label, g->cnt[0],
+                                                      g->cnt[1], &g->d_ctrl->status);
+        CKL();
+        stage_end(g, S_EXPIRE);
+        g->lo += x;
+    }
+    g->batch_id++;
+    g->stats.batches++;
+    fill_result(g, out, seq_lo, hi_new, ex_lo, ex_lo + x);
+    if (est == MN_ERR_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, timeout_msg);
+    if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
+    return MN_OK;
+}
+
+// Entry points that read or change the graph refuse while a batch queued
+// with MN_ASYNC is pending (its completion still changes the graph).
+static mn_status refuse_if_pending(mn_graph *g)
+{
+    if (g->pending.active)
+        return fail(g, MN_ERR_STATE, "a batch queued with MN_ASYNC is pending: call mn_batch_wait first");
+    return MN_OK;
+}
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -1025,6 +1109,7 @@ const char *mn_last_error(const mn_graph *g)
 mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query_id)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (!d || !query_id || !d->edges) return fail(g, MN_ERR_INVALID_ARG, "NULL argument");
     if (g->queries.size() >= g->max_queries) return fail(g, MN_ERR_STATE, "max_queries reached");
     if (d->nv < 2 || d->nv > MN_MAX_QV || d->ne < 1 || d->ne > MN_MAX_QE)
@@ -1098,6 +1183,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
                           mn_batch_result *out)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (n && !edges) return fail(g, MN_ERR_INVALID_ARG, "edges is NULL");
     if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
     if (!g->W && g->hi + n - g->lo > g->C) return fail(g, MN_ERR_ADMISSION, "edge ring is full");
@@ -1170,64 +1256,52 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
     for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
     if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
-    bool over_budget = false;
-    const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
-    if (tune_now && est == MN_OK) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
-        g->tune_ms[g->tune_idx] += ms;
-        g->tune_work[g->tune_idx] += (double)(g->h_ctrl->work[1] + g->h_ctrl->work[2]) + 1.0;
-        if (++g->tune_in >= g->tune_per) {
-            g->tune_in = 0;
-            if (++g->tune_idx == g->tune_cfgs.size()) {       // keep the fastest per unit of work
-                size_t best = 0;
-                for (size_t k = 1; k < g->tune_cfgs.size(); k++)
-                    if (g->tune_ms[k] / g->tune_work[k] < g->tune_ms[best] / g->tune_work[best]) best = k;
-                const auto &c = g->tune_cfgs[best];
-                g->enum_grid = g->nsm * (int)c.bps;
-                g->split_min = c.split_min;
-                g->split_depth = c.split_depth;
-                g->tuning = false;
-            }
+    PendingBatch &pd = g->pending;
+    pd.active = true;
+    pd.id = g->batch_id + 1;
+    pd.n = n;
+    pd.x = x;
+    pd.hi_new = hi_new;
+    pd.count_only = count_only;
+    pd.tune_now = tune_now;
+    pd.nph = nph;
+    for (int k = 0; k < nph; k++) pd.ph[k] = ph[k];
+    if (flags & MN_ASYNC) {
+        // queued: the result's counts are filled in by mn_batch_wait
+        const size_t nq = g->queries.size();
+        g->count_pos.assign(nq, 0);
+        g->count_neg.assign(nq, 0);
+        if (out) {
+            out->batch_id = pd.id;
+            out->seq_lo = g->hi;
+            out->seq_hi = hi_new;
+            out->expired_lo = g->lo;
+            out->expired_hi = g->lo + x;
+            out->num_queries = (uint32_t)nq;
+            out->count_pos = g->count_pos.data();
+            out->count_neg = g->count_neg.data();
         }
+        return MN_OK;
     }
-    if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
-    // commit (also after a timeout: the adjacency update ran; counts are partial)
-    const std::string timeout_msg = g->err;
-    if (g->policy == MN_ORDER_EXPLORE)
-        for (int k = 0; k < nph; k++) g->n_samples += g->h_ctrl->nseeds[ph[k].phase];
-    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
-    const uint64_t seq_lo = g->hi;
-    if (n) {
-        g->cur = 1 - g->cur;
-        g->merged_lo = g->lo;
-        g->last_ts = g->h_ctrl->last_ts;
-        g->have_ts = true;
+    return insert_finish(g, out);
+}
+
+mn_status mn_batch_wait(mn_graph *g, uint64_t batch_id, mn_batch_result *out)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (g->pending.active && g->pending.id == batch_id) {
+        CK(cudaSetDevice(g->device));
+        return insert_finish(g, out);
     }
-    g->hi = hi_new;
-    const uint64_t ex_lo = g->lo;
-    if (x) {
-        stage_begin(g);
-        k_expire<<<cdiv(x, 256), 256, 0, g->stream>>>(g->lo, (uint32_t)x, g->cap_mask, g->L,
-                                                      (uint32_t)g->queries.size(), g->d_debi_ptrs,
-                                                      g->r_src, g->r_dst, g->r_label, g->cnt[0],
-                                                      g->cnt[1], &g->d_ctrl->status);
-        CKL();
-        stage_end(g, S_EXPIRE);
-        g->lo += x;
-    }
-    g->batch_id++;
-    g->stats.batches++;
-    fill_result(g, out, seq_lo, hi_new, ex_lo, ex_lo + x);
-    if (est == MN_ERR_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, timeout_msg);
-    if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
-    return MN_OK;
+    if (!g->pending.active && batch_id <= g->batch_id) return MN_OK;   // completed already
+    return fail(g, MN_ERR_INVALID_ARG, "no batch with this id is queued");
 }
 
 mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_t flags,
                           mn_batch_result *out)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (n && !seqs) return fail(g, MN_ERR_INVALID_ARG, "seqs is NULL");
     if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
     CK(cudaSetDevice(g->device));
@@ -1281,6 +1355,7 @@ mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id,
                               uint64_t *n_written)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (!n_written) return fail(g, MN_ERR_INVALID_ARG, "n_written is NULL");
     *n_written = 0;
     if (query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "unknown query id");
@@ -1317,6 +1392,7 @@ mn_status mn_record_layout(const mn_graph *g, uint32_t query_id, uint32_t *nv, u
 mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (!count || query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     CK(cudaSetDevice(g->device));
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
@@ -1373,6 +1449,7 @@ extern "C" {
 mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *count)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (!count || query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     const uint64_t live = g->hi - g->lo;
     if (live > MN_NOALLOC_MAX_SEEDS)
@@ -1437,6 +1514,7 @@ mn_status mn_read_debi(mn_graph *g, uint32_t query_id, uint64_t seq_lo, uint64_t
                        uint32_t *words)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (query_id >= g->queries.size() || seq_hi < seq_lo || (seq_hi > seq_lo && !words))
         return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     CK(cudaSetDevice(g->device));
@@ -1453,6 +1531,7 @@ mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *k
                             uint64_t *seq, uint64_t *n)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     if (dir > 1 || !n) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     CK(cudaSetDevice(g->device));
     const uint64_t m = g->hi - g->merged_lo;
@@ -1534,6 +1613,7 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
                                float *loss_last)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
     CK(cudaSetDevice(g->device));
     TRY(ensure_model(g));
     unsigned long long total = 0;

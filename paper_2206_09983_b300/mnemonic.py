@@ -25,6 +25,7 @@ MN_ISO, MN_HOMO = 0, 1
 MN_TEMPORAL = {"none": 0, "chain": 1, "pairs": 2}
 MN_DEVICE_PTR = 0x1
 MN_COUNT_ONLY = 0x2
+MN_ASYNC = 0x4
 MN_DST_DEVICE = 0x1
 MN_MAX_QV = 16
 MN_MAX_QE = 16
@@ -39,7 +40,7 @@ EXPORTS = [
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
-    "mn_last_error",
+    "mn_batch_wait", "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -113,6 +114,7 @@ def load(path: str | None = None):
         "mn_destroy_graph": (None, [P]),
         "mn_register_query": (S, [P, C.POINTER(_QueryDesc), C.POINTER(C.c_uint32)]),
         "mn_insert_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
+        "mn_batch_wait": (S, [P, U64, C.POINTER(_BatchResult)]),
         "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
                                     C.POINTER(U64)]),
@@ -254,6 +256,33 @@ class Graph:
             st = self._lib.mn_insert_batch(self._h, a.ctypes.data if len(a) else None, len(a),
                                            flags, C.byref(r))
         self._check(st)
+        return self._result(r)
+
+    def insert_async(self, edges=None, count_only: bool = False, device_ptr: int | None = None,
+                     n: int | None = None) -> int:
+        """Queue a batch (MN_ASYNC) and return its id; wait(id) completes it.
+        A host array is kept referenced until then."""
+        flags = MN_ASYNC | (MN_COUNT_ONLY if count_only else 0)
+        r = _BatchResult()
+        if device_ptr is not None:
+            st = self._lib.mn_insert_batch(self._h, C.c_void_p(device_ptr), n, flags | MN_DEVICE_PTR,
+                                           C.byref(r))
+            self._async_keep = None
+        else:
+            a = np.ascontiguousarray(edges, dtype=EDGE_DTYPE)
+            st = self._lib.mn_insert_batch(self._h, a.ctypes.data if len(a) else None, len(a),
+                                           flags, C.byref(r))
+            self._async_keep = a
+        self._check(st)
+        return r.batch_id
+
+    def wait(self, batch_id: int) -> BatchResult:
+        """Complete the batch queued by insert_async (mn_batch_wait)."""
+        r = _BatchResult()
+        try:
+            self._check(self._lib.mn_batch_wait(self._h, batch_id, C.byref(r)))
+        finally:
+            self._async_keep = None
         return self._result(r)
 
     def insert_ptr(self, ptr: int, n: int, flags: int = 0) -> BatchResult:
