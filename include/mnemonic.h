@@ -20,7 +20,7 @@
  * of the data vertex's mask (0 = any); query edge label -1 (any) or equal;
  * edge attribute and timestamp inside the query edge's half-open ranges;
  * MN_ISO requires f injective, MN_HOMO does not (Sec. III); temporal
- * constraints require ts(g(a)) < ts(g(b)) for precedence pairs (Sec. VI-D).
+ * constraints require ts(g(a)) < ts(g(b)) for precedence pairs (Sec. VII-C).
  *
  * Result records (one per embedding) are, per query, nv uint32 vertex ids
  * (f(u_0) ... f(u_{nv-1})), zero padding to an 8-byte boundary, then ne
@@ -140,7 +140,7 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out);
 void mn_destroy_graph(mn_graph *g);
 
 /* Register a query (Sec. III, InitializeIndex: root, query tree and one
- * matching order per starting query edge, Sec. V "Matching order
+ * matching order per starting query edge, Sec. VI "Matching order
  * computation"; masks of Table I) and build its DEBI words over the live
  * edges (Sec. IV-A).  No embeddings are reported for edges already live.
  * *query_id receives 0, 1, ... in registration order. */
@@ -196,7 +196,7 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
 /* Matching-order policies (mn_set_order_policy).  Every candidate order is
  * a connected order of the query, so the policy changes the work, never the
  * result.  Candidate 0 is the paper's order (Sec. III preprocessing: most
- * selective root, BFS tree; Sec. V: per-seed order, path to the root first);
+ * selective root, BFS tree; Sec. VI: per-seed order, path to the root first);
  * candidates 1-3 are greedy alternatives (most-connected vertex next,
  * query edge nearest in declaration order next, highest query degree next). */
 #define MN_ORDER_PAPER   0   /* always candidate 0 (default) */
@@ -232,6 +232,17 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
                          float *y);
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
                           uint64_t n, float *grad, float *loss);
+
+/* Seed sharding of one stream over `count` graphs, one per GPU.  The work
+ * units of Sec. VI "Work decomposition" are the seeds, and any partition of
+ * them gives the same union.  This graph enumerates only the seeds (seq,
+ * query, query edge) whose hash modulo count is `index`.  Every shard ingests
+ * the whole stream (a search reaches any part of the window); counts and
+ * lists are then this shard's part: disjoint across shards, summing (and
+ * concatenating) to the unsharded result.  Applies to inserts, deletes and
+ * static counts.  Default: index 0 of 1 (no sharding).  MN_ERR_INVALID_ARG
+ * unless index < count; MN_ERR_STATE while a queued batch is pending. */
+mn_status mn_set_shard(mn_graph *g, uint32_t index, uint32_t count);
 
 /* Launch parameters of the enumerator (none changes any result): resident
  * blocks of 4 warps per SM in its persistent grid (0 = the occupancy limit, 5 on B300),
@@ -309,7 +320,7 @@ mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters);
  * around each stage when timing is enabled (mn_set_timing), else 0.  The
  * enumerator counters are summed on the device: seeds taken, adjacency
  * entries tested, candidates bound (search-tree nodes) and embeddings
- * emitted (Sec. VI-A counts traversed edges per update the same way). */
+ * emitted (Sec. VII-A counts traversed edges per update the same way). */
 typedef struct {
     uint64_t kernel_launches;      /* kernels launched by the library */
     uint64_t batches;              /* insert/delete calls */

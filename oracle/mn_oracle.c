@@ -20,10 +20,10 @@
  *     isomorphism: f injective (Sec. II-B); homomorphism: no injectivity and
  *       one data edge may serve several query edges (Sec. III),
  *     temporal order: ts(g(a)) < ts(g(b)) for every precedence pair (a, b)
- *       encoded in the query (Sec. VI-D, time-constrained isomorphism).
+ *       encoded in the query (Sec. VII-C, time-constrained isomorphism).
  *   The incremental result for a batch B is the set of embeddings of the
  *   graph that use at least one edge of B (Sec. II-B: S(G + dG) = S(G) + dS;
- *   new embeddings for insertions, removed ones for deletions, Sec. VI-A).
+ *   new embeddings for insertions, removed ones for deletions, Sec. VII-A).
  *
  * Three tiers, all plain loops:
  *   or_brute_force   every vertex map f in V^{n_q}, then the cartesian

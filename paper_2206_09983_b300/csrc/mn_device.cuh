@@ -12,10 +12,10 @@
 //   k_merge_csr       merge base and delta into the new sorted adjacency
 //   k_scan_*          offsets of every (vertex, label) segment
 //   k_seeds_*         work units: one per (batch edge, query, query edge)
-//                     whose DEBI bit is set (Sec. V "Work decomposition")
+//                     whose DEBI bit is set (Sec. VI "Work decomposition")
 //   k_enumerate       warp-per-seed backtracking (Sec. III enumerator) with
 //                     the masks of Table I and the per-seed matching orders
-//                     of Sec. V
+//                     of Sec. VI
 //   k_expire          clear DEBI words of expired edges (Sec. IV-A)
 #pragma once
 #include <cstdint>
@@ -63,7 +63,7 @@ struct Step {
 static_assert(sizeof(Step) == 16, "Step is 16 bytes");
 
 // Candidate matching orders compiled per (query, seed edge); 0 is the
-// paper's order (Sec. V), the others are greedy alternatives that a learned
+// paper's order (Sec. VI), the others are greedy alternatives that a learned
 // model may pick per seed.
 constexpr int NCAND = 4;
 
@@ -210,7 +210,7 @@ __global__ void k_ingest(IngestParams p)
 }
 
 // Bulk edgeMatcher over live slots [seq_lo, seq_hi) for one query
-// (query registration and periodic reset, Sec. VI-E).
+// (query registration and periodic reset, Sec. VII-D).
 __global__ void k_match_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask,
                               const uint32_t *r_src, const uint32_t *r_dst, const uint8_t *r_label,
                               const int32_t *r_attr, const int64_t *r_ts, const uint8_t *r_dead,
@@ -485,13 +485,42 @@ __global__ void __launch_bounds__(CBLK) k_scan_apply(const uint32_t *c0, const u
 
 // ------------------------------------------------------------------ seeds
 
-// Work units (Sec. V "Work decomposition"): one seed per (edge, query,
+// Work units (Sec. VI "Work decomposition"): one seed per (edge, query,
 // query edge) with the DEBI bit set, for edges with seq in [seq_lo, seq_lo+n).
 // Packed as (seq32 << 32) | (query << 8) | query edge.
+// Seed sharding: the seeds of one stream split over `count` graphs (one per
+// GPU), each enumerating only the seeds (seq, q, j) it owns; the shards'
+// results are disjoint and their union is the unsharded result (each
+// embedding is reported once, by the seed edge the masks of Table I pick).
+// Owner: the splitmix64 finaliser of the seed's key, modulo count.
+__device__ __forceinline__ uint32_t seed_shard(uint64_t seq, uint32_t q, uint32_t j, uint32_t count)
+{
+    unsigned long long z = (seq << 14) ^ ((unsigned long long)q << 6) ^ j;
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (uint32_t)(z % count);
+}
+
+// The bits of seed word w (seed edges of query q at seq) that shard `idx` of
+// `count` owns.
+__device__ __forceinline__ uint32_t shard_bits(uint32_t w, uint64_t seq, uint32_t q, uint32_t idx,
+                                               uint32_t count)
+{
+    if (count <= 1) return w;
+    uint32_t keep = 0;
+    for (uint32_t m = w; m; m &= m - 1) {
+        const uint32_t j = __ffs(m) - 1;
+        if (seed_shard(seq, q, j, count) == idx) keep |= 1u << j;
+    }
+    return keep;
+}
+
 __global__ void k_seeds_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, uint32_t nq,
                               uint32_t *const *debi, uint32_t qsel, uint32_t jmask,
                               unsigned long long *seeds, uint32_t *nseeds, uint32_t seed_cap,
-                              const uint32_t *status)
+                              uint32_t shard_idx, uint32_t shard_cnt, const uint32_t *status)
 {
     if (*status) return;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -502,7 +531,7 @@ __global__ void k_seeds_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, ui
     uint32_t s32 = 0;
     if (i < n) {
         s32 = (uint32_t)(seq_lo + i);
-        w = debi[q][s32 & cap_mask] & jmask;
+        w = shard_bits(debi[q][s32 & cap_mask] & jmask, seq_lo + i, q, shard_idx, shard_cnt);
     }
     const uint32_t c = __popc(w);
     const int lane = threadIdx.x & 31;
@@ -529,7 +558,8 @@ __global__ void k_seeds_range(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, ui
 // Seeds for an explicit deletion list (seqs given as u64).
 __global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_t cap_mask,
                              uint32_t nq, uint32_t *const *debi, unsigned long long *seeds,
-                             uint32_t *nseeds, uint32_t seed_cap, const uint32_t *status)
+                             uint32_t *nseeds, uint32_t seed_cap, uint32_t shard_idx,
+                             uint32_t shard_cnt, const uint32_t *status)
 {
     if (*status) return;
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -537,7 +567,7 @@ __global__ void k_seeds_list(const unsigned long long *seqs, uint32_t n, uint32_
     uint32_t w = 0, s32 = 0;
     if (i < n) {
         s32 = (uint32_t)seqs[i];
-        w = debi[q][s32 & cap_mask];
+        w = shard_bits(debi[q][s32 & cap_mask], seqs[i], q, shard_idx, shard_cnt);
     }
     const uint32_t c = __popc(w);
     const int lane = threadIdx.x & 31;
@@ -741,7 +771,7 @@ __device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi,
     r2 = t1 < t2 ? warp_lower_bound_by(key, r1, hi, t2, lane) : r1;
 }
 
-// Warp-per-unit backtracking enumerator (Sec. III enumerator, Sec. V work
+// Warp-per-unit backtracking enumerator (Sec. III enumerator, Sec. VI work
 // units, matching orders and masks).  Persistent: warps take split-off
 // subtrees from a global task queue first, then seeds (pull-based
 // distribution of work units).  Lane s holds the state of depth s; the

@@ -140,6 +140,7 @@ struct mn_graph {
     Ctrl *d_ctrl = nullptr, *h_ctrl = nullptr;
     std::vector<uint64_t> count_pos, count_neg;
     PendingBatch pending;       // MN_ASYNC batch not yet completed by mn_batch_wait
+    uint32_t shard_idx = 0, shard_cnt = 1;   // seed sharding of the stream (mn_set_shard)
     unsigned long long max_iters = ~0ull;
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     int nsm = 0, enum_max_per_sm = 0;
@@ -315,7 +316,7 @@ void collect_work(mn_graph *g)
 // vertices whose labels contain the query vertex's labels, per unit of query
 // degree; ties to the smaller id.  Query tree = BFS tree from the root with
 // neighbours in ascending id.  Per starting query edge, the matching order of
-// Sec. V: for a tree edge (u_p, u) the path from u to the root, then the other
+// Sec. VI: for a tree edge (u_p, u) the path from u to the root, then the other
 // tree edges in BFS order; for a non-tree edge (u_x, u_y) the tree edges into
 // u_y and u_x, then the path from u_x to the root, then BFS order.  Query edges
 // whose endpoints are both bound are verified right away (verifyNte).
@@ -712,7 +713,7 @@ mn_status launch_seeds_range(mn_graph *g, int phase, uint64_t s_lo, uint64_t n, 
     k_seeds_range<<<cdiv(threads, 256), 256, 0, g->stream>>>(
         s_lo, (uint32_t)n, g->cap_mask, (uint32_t)g->queries.size(), g->d_debi_ptrs, qsel, jmask,
         g->d_seeds[phase], &g->d_ctrl->nseeds[phase], (uint32_t)g->seed_cap[phase],
-        &g->d_ctrl->status);
+        g->shard_idx, g->shard_cnt, &g->d_ctrl->status);
     CKL();
     stage_end(g, S_SEEDS);
     return MN_OK;
@@ -1328,7 +1329,8 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
         k_seeds_list<<<cdiv(n * nq, 256), 256, 0, g->stream>>>(ds, (uint32_t)n, g->cap_mask, nq,
                                                                 g->d_debi_ptrs, g->d_seeds[1],
                                                                 &g->d_ctrl->nseeds[1],
-                                                                (uint32_t)g->seed_cap[1], &g->d_ctrl->status);
+                                                                (uint32_t)g->seed_cap[1], g->shard_idx,
+                                                                g->shard_cnt, &g->d_ctrl->status);
         CKL();
         TRY(launch_enumerate(g, ph, 1, count_only));
         nph = 1;
@@ -1465,7 +1467,7 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     if (live) {
         k_seeds_range<<<cdiv(live, 256), 256, 0, g->stream>>>(
             g->lo, (uint32_t)live, g->cap_mask, (uint32_t)g->queries.size(), g->d_debi_ptrs,
-            query_id, 1u, seeds, &ctl[1], MN_NOALLOC_MAX_SEEDS, &ctl[0]);
+            query_id, 1u, seeds, &ctl[1], MN_NOALLOC_MAX_SEEDS, g->shard_idx, g->shard_cnt, &ctl[0]);
         CKL();
     }
     EnumParams p;
@@ -1668,6 +1670,16 @@ mn_status mn_order_model_params(mn_graph *g, float *get, const float *set)
         CK(cudaStreamSynchronize(g->stream));
         g->packed = false;
     }
+    return MN_OK;
+}
+
+mn_status mn_set_shard(mn_graph *g, uint32_t index, uint32_t count)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (count == 0 || index >= count) return fail(g, MN_ERR_INVALID_ARG, "need index < count");
+    g->shard_idx = index;
+    g->shard_cnt = count;
     return MN_OK;
 }
 

@@ -1,7 +1,7 @@
 """Seeded synthetic edge streams and query graphs.
 
 This module only produces inputs: edge streams shaped like the workloads of
-the Mnemonic evaluation (Sec. VI: power-law flow graphs, insert-only and
+the Mnemonic evaluation (Sec. VII: power-law flow graphs, insert-only and
 sliding-window streams, labelled tree and cyclic queries) and the query graphs
 matched against them.  It holds none of the matching arithmetic, so both the
 CPU oracle and the CUDA path can draw their inputs from it.
@@ -121,7 +121,7 @@ def rmat_stream(scale: int, num_edges: int, a: float, b: float, c: float,
 def flow_stream(num_hosts: int, num_edges: int, num_elabels: int, seed: int,
                 server_frac: float = 0.1, zipf_s: float = 1.1,
                 mean_repeat: float = 8.0) -> dict:
-    """Bipartite-heavy network-flow multigraph (NetFlow-like, Sec. VI).
+    """Bipartite-heavy network-flow multigraph (NetFlow-like, Sec. VII).
 
     Clients (90%) send flows mostly to servers; source activity and server
     popularity are Zipf-distributed; each (src, dst) pair repeats a geometric

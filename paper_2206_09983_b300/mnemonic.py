@@ -40,7 +40,7 @@ EXPORTS = [
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
-    "mn_batch_wait", "mn_last_error",
+    "mn_batch_wait", "mn_set_shard", "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -115,6 +115,7 @@ def load(path: str | None = None):
         "mn_register_query": (S, [P, C.POINTER(_QueryDesc), C.POINTER(C.c_uint32)]),
         "mn_insert_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_batch_wait": (S, [P, U64, C.POINTER(_BatchResult)]),
+        "mn_set_shard": (S, [P, C.c_uint32, C.c_uint32]),
         "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
                                     C.POINTER(U64)]),
@@ -257,6 +258,10 @@ class Graph:
                                            flags, C.byref(r))
         self._check(st)
         return self._result(r)
+
+    def set_shard(self, index: int, count: int):
+        """Enumerate only this shard's seeds of the stream (mn_set_shard)."""
+        self._check(self._lib.mn_set_shard(self._h, index, count))
 
     def insert_async(self, edges=None, count_only: bool = False, device_ptr: int | None = None,
                      n: int | None = None) -> int:

@@ -1,6 +1,6 @@
 """Named synthetic workloads (stream recipes and query sets).
 
-The paper's datasets (NetFlow, LSBench, LANL; Sec. VI) are not available; these
+The paper's datasets (NetFlow, LSBench, LANL; Sec. VII) are not available; these
 seeded streams stand in for their shapes.  Only inputs are defined here.
 
 rmat20_window: R-MAT power-law multigraph (a, b, c) = (0.57, 0.19, 0.19),
