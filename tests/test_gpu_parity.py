@@ -104,6 +104,24 @@ def test_random_queries_multi_query_launch():
     run_stream_parity(s, qs, batch=750, window=2000, preload=2000, only={0, 1})
 
 
+def test_thirty_two_uneven_queries_one_launch():
+    """32 concurrent queries of 3..8 vertices (random labelled trees and
+    cycles with 1-2 chords, isomorphism, temporal chain) on an R-MAT
+    multigraph (scale 10, 12,000 edges, 8 Zipf edge labels): every query's
+    seeds of both phases go through one enumerator launch per batch."""
+    s = gen.rmat_stream(10, 12000, 0.57, 0.19, 0.19, 8, 1.2, 4, 1000, seed=0x4D4E0003)
+    rng = np.random.default_rng(0x4D4E0003)
+    qs = []
+    for i in range(32):
+        nv = int(rng.integers(3, 9))
+        kind = "tree" if i % 2 == 0 else "cycle"
+        q = gen.random_query(rng, nv, kind, 8, 4, chords=int(rng.integers(1, 3)) if nv >= 4 else 0,
+                             iso=True, temporal="chain")
+        q["vmask"] = [m if rng.random() < 0.5 else 0 for m in q["vmask"]]
+        qs.append(q)
+    run_stream_parity(s, qs, batch=3000, window=6000, preload=6000, only={0, 1})
+
+
 def test_output_lists_regrow_exactly():
     """A tiny initial list capacity: lists are regrown and re-enumerated."""
     s = gen.uniform_stream(300, 5000, 2, 2, seed=5)
