@@ -94,7 +94,7 @@ class ClockSampler:
 # launch, the mean of the learned arm's first two timed launches (one per batch) in
 # one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
 # enumerator source it was taken on: reported as null once that has changed.
-ENUM_TRAFFIC = {"source_sha1": "9dea82bc57b5f3f2fb97c68cdd5dd1375f2a00e1", "bytes_per_launch": 1085.8e6}
+ENUM_TRAFFIC = {"source_sha1": "9f332c4157abe6ec25c48472652c38728e320125", "bytes_per_launch": 1079.2e6}
 
 
 def enum_traffic():
