@@ -12,10 +12,11 @@
 //   k_merge_csr       merge base and delta into the new sorted adjacency
 //   k_scan_*          offsets of every (vertex, label) segment
 //   k_seeds_*         work units: one per (batch edge, query, query edge)
-//                     whose DEBI bit is set (Sec. VI "Work decomposition")
+//                     whose DEBI bit is set (Sec. VI "Work decomposition"),
+//                     optionally only this graph's shard of them
 //   k_enumerate       warp-per-seed backtracking (Sec. III enumerator) with
 //                     the masks of Table I and the per-seed matching orders
-//                     of Sec. VI
+//                     of Sec. VI; one launch per batch for dS- and dS+
 //   k_expire          clear DEBI words of expired edges (Sec. IV-A)
 #pragma once
 #include <cstdint>
@@ -626,7 +627,7 @@ constexpr int ENUM_WARPS = 4;              // warps per block
 // 16 warps at 122 registers (the few spilled bytes stay in L1).
 constexpr int ENUM_MIN_BLOCKS = 5;
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
-constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 4 us per poll)
+constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 2 us per poll)
 constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
 
 struct EnumParams {
@@ -772,16 +773,19 @@ __device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi,
 }
 
 // Warp-per-unit backtracking enumerator (Sec. III enumerator, Sec. VI work
-// units, matching orders and masks).  Persistent: warps take split-off
-// subtrees from a global task queue first, then seeds (pull-based
-// distribution of work units).  Lane s holds the state of depth s; the
-// candidates of a depth are tested 32 at a time, one per lane.  A depth's
+// units, matching orders and masks).  Persistent: warps take seeds from a
+// cursor (one or two seed sets: dS- then dS+ of a batch), then split-off
+// subtrees from the task ring (pull-based distribution of work units).  Lane
+// s holds the state of depth s; the candidates of a depth are tested 32 at a
+// time, one per lane, and the last two depths are fused (each candidate of
+// depth last-1 computes its last-depth range in its own lane).  A depth's
 // candidate range is the (vertex, label) slice of the adjacency narrowed by
 // binary search to the seqs allowed by the temporal bounds, the window and
 // the batch mask; what remains is tested against the DEBI bit and
-// injectivity.  When other warps are idle, a warp hands the upper half of a
-// large range to the queue.  Embeddings are staged per warp in shared memory
-// and written out in contiguous blocks.
+// injectivity.  When other warps are idle, a warp hands them work: half of a
+// large range, the pending candidates of a chunk, or whole last-depth
+// ranges.  Embeddings are staged per warp in shared memory and written out in
+// contiguous blocks.
 __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(EnumParams p)
 {
     __shared__ __align__(16) unsigned char stage_all[ENUM_WARPS][STAGE_BYTES];
