@@ -203,9 +203,13 @@ def run_serve(args, local):
         g.insert(packed[lo:lo + B], count_only=True)
     for q in qs:
         g.register_query(q)
+    g.set_order_policy("explore" if args.serve_order == "learned" else "paper")
     for k in range(3):                                          # warm-up
         g.insert(packed[W + k * B: W + (k + 1) * B])
     pos = W + 3 * B
+    if args.serve_order == "learned":                           # train the order model first
+        g.train_order_model(epochs=args.train_epochs, lr=2e-3)
+        g.set_order_policy("learned")
     rate = args.serve_rate
     rng = np.random.default_rng(0x5E4E)
     sched = poisson_batches(rng, args.serve_edges, 1024, B, rate)
@@ -236,7 +240,8 @@ def run_serve(args, local):
         "errors": sum(1 for r in reqs if r.error),
         "config": {"workload": w["name"], "window": W, "max_batch": B,
                    "arrivals": "Poisson, batch sizes log-uniform in [1024, 65536]",
-                   "path": "plain GPU path, continuous batching (queued requests merged)"},
+                   "path": (("learned matching order" if args.serve_order == "learned" else
+                             "paper's matching order") + ", continuous batching (queued requests merged)")},
     }
 
 
@@ -258,6 +263,7 @@ def main():
     ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
     ap.add_argument("--serve-rate", type=float, default=4.0e5, help="offered load, edges/s")
     ap.add_argument("--serve-edges", type=int, default=6_000_000)
+    ap.add_argument("--serve-order", default="learned", choices=["learned", "paper"])
     args = ap.parse_args()
     rank, world, local = env_rank()
 
