@@ -233,6 +233,17 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
                           uint64_t n, float *grad, float *loss);
 
+/* Time-window snapshots instead of a count window (Sec. VII-D: the LANL
+ * stream runs with a 24-hour window): after each insert batch whose newest
+ * timestamp is T, the live edges with ts <= T - window expire, with their dS-
+ * reported as for a count window (computed before their removal; they can
+ * include edges of the batch itself).  Only for graphs created without a
+ * count window (window_edges = 0); edge_capacity must hold the live window
+ * plus a batch, else the insert returns MN_ERR_ADMISSION.  window = 0 turns
+ * it off.  Each insert then reads the cut back from the device once (one
+ * extra host synchronisation). */
+mn_status mn_set_time_window(mn_graph *g, int64_t window);
+
 /* Seed sharding of one stream over `count` graphs, one per GPU.  The work
  * units of Sec. VI "Work decomposition" are the seeds, and any partition of
  * them gives the same union.  This graph enumerates only the seeds (seq,

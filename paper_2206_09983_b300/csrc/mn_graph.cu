@@ -13,6 +13,7 @@
 // Every batch runs as one chain of kernels on the graph's stream with a
 // single host synchronisation at the end (to return the counts).
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -41,6 +42,7 @@ struct Ctrl {
     long long last_ts;
     unsigned long long work[6];
     unsigned long long counts[64 * 3];
+    unsigned long long time_cut;        // edges a time window expires after this batch
 };
 
 enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_COUNT };
@@ -141,6 +143,7 @@ struct mn_graph {
     std::vector<uint64_t> count_pos, count_neg;
     PendingBatch pending;       // MN_ASYNC batch not yet completed by mn_batch_wait
     uint32_t shard_idx = 0, shard_cnt = 1;   // seed sharding of the stream (mn_set_shard)
+    int64_t time_window = 0;    // > 0: expire by timestamp (mn_set_time_window)
     unsigned long long max_iters = ~0ull;
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     int nsm = 0, enum_max_per_sm = 0;
@@ -948,6 +951,31 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     return MN_OK;
 }
 
+namespace mn {
+
+// Time-window snapshots (the paper's LANL runs use a 24-hour window, Sec.
+// VII-D): how many of the seqs [lo, hi) have a timestamp at most
+// newest - window.  They are a prefix (timestamps increase with seq), found by
+// one thread's binary search over the ring.  Nothing when the batch failed
+// validation.
+__global__ void k_time_cut(uint64_t lo, uint64_t hi, uint32_t cap_mask, const int64_t *r_ts,
+                           const long long *newest, long long window, unsigned long long *x_out,
+                           const uint32_t *status)
+{
+    if (*status) { *x_out = 0; return; }
+    const long long t = *newest;
+    const long long cut = t < LLONG_MIN + window ? LLONG_MIN : t - window;
+    uint64_t a = lo, b = hi;                 // first seq with ts > cut
+    while (a < b) {
+        const uint64_t mid = a + (b - a) / 2;
+        if (r_ts[mid & cap_mask] <= cut) a = mid + 1;
+        else b = mid;
+    }
+    *x_out = a - lo;
+}
+
+}  // namespace mn
+
 // Entry points that read or change the graph refuse while a batch queued
 // with MN_ASYNC is pending (its completion still changes the graph).
 static mn_status refuse_if_pending(mn_graph *g)
@@ -1191,7 +1219,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     CK(cudaSetDevice(g->device));
     const bool count_only = (flags & MN_COUNT_ONLY) != 0;
     const uint64_t hi_new = g->hi + n;
-    const uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
+    uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
     if (n) {
         const mn_edge *src = edges;
@@ -1224,6 +1252,18 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         stage_begin(g);
         TRY(launch_adjacency_update(g, n, src, g->hi));
         stage_end(g, S_ADJ);
+        if (g->time_window > 0) {
+            // time window: the oldest edges up to newest - window expire now
+            k_time_cut<<<1, 1, 0, g->stream>>>(g->lo, hi_new, g->cap_mask, g->r_ts, &g->d_ctrl->last_ts,
+                                              (long long)g->time_window, &g->d_ctrl->time_cut,
+                                              &g->d_ctrl->status);
+            CKL();
+            CK(cudaMemcpyAsync(&g->h_ctrl->time_cut, &g->d_ctrl->time_cut, sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            g->stats.d2h_bytes += sizeof(unsigned long long);
+            x = g->h_ctrl->time_cut;
+        }
     }
     // autotuning: run this batch's enumeration under the next candidate
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
@@ -1680,6 +1720,16 @@ mn_status mn_set_shard(mn_graph *g, uint32_t index, uint32_t count)
     if (count == 0 || index >= count) return fail(g, MN_ERR_INVALID_ARG, "need index < count");
     g->shard_idx = index;
     g->shard_cnt = count;
+    return MN_OK;
+}
+
+mn_status mn_set_time_window(mn_graph *g, int64_t window)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (window < 0) return fail(g, MN_ERR_INVALID_ARG, "window must be >= 0");
+    if (window && g->W) return fail(g, MN_ERR_INVALID_ARG, "this graph already has a count window");
+    g->time_window = window;
     return MN_OK;
 }
 

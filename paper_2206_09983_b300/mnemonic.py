@@ -40,7 +40,7 @@ EXPORTS = [
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
-    "mn_batch_wait", "mn_set_shard", "mn_last_error",
+    "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -116,6 +116,7 @@ def load(path: str | None = None):
         "mn_insert_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_batch_wait": (S, [P, U64, C.POINTER(_BatchResult)]),
         "mn_set_shard": (S, [P, C.c_uint32, C.c_uint32]),
+        "mn_set_time_window": (S, [P, C.c_int64]),
         "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
                                     C.POINTER(U64)]),
@@ -258,6 +259,10 @@ class Graph:
                                            flags, C.byref(r))
         self._check(st)
         return self._result(r)
+
+    def set_time_window(self, window: int):
+        """Expire by timestamp: keep edges newer than newest - window."""
+        self._check(self._lib.mn_set_time_window(self._h, window))
 
     def set_shard(self, index: int, count: int):
         """Enumerate only this shard's seeds of the stream (mn_set_shard)."""
