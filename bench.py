@@ -447,6 +447,14 @@ def main():
             "peak_source": f"{peak_kind} HBM copy bandwidth",
             "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per}
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
+    # sector-granular variant: every random touch rounded up to a 32-byte
+    # sector (an upper estimate: each tested entry's DEBI word as one touch,
+    # each seed's ring endpoints as two)
+    sector_bytes = (st["entries_scanned"] * (8 + 32) + st["records"] * (sum(rec_bytes) / len(rec_bytes))
+                    + st["seeds"] * (8 + 64))
+    roof["sector_bytes_per_launch"] = sector_bytes / launches
+    roof["sector_achieved"] = ((sector_bytes / launches) / (enum_ms_per / 1e3) / 1e9
+                               if enum_ms_per else None)
     nq = len(qs)
     tu = learned.get("tuning_used") or {}
     enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * ENUM_WARPS_PER_BLOCK
