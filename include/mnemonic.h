@@ -233,6 +233,20 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
                           uint64_t n, float *grad, float *loss);
 
+/* Device memory the graph holds now (*used), the most it has held (*peak)
+ * and its budget (mem_budget_bytes, 0 = none), in bytes (Sec. VII-D measures
+ * the index's memory over a stream).  Any pointer may be NULL. */
+mn_status mn_memory_info(const mn_graph *g, uint64_t *used, uint64_t *peak, uint64_t *budget);
+
+/* Periodic reset (Sec. VII-D: the cumulative index can be discarded at any
+ * snapshot and rebuilt from it): every registered query's DEBI words are
+ * cleared and recomputed by the edgeMatcher over the live window.  The words
+ * here are a function of each edge alone, so the rebuilt index equals the old
+ * one and later results are unchanged; the call restores that state after
+ * anything that disturbed it.  MN_ERR_STATE while a queued batch is
+ * pending. */
+mn_status mn_reset_index(mn_graph *g);
+
 /* Time-window snapshots instead of a count window (Sec. VII-D: the LANL
  * stream runs with a 24-hour window): after each insert batch whose newest
  * timestamp is T, the live edges with ts <= T - window expire, with their dS-

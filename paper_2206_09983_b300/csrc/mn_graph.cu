@@ -97,7 +97,7 @@ struct mn_graph {
     uint32_t V = 0, L = 0;
     uint64_t W = 0, max_batch = 0, C = 0;
     uint32_t cap_mask = 0;
-    uint64_t mem_budget = 0, mem_used = 0;
+    uint64_t mem_budget = 0, mem_used = 0, mem_peak = 0;
     uint32_t max_queries = 0;
     uint64_t default_out_cap = 0;
     std::vector<uint32_t> vmask_host;
@@ -222,6 +222,7 @@ mn_status dalloc(mn_graph *g, T **p, uint64_t count, bool zero = true)
         if (e != cudaSuccess) return fail(g, MN_ERR_DEVICE, cudaGetErrorString(e));
     }
     g->mem_used += bytes;
+    g->mem_peak = std::max(g->mem_peak, g->mem_used);
     g->allocs.push_back(q);
     *p = reinterpret_cast<T *>(q);
     return MN_OK;
@@ -1730,6 +1731,35 @@ mn_status mn_set_time_window(mn_graph *g, int64_t window)
     if (window < 0) return fail(g, MN_ERR_INVALID_ARG, "window must be >= 0");
     if (window && g->W) return fail(g, MN_ERR_INVALID_ARG, "this graph already has a count window");
     g->time_window = window;
+    return MN_OK;
+}
+
+mn_status mn_memory_info(const mn_graph *g, uint64_t *used, uint64_t *peak, uint64_t *budget)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (used) *used = g->mem_used;
+    if (peak) *peak = g->mem_peak;
+    if (budget) *budget = g->mem_budget;
+    return MN_OK;
+}
+
+mn_status mn_reset_index(mn_graph *g)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    CK(cudaSetDevice(g->device));
+    const uint64_t live = g->hi - g->lo;
+    for (size_t q = 0; q < g->queries.size(); q++) {
+        const QueryHost &Q = g->queries[q];
+        CK(cudaMemsetAsync(Q.debi, 0, g->C * sizeof(uint32_t), g->stream));
+        if (live) {
+            k_match_range<<<cdiv(live, 256), 256, 0, g->stream>>>(
+                g->lo, (uint32_t)live, g->cap_mask, g->r_src, g->r_dst, g->r_label, g->r_attr, g->r_ts,
+                g->r_dead, g->d_vmask, g->d_queries + q, Q.debi);
+            CKL();
+        }
+    }
+    CK(cudaStreamSynchronize(g->stream));
     return MN_OK;
 }
 

@@ -40,7 +40,8 @@ EXPORTS = [
     "mn_set_timing", "mn_get_stats", "mn_reset_stats", "mn_count_static_noalloc",
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
-    "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_last_error",
+    "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
+    "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -117,6 +118,8 @@ def load(path: str | None = None):
         "mn_batch_wait": (S, [P, U64, C.POINTER(_BatchResult)]),
         "mn_set_shard": (S, [P, C.c_uint32, C.c_uint32]),
         "mn_set_time_window": (S, [P, C.c_int64]),
+        "mn_memory_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64)]),
+        "mn_reset_index": (S, [P]),
         "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
                                     C.POINTER(U64)]),
@@ -259,6 +262,16 @@ class Graph:
                                            flags, C.byref(r))
         self._check(st)
         return self._result(r)
+
+    def memory_info(self) -> dict:
+        """Device bytes held now, the peak, and the budget (0 = none)."""
+        u, p, b = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        self._check(self._lib.mn_memory_info(self._h, C.byref(u), C.byref(p), C.byref(b)))
+        return {"used": u.value, "peak": p.value, "budget": b.value}
+
+    def reset_index(self):
+        """Clear and rebuild every query's DEBI words over the live window."""
+        self._check(self._lib.mn_reset_index(self._h))
 
     def set_time_window(self, window: int):
         """Expire by timestamp: keep edges newer than newest - window."""
