@@ -233,6 +233,21 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
                           uint64_t n, float *grad, float *loss);
 
+/* Dual simulation of a registered query over the live window (Sec. III
+ * names it among the matching variants the index serves; Sec. VII-C runs it
+ * per snapshot): the largest relation S between query vertices u and data
+ * vertices v such that v carries u's vertex labels and, for every query edge
+ * e leaving (entering) u, some live data edge leaving (entering) v matches e
+ * (the edgeMatcher, i.e. its DEBI bit e) and leads to (comes from) a data
+ * vertex related to e's other endpoint.  If some query vertex is related to
+ * no data vertex the query does not match and S is empty.  Temporal
+ * precedence is ignored (it constrains edge instances, not vertices).
+ * sim (host, or device with MN_DST_DEVICE; may be NULL) receives
+ * num_vertices words, bit u of word v set iff (u, v) is in S; *pairs (may be
+ * NULL) gets |S|.  The relation is recomputed from the index on every call. */
+mn_status mn_dual_simulation(mn_graph *g, uint32_t query_id, uint32_t *sim, uint32_t dst_flags,
+                             uint64_t *pairs);
+
 /* Device memory the graph holds now (*used), the most it has held (*peak)
  * and its budget (mem_budget_bytes, 0 = none), in bytes (Sec. VII-D measures
  * the index's memory over a stream).  Any pointer may be NULL. */

@@ -23,6 +23,7 @@
 
 #include "mn_device.cuh"
 #include "mn_learned.cuh"
+#include "mn_dualsim.cuh"
 
 using namespace mn;
 
@@ -144,6 +145,8 @@ struct mn_graph {
     PendingBatch pending;       // MN_ASYNC batch not yet completed by mn_batch_wait
     uint32_t shard_idx = 0, shard_cnt = 1;   // seed sharding of the stream (mn_set_shard)
     int64_t time_window = 0;    // > 0: expire by timestamp (mn_set_time_window)
+    uint32_t *d_sim = nullptr;  // dual simulation: [V] words
+    unsigned long long *d_simctl = nullptr;   // its two flag words, then the pair count
     unsigned long long max_iters = ~0ull;
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     int nsm = 0, enum_max_per_sm = 0;
@@ -1760,6 +1763,79 @@ mn_status mn_reset_index(mn_graph *g)
         }
     }
     CK(cudaStreamSynchronize(g->stream));
+    return MN_OK;
+}
+
+mn_status mn_dual_simulation(mn_graph *g, uint32_t query_id, uint32_t *sim, uint32_t dst_flags,
+                             uint64_t *pairs)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "no such query");
+    CK(cudaSetDevice(g->device));
+    if (!g->d_sim) TRY(dalloc(g, &g->d_sim, (uint64_t)g->V, false));
+    if (!g->d_simctl) TRY(dalloc(g, &g->d_simctl, 2));
+    const QueryHost &Q = g->queries[query_id];
+    DualSimParams p;
+    memset(&p, 0, sizeof(p));
+    p.nv = Q.nv;
+    p.ne = Q.ne;
+    p.V = g->V;
+    p.L = g->L;
+    p.cap_mask = g->cap_mask;
+    p.base32 = (uint32_t)g->merged_lo;
+    p.vis_lo = (uint32_t)(g->lo - g->merged_lo);
+    p.vis_hi = (uint32_t)(g->hi - g->merged_lo);
+    for (uint32_t u = 0; u < Q.nv; u++) p.qmask[u] = Q.vmask[u];
+    for (uint32_t e = 0; e < Q.ne; e++) {
+        p.esrc[e] = (uint8_t)Q.edges[e].src;
+        p.edst[e] = (uint8_t)Q.edges[e].dst;
+        p.out_e[Q.edges[e].src] |= 1u << e;
+        p.in_e[Q.edges[e].dst] |= 1u << e;
+    }
+    for (int d = 0; d < 2; d++) {
+        p.offs[d] = g->offs[d];
+        p.nbr[d] = g->base[g->cur][d].nbr;
+        p.s32[d] = g->base[g->cur][d].s32;
+    }
+    p.debi = Q.debi;
+    p.vmask = g->d_vmask;
+    p.sim = g->d_sim;
+    p.flags = reinterpret_cast<uint32_t *>(g->d_simctl);
+    unsigned long long *d_pairs = g->d_simctl + 1;
+    const uint32_t grid = cdiv(g->V, 256);
+    k_dualsim_init<<<grid, 256, 0, g->stream>>>(p);
+    CKL();
+    // refine until a pass removes nothing (each pass that changes anything
+    // removes a pair, so V * nv + 1 passes bound the loop)
+    uint32_t changed = 1;
+    for (uint64_t pass = 0; changed; pass++) {
+        if (pass > (uint64_t)g->V * Q.nv + 1) return fail(g, MN_ERR_DEVICE, "dual simulation did not settle");
+        CK(cudaMemsetAsync(p.flags, 0, sizeof(uint32_t), g->stream));
+        k_dualsim_pass<<<grid, 256, 0, g->stream>>>(p);
+        CKL();
+        CK(cudaMemcpyAsync(&changed, p.flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+    }
+    CK(cudaMemsetAsync(g->d_simctl, 0, 2 * sizeof(unsigned long long), g->stream));
+    k_dualsim_summary<<<grid, 256, 0, g->stream>>>(p, d_pairs);
+    CKL();
+    uint32_t present = 0;
+    unsigned long long npairs = 0;
+    CK(cudaMemcpyAsync(&present, p.flags + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(&npairs, d_pairs, sizeof(npairs), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    const bool match = present == (Q.nv >= 32 ? 0xffffffffu : (1u << Q.nv) - 1u);
+    if (!match) {                    // some query vertex has no image: no match
+        CK(cudaMemsetAsync(g->d_sim, 0, sizeof(uint32_t) * g->V, g->stream));
+        npairs = 0;
+    }
+    if (sim) {
+        const cudaMemcpyKind k = (dst_flags & MN_DST_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        CK(cudaMemcpyAsync(sim, g->d_sim, sizeof(uint32_t) * g->V, k, g->stream));
+    }
+    CK(cudaStreamSynchronize(g->stream));
+    if (pairs) *pairs = npairs;
     return MN_OK;
 }
 

@@ -41,7 +41,7 @@ EXPORTS = [
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
-    "mn_last_error",
+    "mn_dual_simulation", "mn_last_error",
 ]
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
@@ -120,6 +120,7 @@ def load(path: str | None = None):
         "mn_set_time_window": (S, [P, C.c_int64]),
         "mn_memory_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(U64)]),
         "mn_reset_index": (S, [P]),
+        "mn_dual_simulation": (S, [P, C.c_uint32, P, C.c_uint32, C.POINTER(U64)]),
         "mn_delete_batch": (S, [P, P, U64, C.c_uint32, C.POINTER(_BatchResult)]),
         "mn_fetch_embeddings": (S, [P, U64, C.c_uint32, C.c_int32, U64, U64, P, C.c_uint32,
                                     C.POINTER(U64)]),
@@ -195,6 +196,7 @@ class Graph:
         if st != MN_OK:
             raise MnError(st, self._lib.mn_last_error(None).decode())
         self._h = h
+        self._num_vertices = num_vertices
         self.layouts = []
         self.last = None
 
@@ -262,6 +264,15 @@ class Graph:
                                            flags, C.byref(r))
         self._check(st)
         return self._result(r)
+
+    def dual_simulation(self, qid: int) -> np.ndarray:
+        """Dual simulation over the live window: uint32 per data vertex, bit u
+        set iff query vertex u is related to it (mn_dual_simulation)."""
+        V = self._num_vertices
+        out = np.zeros(V, dtype=np.uint32)
+        pairs = C.c_uint64()
+        self._check(self._lib.mn_dual_simulation(self._h, qid, out.ctypes.data, 0, C.byref(pairs)))
+        return out
 
     def memory_info(self) -> dict:
         """Device bytes held now, the peak, and the budget (0 = none)."""
