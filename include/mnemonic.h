@@ -244,13 +244,17 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
  * precedence is ignored (it constrains edge instances, not vertices).
  * sim (host, or device with MN_DST_DEVICE; may be NULL) receives
  * num_vertices words, bit u of word v set iff (u, v) is in S; *pairs (may be
- * NULL) gets |S|.  The relation is recomputed from the index on every call. */
+ * NULL) gets |S|.  The relation is recomputed from the index on every call;
+ * the first call allocates num_vertices words of device scratch (kept until
+ * mn_destroy_graph; MN_ERR_OOM beyond mem_budget_bytes).  MN_ERR_INVALID_ARG
+ * for an unknown query_id, MN_ERR_STATE while a queued batch is pending. */
 mn_status mn_dual_simulation(mn_graph *g, uint32_t query_id, uint32_t *sim, uint32_t dst_flags,
                              uint64_t *pairs);
 
 /* Device memory the graph holds now (*used), the most it has held (*peak)
  * and its budget (mem_budget_bytes, 0 = none), in bytes (Sec. VII-D measures
- * the index's memory over a stream).  Any pointer may be NULL. */
+ * the index's memory over a stream).  Any pointer may be NULL; the only error
+ * is a NULL graph (MN_ERR_INVALID_ARG). */
 mn_status mn_memory_info(const mn_graph *g, uint64_t *used, uint64_t *peak, uint64_t *budget);
 
 /* Periodic reset (Sec. VII-D: the cumulative index can be discarded at any
