@@ -50,10 +50,22 @@ def zipf_labels(rng: np.random.Generator, n: int, k: int, s: float) -> np.ndarra
     return rng.choice(k, size=n, p=p).astype(np.uint8)
 
 
+def extra_vertex_labels(rng: np.random.Generator, vmask: np.ndarray, num_vlabels: int,
+                        p: float) -> np.ndarray:
+    """Multi-label vertices: to each vertex's mask add every label bit
+    independently with probability p (Sec. II-A: a vertex carries a set of
+    labels)."""
+    out = vmask.copy()
+    for b in range(num_vlabels):
+        out |= (rng.random(len(vmask)) < p).astype(np.uint32) << np.uint32(b)
+    return out
+
+
 def uniform_stream(num_vertices: int, num_edges: int, num_vlabels: int,
                    num_elabels: int, seed: int, attr_range: int = 1,
-                   self_loops: bool = True) -> dict:
-    """Uniform random directed multigraph stream (parallel edges allowed)."""
+                   self_loops: bool = True, multi_label_p: float = 0.0) -> dict:
+    """Uniform random directed multigraph stream (parallel edges allowed).
+    multi_label_p > 0 gives vertices extra label bits (extra_vertex_labels)."""
     rng = _rng(seed)
     src = rng.integers(0, num_vertices, size=num_edges, dtype=np.int64)
     dst = rng.integers(0, num_vertices, size=num_edges, dtype=np.int64)
@@ -63,7 +75,7 @@ def uniform_stream(num_vertices: int, num_edges: int, num_vlabels: int,
             dst[loop] = rng.integers(0, num_vertices, size=int(loop.sum()))
             loop = src == dst
     vlab = rng.integers(0, num_vlabels, size=num_vertices)
-    return {
+    out = {
         "src": src.astype(np.uint32),
         "dst": dst.astype(np.uint32),
         "label": rng.integers(0, num_elabels, size=num_edges).astype(np.uint8),
@@ -73,11 +85,14 @@ def uniform_stream(num_vertices: int, num_edges: int, num_vlabels: int,
         "num_vertices": int(num_vertices),
         "num_edge_labels": int(num_elabels),
     }
+    if multi_label_p > 0:
+        out["vmask"] = extra_vertex_labels(rng, out["vmask"], num_vlabels, multi_label_p)
+    return out
 
 
 def rmat_stream(scale: int, num_edges: int, a: float, b: float, c: float,
                 num_elabels: int, label_zipf: float, num_vlabels: int,
-                attr_range: int, seed: int) -> dict:
+                attr_range: int, seed: int, multi_label_p: float = 0.0) -> dict:
     """R-MAT power-law directed multigraph (Chakrabarti et al. 2004).
 
     Each edge picks one quadrant per bit level with probabilities (a, b, c, d);
@@ -106,7 +121,7 @@ def rmat_stream(scale: int, num_edges: int, a: float, b: float, c: float,
     src = perm[src]
     dst = perm[dst]
     vlab = rng.integers(0, num_vlabels, size=n)
-    return {
+    out = {
         "src": src.astype(np.uint32),
         "dst": dst.astype(np.uint32),
         "label": zipf_labels(rng, num_edges, num_elabels, label_zipf),
@@ -116,6 +131,9 @@ def rmat_stream(scale: int, num_edges: int, a: float, b: float, c: float,
         "num_vertices": n,
         "num_edge_labels": int(num_elabels),
     }
+    if multi_label_p > 0:
+        out["vmask"] = extra_vertex_labels(rng, out["vmask"], num_vlabels, multi_label_p)
+    return out
 
 
 def flow_stream(num_hosts: int, num_edges: int, num_elabels: int, seed: int,
@@ -222,10 +240,11 @@ def q_tree6(labels=None, vmask=None, **kw):
     return make_query(6, [(s, d, labels[i]) for i, (s, d) in enumerate(E)], vmask, **kw)
 
 
-def random_query(rng: np.random.Generator, nv: int, kind: str, num_elabels: int,
-                 num_vlabels: int, chords: int = 0, label_p=None, **kw):
-    """Random labelled tree (random attachment, random directions) or a cycle
-    of length nv with ``chords`` extra edges between non-adjacent vertices."""
+def random_shape(rng: np.random.Generator, nv: int, kind: str, chords: int = 0):
+    """Edge list (src, dst) of a random tree on nv vertices (random
+    attachment, random directions) or of the directed cycle u0->...->u_{nv-1}->u0
+    plus ``chords`` extra edges between non-adjacent vertices (random
+    directions)."""
     edges = []
     if kind == "tree":
         for v in range(1, nv):
@@ -244,6 +263,14 @@ def random_query(rng: np.random.Generator, nv: int, kind: str, num_elabels: int,
             have.add(frozenset((a, b)))
             edges.append((a, b) if rng.random() < 0.5 else (b, a))
             chords -= 1
+    return edges
+
+
+def random_query(rng: np.random.Generator, nv: int, kind: str, num_elabels: int,
+                 num_vlabels: int, chords: int = 0, label_p=None, **kw):
+    """Random labelled tree (random attachment, random directions) or a cycle
+    of length nv with ``chords`` extra edges between non-adjacent vertices."""
+    edges = random_shape(rng, nv, kind, chords)
     labels = rng.choice(num_elabels, size=len(edges), p=label_p)
     vm = [int(1 << int(rng.integers(0, num_vlabels))) for _ in range(nv)]
     return make_query(nv, [(s, d, int(l)) for (s, d), l in zip(edges, labels)], vm, **kw)

@@ -300,3 +300,116 @@ def test_parallel_edges_multiply(oracle_lib):
     # ts(e0) < ts(e1): u0->u1 at t in {1,2,3} then u1->u0 at t in {4,5}: 3*2;
     # u0 = 1: edge 1->0 (t 4,5) then 0->1 (t 1..3) later: none
     assert oracle_lib.count_static(s, 0, 5, qt) == 6
+
+
+# ---------------------------------------------------------------- multi-label vertices
+
+def multi_stream(seed, n=7, m=36, vl=3, el=2):
+    return gen.uniform_stream(n, m, vl, el, seed=seed, attr_range=2, multi_label_p=0.45)
+
+
+def test_multi_label_generator_gives_proper_supersets():
+    s = multi_stream(1)
+    pop = np.array([bin(int(x)).count("1") for x in s["vmask"]])
+    assert (pop >= 1).all() and (pop >= 2).any()
+
+
+def test_subset_test_hand_fixture(oracle_lib):
+    """L_Q(u) subset-of L(f(u)) with several labels per data vertex (Sec. II-B):
+    vertex masks 0b011, 0b001, 0b110, 0b111; a one-edge query whose source
+    mask is 0b011 only starts at vertices 0 and 3 (both hold labels 0 and 1),
+    and a destination mask 0b100 only ends at vertices 2 and 3."""
+    s = {
+        "src": np.array([0, 0, 1, 2, 3, 3, 1, 0], dtype=np.uint32),
+        "dst": np.array([1, 2, 2, 3, 0, 2, 3, 3], dtype=np.uint32),
+        "label": np.zeros(8, dtype=np.uint8),
+        "attr": np.zeros(8, dtype=np.int32),
+        "ts": np.arange(1, 9, dtype=np.int64),
+        "vmask": np.array([0b011, 0b001, 0b110, 0b111], dtype=np.uint32),
+        "num_vertices": 4, "num_edge_labels": 1,
+    }
+    # sources with both labels 0 and 1: vertices 0 (edges 0, 1, 7) and 3 (edges 4, 5)
+    q = gen.make_query(2, [(0, 1)], vmask=[0b011, 0], iso=True)
+    rows = oracle_lib.list_static(s, 0, 8, q)
+    assert sorted(int(r[2]) for r in rows) == [0, 1, 4, 5, 7]
+    # and destinations holding label 2: vertices 2, 3 -> edges 1 (0->2), 5 (3->2), 7 (0->3)
+    q2 = gen.make_query(2, [(0, 1)], vmask=[0b011, 0b100], iso=True)
+    assert sorted(int(r[2]) for r in oracle_lib.list_static(s, 0, 8, q2)) == [1, 5, 7]
+    # a mask no vertex holds completely matches nothing
+    q3 = gen.make_query(2, [(0, 1)], vmask=[0b1000, 0], iso=True)
+    assert oracle_lib.count_static(s, 0, 8, q3) == 0
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_multi_label_closed_forms(oracle_lib, seed):
+    """Homomorphism walk counts with multi-bit data and query masks: the
+    diagonal D_u = [qmask(u) subset-of vmask(v)] carries the subset test."""
+    s = multi_stream(1200 + seed)
+    rng = np.random.default_rng(seed)
+    masks = [0, 1, 2, 3, 4, 5, 6]
+    vm = [int(rng.choice(masks)) for _ in range(4)]
+    qc = gen.q_cycle(3, vmask=vm[:3], iso=False)
+    assert all_count(oracle_lib, s, qc) == walk_count_cycle(s, qc)
+    qp = gen.q_path(3, vmask=vm, iso=False)
+    assert all_count(oracle_lib, s, qp) == walk_count_path(s, qp)
+    assert len(oracle_lib.brute_force(s, 0, len(s["src"]), qc)) == walk_count_cycle(s, qc)
+    qs = gen.q_out_star(3, vmask=vm, iso=False)
+    assert all_count(oracle_lib, s, qs) == star_count(s, qs)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_multi_label_brute_force_equals_seed_oracle(oracle_lib, seed):
+    rng = np.random.default_rng(4000 + seed)
+    s = multi_stream(1300 + seed, n=int(rng.integers(4, 7)), m=int(rng.integers(12, 26)))
+    q = random_tiny_query(rng)
+    q["vmask"] = [int(rng.integers(0, 8)) for _ in range(q["nv"])]
+    n = len(s["src"])
+    bf = oracle_lib.brute_force(s, 0, n, q)
+    st = oracle_lib.list_static(s, 0, n, q)
+    assert bf.shape == st.shape and (bf == st).all()
+
+
+# ---------------------------------------------------------------- budgeted delta count
+
+@pytest.mark.parametrize("seed", range(10))
+def test_delta_count_budget_unlimited_is_exact(oracle_lib, seed):
+    """With no node budget (0) the count is |S(G + ins) \\ S(G)| by brute
+    force, reported complete."""
+    rng = np.random.default_rng(5000 + seed)
+    s = tiny_stream(1400 + seed, n=5, m=24)
+    q = random_tiny_query(rng)
+    lo, hi, hi_new = 2, 13, 20
+    before = as_set(oracle_lib.brute_force(s, lo, hi, q))
+    after = as_set(oracle_lib.brute_force(s, lo, hi_new, q))
+    mask = np.zeros(hi_new - lo, dtype=np.uint8)
+    mask[hi - lo:] = 1
+    cnt, complete = oracle_lib.delta_count_budget(s, lo, hi_new, q, mask, 0)
+    assert complete and cnt == len(after - before)
+    big, complete = oracle_lib.delta_count_budget(s, lo, hi_new, q, mask, 10**9)
+    assert complete and big == cnt
+
+
+def test_delta_count_budget_partial_is_flagged_and_bounded(oracle_lib):
+    """A budget that runs out is reported incomplete, and the partial count
+    never exceeds the exact one and grows with the budget."""
+    s = gen.uniform_stream(12, 200, 1, 1, seed=77)
+    q = gen.q_path(3, iso=False)
+    lo, hi, hi_new = 0, 150, 200
+    exact = len(as_set(oracle_lib.brute_force(s, lo, hi_new, q)) -
+                as_set(oracle_lib.brute_force(s, lo, hi, q)))
+    assert exact > 100
+    mask = np.zeros(hi_new - lo, dtype=np.uint8)
+    mask[hi - lo:] = 1
+    prev = -1
+    saw_partial = False
+    for budget in (1, 10, 100, 1000, 10**4, 10**5, 10**7):
+        cnt, complete = oracle_lib.delta_count_budget(s, lo, hi_new, q, mask, budget)
+        assert cnt <= exact and cnt >= prev
+        if not complete:
+            saw_partial = True
+        else:
+            assert cnt == exact
+        prev = cnt
+    assert saw_partial and prev == exact
+    cnt, complete = oracle_lib.delta_count_budget(s, lo, hi_new, q, mask, 1)
+    assert not complete
