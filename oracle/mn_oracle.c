@@ -34,6 +34,8 @@
  *                    (no masking: duplicates are removed by the set);
  *   or_count_static  |S(G)|: the same DFS seeded from every live edge at
  *                    query edge 0 only, counted without storing.
+ *   or_delta_count_omp  the first-edge count of dS with the batch edges
+ *                    spread over OpenMP threads (timing of the CPU baseline).
  * Every candidate is re-checked against the full definition at the leaf.
  *
  * Records are rows of (n_q + k_q) uint64 values: f(u_0..u_{n_q-1}) followed
@@ -42,6 +44,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_MAXV 16
 #define OR_MAXE 16
@@ -483,6 +488,72 @@ int or_delta_count_budget(const or_graph *G, const or_query *q, uint64_t max_nod
     free(scratch.rows);
     free_adjacency(&c);
     return (max_nodes && c.nodes >= max_nodes) ? 1 : 0;
+}
+
+/* |dS| as or_delta_count computes it, with the batch edges spread over
+ * `nthreads` OpenMP threads (0 = all cores): the CPU design point of the
+ * paper's system (Sec. VI, OpenMP over work units; Sec. VII, 24 threads),
+ * used to time the CPU baseline.  Each thread has its own DFS state and
+ * scratch list; the adjacency is built once and only read.  The sum does not
+ * depend on the schedule. */
+uint64_t or_delta_count_omp(const or_graph *G, const or_query *q, int nthreads)
+{
+    dfs_ctx c0;
+    memset(&c0, 0, sizeof(c0));
+    c0.G = G; c0.q = q; c0.need_batch = 1;
+    int tmp[OR_MAXE];
+    if (!connected_order(q, 0, tmp) || G->in_batch == NULL) return 0;
+    build_adjacency(&c0);
+    uint64_t total = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel reduction(+ : total)
+    {
+        dfs_ctx c = c0;
+        or_result scratch;
+        memset(&scratch, 0, sizeof(scratch));
+        scratch.width = q->nv + q->ne;
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t xi = 0; xi < (int64_t)G->m; xi++) {
+            const uint64_t x = (uint64_t)xi;
+            if (!G->in_batch[x] || !edge_live(G, x)) continue;
+            for (int e = 0; e < q->ne; e++) {
+                c.out = &scratch;
+                scratch.n = 0;
+                seed(&c, e, x);
+                for (uint64_t r = 0; r < scratch.n; r++) {
+                    const uint64_t *row = scratch.rows + r * scratch.width;
+                    int first = 1;
+                    for (int i = 0; i < e && first; i++) {
+                        uint64_t sq = row[q->nv + i];
+                        uint64_t lo = 0, hi = G->m;
+                        while (lo < hi) {
+                            uint64_t mid = (lo + hi) / 2;
+                            if (G->seq[mid] < sq) lo = mid + 1; else hi = mid;
+                        }
+                        if (lo < G->m && G->seq[lo] == sq && G->in_batch[lo]) first = 0;
+                    }
+                    total += (uint64_t)first;
+                }
+            }
+        }
+        free(scratch.rows);
+    }
+    free_adjacency(&c0);
+    return total;
+}
+
+/* Threads or_delta_count_omp runs with when asked for all cores. */
+int or_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* |S(G)|: every embedding has exactly one image of query edge 0. */

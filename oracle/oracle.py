@@ -31,7 +31,7 @@ def build(force: bool = False, out: str | None = None, defines=()) -> str:
     """Compile mn_oracle.c with gcc into a shared library; returns its path."""
     out = out or _LIB
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", out, _SRC]
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", out, _SRC]
         cmd += [f"-D{d}" for d in defines]
         subprocess.check_call(cmd)
     return out
@@ -83,6 +83,10 @@ def _load(path: str | None = None):
         fn = getattr(lib, name)
         fn.restype = C.c_uint64
         fn.argtypes = [C.POINTER(_Graph), C.POINTER(_Query)]
+    lib.or_delta_count_omp.restype = C.c_uint64
+    lib.or_delta_count_omp.argtypes = [C.POINTER(_Graph), C.POINTER(_Query), C.c_int]
+    lib.or_max_threads.restype = C.c_int
+    lib.or_max_threads.argtypes = []
     lib.or_delta_count_budget.restype = C.c_int
     lib.or_delta_count_budget.argtypes = [C.POINTER(_Graph), C.POINTER(_Query), C.c_uint64,
                                           C.POINTER(C.c_uint64)]
@@ -187,6 +191,20 @@ def delta_count_first_edge(stream, lo, hi, batch_lo, batch_hi, q, lib_path=None)
     gv = _GraphView(stream, lo, hi, None, ib)
     qs = _query_struct(q)
     return int(lib.or_delta_count(C.byref(gv.g), C.byref(qs)))
+
+
+def delta_count_parallel(stream, lo, hi, q, batch_mask, threads=0, lib_path=None) -> int:
+    """|dS| for the flagged batch edges (first-edge rule), with the seeds
+    spread over OpenMP threads (0 = all cores)."""
+    lib = _load(lib_path)
+    gv = _GraphView(stream, lo, hi, None, batch_mask)
+    qs = _query_struct(q)
+    return int(lib.or_delta_count_omp(C.byref(gv.g), C.byref(qs), int(threads)))
+
+
+def max_threads(lib_path=None) -> int:
+    """Threads the parallel count uses when asked for all cores."""
+    return int(_load(lib_path).or_max_threads())
 
 
 def delta_count_budget(stream, lo, hi, q, batch_mask, max_nodes, lib_path=None):

@@ -413,3 +413,32 @@ def test_delta_count_budget_partial_is_flagged_and_bounded(oracle_lib):
     assert saw_partial and prev == exact
     cnt, complete = oracle_lib.delta_count_budget(s, lo, hi_new, q, mask, 1)
     assert not complete
+
+
+# ---------------------------------------------------------------- parallel (timing) oracle
+
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_parallel_delta_count_is_the_set_difference(oracle_lib, seed, threads):
+    """The OpenMP count over seeds (the CPU baseline's timing oracle) gives
+    |S(G + ins) minus S(G)| by brute force, for any thread count."""
+    rng = np.random.default_rng(6000 + seed)
+    s = tiny_stream(1500 + seed, n=5, m=26)
+    q = random_tiny_query(rng)
+    lo, hi, hi_new = 1, 12, 22
+    before = as_set(oracle_lib.brute_force(s, lo, hi, q))
+    after = as_set(oracle_lib.brute_force(s, lo, hi_new, q))
+    mask = np.zeros(hi_new - lo, dtype=np.uint8)
+    mask[hi - lo:] = 1
+    assert oracle_lib.delta_count_parallel(s, lo, hi_new, q, mask, threads) == len(after - before)
+
+
+def test_parallel_delta_count_on_a_larger_stream(oracle_lib):
+    s = gen.rmat_stream(9, 6000, 0.57, 0.19, 0.19, 2, 1.2, 2, 10, seed=3)
+    q = gen.q_path(3, labels=[0, 1, 0], iso=True, temporal="chain")
+    mask = np.zeros(6000, dtype=np.uint8)
+    mask[4000:] = 1
+    want = len(oracle_lib.delta(s, 0, 6000, 4000, 6000, q))
+    assert want > 100
+    for t in (1, 2, 0):
+        assert oracle_lib.delta_count_parallel(s, 0, 6000, q, mask, t) == want
