@@ -246,7 +246,8 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
  * num_vertices words, bit u of word v set iff (u, v) is in S; *pairs (may be
  * NULL) gets |S|.  The relation is recomputed from the index on every call;
  * the first call allocates num_vertices words of device scratch (kept until
- * mn_destroy_graph; MN_ERR_OOM beyond mem_budget_bytes).  MN_ERR_INVALID_ARG
+ * mn_destroy_graph; MN_ERR_OOM beyond mem_budget_bytes).  The passes run
+ * in groups of 8 per host check; mn_stats.dualsim_passes counts them.  MN_ERR_INVALID_ARG
  * for an unknown query_id, MN_ERR_STATE while a queued batch is pending. */
 mn_status mn_dual_simulation(mn_graph *g, uint32_t query_id, uint32_t *sim, uint32_t dst_flags,
                              uint64_t *pairs);
@@ -301,15 +302,38 @@ mn_status mn_set_tuning(mn_graph *g, uint32_t blocks_per_sm, uint32_t split_min,
 mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *max_blocks_per_sm,
                         uint32_t *split_min, uint32_t *split_depth, int32_t *smem_carveout);
 
+/* Learned work splits (the learned counterpart of the paper's pull-based
+ * distribution of work units, Sec. VI): under MN_ORDER_LEARNED, a seed whose
+ * predicted work under its chosen order is at least 2^log2_cycles SM cycles
+ * has the candidate range of its first search depth handed to the
+ * work-splitting queue in up to 16 pieces as soon as a warp takes it, instead
+ * of waiting for idle warps to ask.  log2_cycles <= 0 turns it off (the
+ * default); NaN is MN_ERR_INVALID_ARG.  Results are unaffected.
+ * mn_get_presplit reads the threshold back (0 = off). */
+mn_status mn_set_presplit(mn_graph *g, float log2_cycles);
+mn_status mn_get_presplit(const mn_graph *g, float *log2_cycles);
+
 /* Online autotuning of the launch parameters above: each of the next
- * insert batches that enumerates runs under one candidate configuration
- * (blocks per SM x split threshold x split depth), `batches_per_config` batches
- * each; then the configuration with the least enumeration time per unit of
- * work (adjacency entries tested + candidates bound) is kept.  Results are
- * unaffected.  mn_autotune_state reports whether tuning is still running and
- * how many configurations are left. */
+ * insert batches that enumerates runs under one candidate configuration,
+ * `batches_per_config` batches each; then the configuration with the least
+ * enumeration time per unit of work (adjacency entries tested + candidates
+ * bound) is kept.  Results are unaffected.  The candidates (listed by
+ * mn_autotune_candidates) are: resident blocks per SM at the occupancy limit
+ * x split threshold {40, 64, 128} x split depth {3, any} x pre-split
+ * threshold {off, 2^20, 2^22 cycles}.  mn_autotune_state reports whether
+ * tuning is still running and how many configurations are left. */
 mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config);
 mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left);
+
+/* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off). */
+typedef struct {
+    uint32_t blocks_per_sm, split_min, split_depth;
+    float presplit_log2;
+} mn_tune_config;
+
+/* Copy the autotuner's candidates to out[0..cap) (out may be NULL to ask for
+ * the count); *n gets the count; MN_ERR_INVALID_ARG if out is too small. */
+mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out, uint32_t *n);
 
 /* Largest live window mn_count_static_noalloc accepts: its seed scratch
  * holds one 8-byte work unit per live edge. */
@@ -359,6 +383,24 @@ mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi,
  * default).  Lets tests drive the bounded-wait path without faulting. */
 mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters);
 
+/* Bound of the enumerator's only device-side wait.  When a warp runs out of
+ * work units (Sec. VI: work units are pulled), it takes a ticket of the
+ * work-splitting queue and polls its slot (backing off to ~2 us per poll)
+ * until a busy warp hands it a subtree there.  It gives the slot up -- the
+ * normal exit, which never loses work: a warp that later publishes into an
+ * abandoned slot keeps its task -- once no warp is busy, or after max_polls
+ * polls even while warps are busy (0 = the default, 65,536 polls, ~0.13 s).
+ * A slot that a publishing warp has reserved but not published within
+ * another 4,096 polls (~8 ms; publishing takes microseconds) is given up
+ * with a device status: the batch is applied, its counts may be partial and
+ * the call returns MN_ERR_TIMEOUT; the graph stays usable.  max_polls above
+ * 2^30 is MN_ERR_INVALID_ARG.  Flags: MN_WAIT_HOLD (a test hook) makes every
+ * waiting warp neither take a task nor give up its slot, so each such wait
+ * runs to its bound and reports MN_ERR_TIMEOUT: the timeout path can be
+ * tested without faulting or hanging the GPU. */
+#define MN_WAIT_HOLD 0x1u
+mn_status mn_set_wait_limit(mn_graph *g, uint32_t max_polls, uint32_t flags);
+
 /* Counters of one graph since creation (or the last mn_reset_stats).  Stage
  * times are device time measured with CUDA events on the graph's stream
  * around each stage when timing is enabled (mn_set_timing), else 0.  The
@@ -382,6 +424,8 @@ typedef struct {
     uint64_t tasks_split;          /* subtrees handed from busy to idle warps */
     uint64_t h2d_bytes;            /* bytes the library copied host -> device */
     uint64_t d2h_bytes;            /* bytes copied device -> host (counts, status) */
+    uint64_t rerun_launches;       /* enumerator launches that re-ran the seeds of overflowed lists */
+    uint64_t dualsim_passes;       /* refinement passes run by mn_dual_simulation */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

@@ -627,8 +627,19 @@ constexpr int ENUM_WARPS = 4;              // warps per block
 // 16 warps at 122 registers (the few spilled bytes stay in L1).
 constexpr int ENUM_MIN_BLOCKS = 5;
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
-constexpr uint32_t IDLE_SPINS = 1u << 24;  // idle wait bound (backoff up to 2 us per poll)
+// Idle wait of a ticket holder (polls of its task-ring slot, backing off to
+// 2 us per poll): it gives its slot up after wait_polls polls (default
+// WAIT_POLLS, ~0.13 s) even while other warps are busy, and reports
+// ST_TIMEOUT when a slot that a publisher reserved stays unpublished for
+// RESERVE_POLLS more polls (~8 ms; publishing takes microseconds).
+constexpr uint32_t WAIT_POLLS = 1u << 16;
+constexpr uint32_t RESERVE_POLLS = 1u << 12;
 constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
+// Seed word flag (set by k_pick): the seed's predicted work is above the
+// pre-split threshold.  Seed words: seq32 << 32 | flags and candidate order
+// << 24 | query << 8 | query edge.
+constexpr unsigned long long SEED_PRESPLIT = 1ull << 31;
+constexpr int PRESPLIT_PIECES = 16;
 
 struct EnumParams {
     const uint32_t *nbr[NPROB];         // 0,1: by neighbour (out, in); 2,3: by arrival
@@ -668,6 +679,9 @@ struct EnumParams {
     unsigned long long *seed_work1;
     uint32_t split_min;                 // smallest range handed to an idle warp
     uint32_t split_depth;               // deepest search depth that may be split
+    uint32_t wait_polls;                // idle wait bound (WAIT_POLLS)
+    uint32_t wait_hold;                 // test: holders neither take nor give up their slot
+    unsigned long long qrun[2];         // per seed set: bit q set = enumerate query q's seeds
 };
 
 __device__ __forceinline__ uint32_t vload(const uint32_t *p)
@@ -851,14 +865,16 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                     bool leave = false;
                     for (uint32_t it = 0;; it++) {
                         const unsigned long long v = vload64(st);
-                        if (v == key + SLOT_PUBLISHED) { kind = 2; unit = t; break; }
-                        if (v >= key + 4) break;        // skipped by a later lap
-                        if (v != key + SLOT_RESERVED && slot_free(v, p.epoch) &&
-                            (it >= IDLE_SPINS || quiet >= 4)) {
-                            if (atomicCAS(st, v, key + SLOT_ABANDONED) == v) { leave = true; break; }
-                            continue;                   // state moved on: look again
+                        if (!p.wait_hold) {
+                            if (v == key + SLOT_PUBLISHED) { kind = 2; unit = t; break; }
+                            if (v >= key + 4) break;    // skipped by a later lap
+                            if (v != key + SLOT_RESERVED && slot_free(v, p.epoch) &&
+                                (it >= p.wait_polls || quiet >= 4)) {
+                                if (atomicCAS(st, v, key + SLOT_ABANDONED) == v) { leave = true; break; }
+                                continue;               // state moved on: look again
+                            }
                         }
-                        if (it >= 2 * IDLE_SPINS) {     // a reserved slot never published
+                        if (it >= p.wait_polls + RESERVE_POLLS) {   // a reserved slot never published
                             atomicOr(p.status, ST_TIMEOUT);
                             leave = true;
                             break;
@@ -880,7 +896,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
 
         // ---------------------------------------------------------- set up the unit
         uint32_t q, j, kc = 0, sid = 0, set = 0, root, f = 0, g = 0, tbeg = 0, tend = 0;
-        bool skip = false;
+        bool skip = false, presplit = false;
         if (kind == 1) {
             w_seeds++;
             set = unit >= nseeds0 ? 1u : 0u;
@@ -890,11 +906,14 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
             q = (uint32_t)(sd >> 8) & 0xffffu;
             j = (uint32_t)sd & 0xffu;
             kc = (uint32_t)(sd >> 24) & (NCAND - 1);
+            presplit = (sd & SEED_PRESPLIT) != 0;
             sid = unit;
             const Plan *pl = &p.plans[(q * MN_MAX_QE + j) * NCAND + kc];
             const uint32_t slot0 = seed32 & p.cap_mask;
             const uint32_t vs = p.ring_src[slot0], vd = p.ring_dst[slot0];
             if (pl->iso && vs == vd) skip = true;
+            const unsigned long long qr = set ? p.qrun[1] : p.qrun[0];
+            if (!((qr >> (q & 63)) & 1ull)) skip = true;   // this query's seeds are not run
             if (lane == (int)pl->seed_src) f = vs;
             if (lane == (int)pl->seed_dst) f = vd;
             if (lane == (int)j) g = seed32 - p.base32;
@@ -1249,6 +1268,23 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
             };
 
             open(lvl, kind == 2);
+            // a seed whose predicted work is above the threshold (k_pick):
+            // its first depth's candidates go to the task ring in up to
+            // PRESPLIT_PIECES ranges right away, before any warp is idle
+            if (presplit && p.tasks && lvl < last) {
+                const uint32_t len = end > cur ? end - cur : 0u;
+                const uint32_t pieces = min(len, (uint32_t)PRESPLIT_PIECES);
+                if (pieces > 1) {
+                    const uint32_t sz = (len + pieces - 1) / pieces;
+                    uint32_t cut = end;
+                    for (uint32_t b0 = cur + sz; b0 < end; b0 += sz) {
+                        if (!push(lvl, b0, min(end, b0 + sz))) break;
+                        if (cut == end) cut = b0;
+                    }
+                    end = cut;
+                    if (lane == (int)lvl) Lend = cut;
+                }
+            }
             while (lvl >= root) {
                 if (++iters > p.max_iters) {
                     if (lane == 0) atomicOr(p.status, ST_TIMEOUT);

@@ -13,6 +13,7 @@
 // Every batch runs as one chain of kernels on the graph's stream with a
 // single host synchronisation at the end (to return the counts).
 #include <algorithm>
+#include <cmath>
 #include <climits>
 #include <cstdio>
 #include <cstring>
@@ -148,12 +149,17 @@ struct mn_graph {
     uint32_t *d_sim = nullptr;  // dual simulation: [V] words
     unsigned long long *d_simctl = nullptr;   // its two flag words, then the pair count
     unsigned long long max_iters = ~0ull;
+    uint32_t wait_polls = WAIT_POLLS, wait_hold = 0;   // idle wait of the enumerator (mn_set_wait_limit)
+    // per (query, sign): decayed maximum of records per inserted (sign 0) or
+    // expired (sign 1) edge, used to size the lists before a launch
+    std::vector<double> rec_rate[2];
     int enum_grid = 0;          // persistent grid: SMs x resident blocks per SM
     int nsm = 0, enum_max_per_sm = 0;
     uint32_t split_min = SPLIT_MIN, split_depth = MN_MAX_QE;
+    float presplit_log2 = INFINITY;   // learned pre-splitting threshold (log2 predicted cycles); inf = off
     int smem_carveout = -1;     // preferred shared-memory carve-out of the enumerator (%), -1 = driver
     // online autotuner: candidate launch configurations tried on live batches
-    struct TuneCfg { uint32_t bps, split_min, split_depth; };
+    struct TuneCfg { uint32_t bps, split_min, split_depth; float presplit_log2; };
     bool tuning = false;
     std::vector<TuneCfg> tune_cfgs;
     std::vector<double> tune_ms, tune_work;
@@ -596,7 +602,7 @@ mn_status choose_orders(mn_graph *g, int phase)
                                                               0, g->d_w1t, g->d_w2t, g->d_P, g->d_y);
         CKL();
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
-                                            1.0f);
+                                            1.0f, g->presplit_log2);
         CKL();
     }
     if (g->policy == MN_ORDER_EXPLORE)
@@ -637,7 +643,8 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
 // One enumerator launch over the seeds of one or two phases (dS+ and dS- of
 // one batch share the adjacency buffer and visibility; a single launch has
 // one tail instead of two).  The first phase's seeds are taken first.
-mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_only)
+mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_only,
+                           const unsigned long long *qrun = nullptr)
 {
     const Phase &a = ph[0];
     EnumParams p;
@@ -678,8 +685,13 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     p.max_iters = g->max_iters;
     p.status = &g->d_ctrl->status;
     p.work = g->d_ctrl->work;
-    const bool explore = g->policy == MN_ORDER_EXPLORE;
+    // a re-run (qrun given) logs no work: its seeds were logged by the first run
+    const bool explore = g->policy == MN_ORDER_EXPLORE && !qrun;
     p.seed_work = explore && a.phase < 2 ? seed_work_of(g, a.phase) : nullptr;
+    p.qrun[0] = qrun ? qrun[0] : ~0ull;
+    p.qrun[1] = qrun ? qrun[1] : ~0ull;
+    p.wait_polls = g->wait_polls;
+    p.wait_hold = g->wait_hold;
     if (nph > 1) {
         const Phase &b = ph[1];
         if (b.buf != a.buf || b.base != a.base || b.vis_hi != a.vis_hi || b.flags != a.flags)
@@ -803,43 +815,99 @@ mn_status read_ctrl(mn_graph *g)
     return MN_OK;
 }
 
-// Grow the result lists of `phase` to the exact counts (within the memory
-// budget).  Returns true in *regrown when something was too small.
-mn_status grow_outputs(mn_graph *g, int phase, bool *regrown, bool *over_budget)
+// Make the list of (query q, phase) hold at least `need` records (grown to
+// a power of two with a quarter of headroom), within the memory budget.
+// *grown tells whether it was reallocated; the device pointer table is
+// refreshed by sync_out_table.
+mn_status ensure_out_cap(mn_graph *g, size_t q, int phase, uint64_t need, bool *grown, bool *over_budget)
 {
-    *regrown = false;
-    for (size_t q = 0; q < g->queries.size(); q++) {
-        QueryHost &Q = g->queries[q];
-        const unsigned long long c = g->h_ctrl->counts[q * 3 + phase];
-        if (c <= Q.out_cap[phase]) continue;
-        const uint64_t cap = next_pow2(c);
-        const uint64_t bytes = cap * Q.rec_bytes;
-        const uint64_t old = Q.out_cap[phase] * Q.rec_bytes;
-        if (g->mem_budget && g->mem_used - old + bytes > g->mem_budget) {
-            *over_budget = true;
-            continue;
-        }
-        dfree(g, Q.out[phase], old);
-        Q.out[phase] = nullptr;
-        Q.out_cap[phase] = 0;
-        TRY(dalloc(g, &Q.out[phase], bytes, false));
-        Q.out_cap[phase] = cap;
-        *regrown = true;
+    *grown = false;
+    QueryHost &Q = g->queries[q];
+    if (need <= Q.out_cap[phase]) return MN_OK;
+    const uint64_t cap = next_pow2(need + need / 4);
+    const uint64_t bytes = cap * Q.rec_bytes;
+    const uint64_t old = Q.out_cap[phase] * Q.rec_bytes;
+    if (g->mem_budget && g->mem_used - old + bytes > g->mem_budget) {
+        *over_budget = true;
+        return MN_OK;
     }
-    if (*regrown) {
-        std::vector<uint8_t *> ptrs(g->max_queries * 2, nullptr);
-        std::vector<unsigned long long> caps(g->max_queries * 2, 0);
-        for (size_t q = 0; q < g->queries.size(); q++)
-            for (int s = 0; s < 2; s++) {
-                ptrs[q * 2 + s] = g->queries[q].out[s];
-                caps[q * 2 + s] = g->queries[q].out_cap[s];
-            }
-        CK(cudaMemcpyAsync(g->d_out_ptrs, ptrs.data(), ptrs.size() * sizeof(uint8_t *),
-                           cudaMemcpyHostToDevice, g->stream));
-        CK(cudaMemcpyAsync(g->d_out_cap, caps.data(), caps.size() * sizeof(unsigned long long),
-                           cudaMemcpyHostToDevice, g->stream));
-    }
+    dfree(g, Q.out[phase], old);
+    Q.out[phase] = nullptr;
+    Q.out_cap[phase] = 0;
+    TRY(dalloc(g, &Q.out[phase], bytes, false));
+    Q.out_cap[phase] = cap;
+    *grown = true;
     return MN_OK;
+}
+
+mn_status sync_out_table(mn_graph *g)
+{
+    std::vector<uint8_t *> ptrs(g->max_queries * 2, nullptr);
+    std::vector<unsigned long long> caps(g->max_queries * 2, 0);
+    for (size_t q = 0; q < g->queries.size(); q++)
+        for (int s = 0; s < 2; s++) {
+            ptrs[q * 2 + s] = g->queries[q].out[s];
+            caps[q * 2 + s] = g->queries[q].out_cap[s];
+        }
+    CK(cudaMemcpyAsync(g->d_out_ptrs, ptrs.data(), ptrs.size() * sizeof(uint8_t *),
+                       cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_out_cap, caps.data(), caps.size() * sizeof(unsigned long long),
+                       cudaMemcpyHostToDevice, g->stream));
+    // the host arrays are freed on return: the copies must have read them
+    CK(cudaStreamSynchronize(g->stream));
+    return MN_OK;
+}
+
+// Grow the result lists of `phase` to the exact counts (within the memory
+// budget).  Sets bit q of *rerun for every list that was too small.
+mn_status grow_outputs(mn_graph *g, int phase, unsigned long long *rerun, bool *over_budget)
+{
+    *rerun = 0;
+    bool any = false;
+    for (size_t q = 0; q < g->queries.size(); q++) {
+        const unsigned long long c = g->h_ctrl->counts[q * 3 + phase];
+        if (c <= g->queries[q].out_cap[phase]) continue;
+        bool grown = false;
+        TRY(ensure_out_cap(g, q, phase, c, &grown, over_budget));
+        if (grown) { *rerun |= 1ull << q; any = true; }
+    }
+    if (any) TRY(sync_out_table(g));
+    return MN_OK;
+}
+
+// Before a launch: lists of queries whose recent batches produced more
+// records per edge than this batch's lists hold are grown now, so that the
+// batch is not enumerated twice.
+mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
+{
+    bool any = false, over = false;
+    for (int s = 0; s < 2; s++) {
+        const uint64_t edges = s == 0 ? n_new : n_expired;
+        if (!edges) continue;
+        for (size_t q = 0; q < g->queries.size() && q < g->rec_rate[s].size(); q++) {
+            const double est = g->rec_rate[s][q] * (double)edges;
+            if (est <= (double)g->queries[q].out_cap[s]) continue;
+            bool grown = false;
+            TRY(ensure_out_cap(g, q, s, (uint64_t)est, &grown, &over));
+            any = any || grown;
+        }
+    }
+    if (any) TRY(sync_out_table(g));
+    return MN_OK;
+}
+
+// After a batch: update the records-per-edge estimates (a decayed maximum).
+void note_rates(mn_graph *g, uint64_t n_new, uint64_t n_expired)
+{
+    for (int s = 0; s < 2; s++) {
+        const uint64_t edges = s == 0 ? n_new : n_expired;
+        g->rec_rate[s].resize(g->queries.size(), 0.0);
+        if (!edges) continue;
+        for (size_t q = 0; q < g->queries.size(); q++) {
+            const double r = (double)g->h_ctrl->counts[q * 3 + s] / (double)edges;
+            g->rec_rate[s][q] = std::max(0.9 * g->rec_rate[s][q], r);
+        }
+    }
 }
 
 void fill_result(mn_graph *g, mn_batch_result *out, uint64_t seq_lo, uint64_t seq_hi,
@@ -863,29 +931,43 @@ void fill_result(mn_graph *g, mn_batch_result *out, uint64_t seq_lo, uint64_t se
     out->count_neg = g->count_neg.data();
 }
 
-// One enumeration phase as launched (kept to re-run it after growing lists).
-// Check the phases' status, re-running any whose lists overflowed after
-// growing them to the exact counts.
+// Check the status of the launched phases.  Counts are exact even when a
+// list overflowed (records past a list's end are counted, not written); the
+// lists that overflowed are grown to the exact count and only their
+// (query, phase) seeds are enumerated again, in one launch.
 mn_status enumerate_phases(mn_graph *g, const Phase *ph, int nph, bool count_only, bool *over_budget)
 {
     TRY(read_ctrl(g));
     if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     if (count_only) return MN_OK;
     for (int round = 0; round < 2; round++) {
-        bool any = false;
-        for (int k = 0; k < nph; k++) {
-            bool regrown = false;
-            TRY(grow_outputs(g, ph[k].phase, &regrown, over_budget));
-            any = any || regrown;
-        }
-        if (!any) break;
-        // the phases share a launch and the counters: re-run them together
-        CK(cudaMemsetAsync(&g->d_ctrl->counts[0], 0, sizeof(g->h_ctrl->counts), g->stream));
-        TRY(launch_enumerate(g, ph, nph, false));
+        unsigned long long rerun[2] = {0, 0};   // per launch seed set
+        for (int k = 0; k < nph; k++) TRY(grow_outputs(g, ph[k].phase, &rerun[k], over_budget));
+        if (!rerun[0] && !rerun[1]) break;
+        for (int k = 0; k < nph; k++)
+            for (size_t q = 0; q < g->queries.size(); q++)
+                if ((rerun[k] >> q) & 1ull)
+                    CK(cudaMemsetAsync(&g->d_ctrl->counts[q * 3 + ph[k].phase], 0, sizeof(unsigned long long),
+                                       g->stream));
+        TRY(launch_enumerate(g, ph, nph, false, rerun));
+        g->stats.rerun_launches++;
         TRY(read_ctrl(g));
         if (g->h_ctrl->status) return map_status(g, g->h_ctrl->status);
     }
     return MN_OK;
+}
+
+// The autotuner's candidate launch configurations, at the occupancy limit of
+// resident blocks per SM (the kernel is latency-bound): split threshold x
+// split depth x learned pre-split threshold (off, or seeds predicted above
+// 2^20 / 2^22 SM cycles; it acts only under MN_ORDER_LEARNED).
+void build_tune_candidates(mn_graph *g)
+{
+    g->tune_cfgs.clear();
+    const uint32_t b = (uint32_t)g->enum_max_per_sm;
+    for (uint32_t sm : {40u, 64u, 128u})
+        for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE})
+            for (float th : {INFINITY, 20.f, 22.f}) g->tune_cfgs.push_back({b, sm, sd, th});
 }
 
 }  // namespace
@@ -918,6 +1000,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
                 g->enum_grid = g->nsm * (int)c.bps;
                 g->split_min = c.split_min;
                 g->split_depth = c.split_depth;
+                g->presplit_log2 = c.presplit_log2;
                 g->tuning = false;
             }
         }
@@ -949,6 +1032,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     }
     g->batch_id++;
     g->stats.batches++;
+    if (!count_only && est == MN_OK) note_rates(g, n, x);
     fill_result(g, out, seq_lo, hi_new, ex_lo, ex_lo + x);
     if (est == MN_ERR_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, timeout_msg);
     if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
@@ -1276,6 +1360,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         g->enum_grid = g->nsm * (int)c.bps;
         g->split_min = c.split_min;
         g->split_depth = c.split_depth;
+        g->presplit_log2 = c.presplit_log2;
         CK(cudaEventRecord(g->tune_e0, g->stream));
     }
     // the adjacency enumerated holds seqs from `base` on: the new buffer was
@@ -1298,6 +1383,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     if (nph && g->policy != MN_ORDER_PAPER)
         TRY(ensure_learn_rows(g, std::max(g->seed_cap[0], g->seed_cap[1])));
     for (int k = 0; k < nph; k++) TRY(choose_orders(g, ph[k].phase));
+    if (nph && !count_only) TRY(presize_outputs(g, n, x));
     if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
     for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
     if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
@@ -1459,10 +1545,12 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
 namespace {
 
 // Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status and seed
-// count (u32 each), [4, 8) work counters, [8, 200) counts, [256, 336)
-// scheduler words (one 128-byte line each), [384, 384 + MN_NOALLOC_MAX_SEEDS)
-// seeds.
-constexpr uint32_t NA_WORK = 4, NA_COUNTS = 8, NA_SCHED = 256, NA_SEEDS = 384;
+// count (u32 each), [4, 10) the enumerator's six work counters, [16, 208)
+// counts (3 per query, 64 queries), [256, 336) scheduler words (one 128-byte
+// line each), [384, 384 + MN_NOALLOC_MAX_SEEDS) seeds.
+constexpr uint32_t NA_WORK = 4, NA_COUNTS = 16, NA_SCHED = 256, NA_SEEDS = 384;
+static_assert(NA_WORK + 6 <= NA_COUNTS, "work counters overlap the counts");
+static_assert(NA_COUNTS + 3 * 64 <= NA_SCHED, "counts overlap the scheduler words");
 static_assert(NA_SCHED * 8 + sizeof(Sched) <= NA_SEEDS * 8, "scheduler words overlap the seeds");
 constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
 static __device__ __align__(256) unsigned long long mn_noalloc_scratch[NA_WORDS];
@@ -1543,6 +1631,9 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     p.max_iters = g->max_iters;
     p.status = &ctl[0];
     p.work = base + NA_WORK;
+    p.wait_polls = g->wait_polls;
+    p.qrun[0] = p.qrun[1] = ~0ull;
+    CK(cudaFuncSetAttribute(k_enumerate, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
     k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     uint32_t st = 0;
@@ -1807,16 +1898,25 @@ mn_status mn_dual_simulation(mn_graph *g, uint32_t query_id, uint32_t *sim, uint
     k_dualsim_init<<<grid, 256, 0, g->stream>>>(p);
     CKL();
     // refine until a pass removes nothing (each pass that changes anything
-    // removes a pair, so V * nv + 1 passes bound the loop)
+    // removes a pair, so V * nv + 1 passes bound the loop); DS_PASSES passes
+    // per host check: the changed flag is sticky over a group (a pass after
+    // the fixpoint changes nothing, so the extra passes are harmless)
+    constexpr uint32_t DS_PASSES = 8;
     uint32_t changed = 1;
-    for (uint64_t pass = 0; changed; pass++) {
-        if (pass > (uint64_t)g->V * Q.nv + 1) return fail(g, MN_ERR_DEVICE, "dual simulation did not settle");
+    uint64_t passes = 0;
+    while (changed) {
+        if (passes > (uint64_t)g->V * Q.nv + DS_PASSES)
+            return fail(g, MN_ERR_DEVICE, "dual simulation did not settle");
         CK(cudaMemsetAsync(p.flags, 0, sizeof(uint32_t), g->stream));
-        k_dualsim_pass<<<grid, 256, 0, g->stream>>>(p);
-        CKL();
+        for (uint32_t k = 0; k < DS_PASSES; k++) {
+            k_dualsim_pass<<<grid, 256, 0, g->stream>>>(p);
+            CKL();
+        }
+        passes += DS_PASSES;
         CK(cudaMemcpyAsync(&changed, p.flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
     }
+    g->stats.dualsim_passes += passes;
     CK(cudaMemsetAsync(g->d_simctl, 0, 2 * sizeof(unsigned long long), g->stream));
     k_dualsim_summary<<<grid, 256, 0, g->stream>>>(p, d_pairs);
     CKL();
@@ -1860,12 +1960,7 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     CK(cudaSetDevice(g->device));
     if (!g->tune_e0) CK(cudaEventCreate(&g->tune_e0));
     if (!g->tune_e1) CK(cudaEventCreate(&g->tune_e1));
-    g->tune_cfgs.clear();
-    std::vector<uint32_t> bps = {(uint32_t)g->enum_max_per_sm};
-    if (g->enum_max_per_sm > 1) bps.push_back((uint32_t)g->enum_max_per_sm - 1u);
-    for (uint32_t b : bps)
-        for (uint32_t sm : {33u, 40u, 64u, 128u})
-            for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE}) g->tune_cfgs.push_back({b, sm, sd});
+    build_tune_candidates(g);
     g->tune_ms.assign(g->tune_cfgs.size(), 0.0);
     g->tune_work.assign(g->tune_cfgs.size(), 0.0);
     g->tune_per = std::max<uint32_t>(batches_per_config, 1);
@@ -1875,11 +1970,42 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     return MN_OK;
 }
 
+mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out, uint32_t *n)
+{
+    if (!g || !n) return fail(g, MN_ERR_INVALID_ARG, "NULL argument");
+    build_tune_candidates(g);
+    *n = (uint32_t)g->tune_cfgs.size();
+    for (uint32_t k = 0; k < *n && k < cap && out; k++) {
+        const auto &c = g->tune_cfgs[k];
+        out[k].blocks_per_sm = c.bps;
+        out[k].split_min = c.split_min;
+        out[k].split_depth = c.split_depth;
+        out[k].presplit_log2 = std::isinf(c.presplit_log2) ? 0.f : c.presplit_log2;
+    }
+    if (out && cap < *n) return fail(g, MN_ERR_INVALID_ARG, "array too small");
+    return MN_OK;
+}
+
+mn_status mn_set_presplit(mn_graph *g, float log2_cycles)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (std::isnan(log2_cycles)) return fail(g, MN_ERR_INVALID_ARG, "threshold is NaN");
+    g->presplit_log2 = log2_cycles > 0.f ? log2_cycles : INFINITY;
+    return MN_OK;
+}
+
 mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left)
 {
     if (!g) return MN_ERR_INVALID_ARG;
     if (active) *active = g->tuning ? 1 : 0;
     if (configs_left) *configs_left = g->tuning ? (uint32_t)(g->tune_cfgs.size() - g->tune_idx) : 0u;
+    return MN_OK;
+}
+
+mn_status mn_get_presplit(const mn_graph *g, float *log2_cycles)
+{
+    if (!g || !log2_cycles) return MN_ERR_INVALID_ARG;
+    *log2_cycles = std::isinf(g->presplit_log2) ? 0.f : g->presplit_log2;
     return MN_OK;
 }
 
@@ -1901,6 +2027,16 @@ mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters)
 {
     if (!g) return MN_ERR_INVALID_ARG;
     g->max_iters = max_iters ? max_iters : ~0ull;
+    return MN_OK;
+}
+
+mn_status mn_set_wait_limit(mn_graph *g, uint32_t max_polls, uint32_t flags)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (flags & ~MN_WAIT_HOLD) return fail(g, MN_ERR_INVALID_ARG, "unknown wait flags");
+    if (max_polls > (1u << 30)) return fail(g, MN_ERR_INVALID_ARG, "max_polls above 2^30");
+    g->wait_polls = max_polls ? max_polls : WAIT_POLLS;
+    g->wait_hold = (flags & MN_WAIT_HOLD) ? 1u : 0u;
     return MN_OK;
 }
 

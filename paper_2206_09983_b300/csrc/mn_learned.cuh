@@ -315,9 +315,11 @@ __global__ void k_adam(float *P, const float *G, float *M1, float *M2, int n, fl
 
 // Per seed: the candidate order with the smallest predicted cost, but the
 // paper's order (candidate 0) unless the best prediction beats it by at least
-// `margin` (log2 units): the paper's order is the fallback.
+// `margin` (log2 units): the paper's order is the fallback.  A seed whose
+// predicted cost under the chosen order is at least `split_log2` is flagged
+// for pre-splitting (SEED_PRESPLIT; split_log2 = +inf: never).
 __global__ void k_pick(unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
-                       const float *y, float margin)
+                       const float *y, float margin, float split_log2)
 {
     const uint32_t n = min(*nseeds, seed_cap);
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -328,8 +330,10 @@ __global__ void k_pick(unsigned long long *seeds, const uint32_t *nseeds, uint32
             const float v = y[(size_t)s * NCAND + k];
             if (v < bv) { bv = v; best = k; }
         }
-        if (bv > y0 - margin) best = 0;
-        seeds[s] = (seeds[s] & ~(0xffull << 24)) | ((unsigned long long)best << 24);
+        if (bv > y0 - margin) { best = 0; bv = y0; }
+        unsigned long long w = (seeds[s] & ~(0xffull << 24)) | ((unsigned long long)best << 24);
+        if (bv >= split_log2) w |= SEED_PRESPLIT;
+        seeds[s] = w;
     }
 }
 

@@ -41,8 +41,10 @@ EXPORTS = [
     "mn_set_order_policy", "mn_train_order_model", "mn_order_model_params", "mn_mlp_forward",
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
-    "mn_dual_simulation", "mn_last_error",
+    "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
+    "mn_autotune_candidates", "mn_last_error",
 ]
+MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
 MLP_PARAMS = 18817
 
@@ -80,10 +82,16 @@ class Stats(C.Structure):
                 ("ms_enumerate", C.c_double), ("ms_expire", C.c_double),
                 ("seeds", C.c_uint64), ("entries_scanned", C.c_uint64),
                 ("binds", C.c_uint64), ("records", C.c_uint64), ("busy_cycles", C.c_uint64), ("tasks_split", C.c_uint64),
-                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _TuneConfig(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_uint32), ("split_min", C.c_uint32), ("split_depth", C.c_uint32),
+                ("presplit_log2", C.c_float)]
 
 
 class _BatchResult(C.Structure):
@@ -143,6 +151,10 @@ def load(path: str | None = None):
         "mn_read_adjacency": (S, [P, C.c_uint32, U64, P, P, P, C.POINTER(U64)]),
         "mn_graph_info": (S, [P, C.POINTER(U64), C.POINTER(U64), C.POINTER(C.c_uint32)]),
         "mn_set_work_budget": (S, [P, U64]),
+        "mn_set_wait_limit": (S, [P, C.c_uint32, C.c_uint32]),
+        "mn_set_presplit": (S, [P, C.c_float]),
+        "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
+        "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_set_timing": (S, [P, C.c_int32]),
         "mn_get_stats": (S, [P, C.POINTER(Stats)]),
         "mn_reset_stats": (S, [P]),
@@ -405,6 +417,11 @@ class Graph:
     def set_work_budget(self, max_iters: int):
         self._check(self._lib.mn_set_work_budget(self._h, max_iters))
 
+    def set_wait_limit(self, max_polls: int = 0, hold: bool = False):
+        """Bound of the enumerator's idle wait (mn_set_wait_limit); hold is a
+        test hook that makes every idle wait run to its bound."""
+        self._check(self._lib.mn_set_wait_limit(self._h, max_polls, MN_WAIT_HOLD if hold else 0))
+
     def set_timing(self, on: bool):
         self._check(self._lib.mn_set_timing(self._h, 1 if on else 0))
 
@@ -436,6 +453,23 @@ class Graph:
     def autotune(self, batches_per_config: int = 1):
         self._check(self._lib.mn_autotune(self._h, batches_per_config))
 
+    def set_presplit(self, log2_cycles: float):
+        """Learned pre-splitting threshold in log2 predicted SM cycles (0 = off)."""
+        self._check(self._lib.mn_set_presplit(self._h, log2_cycles))
+
+    def get_presplit(self) -> float:
+        v = C.c_float()
+        self._check(self._lib.mn_get_presplit(self._h, C.byref(v)))
+        return v.value
+
+    def autotune_candidates(self):
+        """The autotuner's candidates: (blocks_per_sm, split_min, split_depth, presplit_log2)."""
+        n = C.c_uint32()
+        self._check(self._lib.mn_autotune_candidates(self._h, 0, None, C.byref(n)))
+        arr = (_TuneConfig * max(1, n.value))()
+        self._check(self._lib.mn_autotune_candidates(self._h, n.value, arr, C.byref(n)))
+        return [(c.blocks_per_sm, c.split_min, c.split_depth, c.presplit_log2) for c in arr[:n.value]]
+
     def autotune_state(self):
         a, left = C.c_int32(), C.c_uint32()
         self._check(self._lib.mn_autotune_state(self._h, C.byref(a), C.byref(left)))
@@ -444,8 +478,10 @@ class Graph:
     def get_tuning(self) -> dict:
         v = [C.c_uint32() for _ in range(4)] + [C.c_int32()]
         self._check(self._lib.mn_get_tuning(self._h, *[C.byref(x) for x in v]))
-        return dict(zip(("blocks_per_sm", "max_blocks_per_sm", "split_min", "split_depth",
-                         "smem_carveout"), [x.value for x in v]))
+        d = dict(zip(("blocks_per_sm", "max_blocks_per_sm", "split_min", "split_depth",
+                      "smem_carveout"), [x.value for x in v]))
+        d["presplit_log2"] = self.get_presplit()
+        return d
 
     def reset_stats(self):
         self._check(self._lib.mn_reset_stats(self._h))
