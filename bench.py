@@ -128,7 +128,10 @@ def measured_peaks():
 
 def oracle_sample(stream, queries, W, B, batch_index, sample, seed=7):
     """Time the CPU oracle on `sample` edges of one batch of the window
-    stream: dS+ (embeddings containing a sampled new edge) for every query."""
+    stream: |dS+| (embeddings containing a sampled new edge, each counted at
+    its first sampled edge) of every query, the seeds spread over all host
+    cores with OpenMP (the paper's CPU design point).  Returns (seconds,
+    embeddings, threads)."""
     from oracle import oracle
     lo = batch_index * B
     hi_new = lo + W + B
@@ -136,11 +139,19 @@ def oracle_sample(stream, queries, W, B, batch_index, sample, seed=7):
     pick = rng.choice(B, size=sample, replace=False)
     mask = np.zeros(hi_new - lo, dtype=np.uint8)
     mask[W + pick] = 1
+    threads = oracle.max_threads()
     t = time.perf_counter()
     rows = 0
     for q in queries:
-        rows += len(oracle.delta(stream, lo, hi_new, 0, 0, q, batch_mask=mask))
-    return time.perf_counter() - t, rows
+        rows += oracle.delta_count_parallel(stream, lo, hi_new, q, mask, 0)
+    return time.perf_counter() - t, rows, threads
+
+
+def oracle_sample_size(B):
+    """Sampled edges per batch: 256 per host core, so a step takes a few
+    seconds whatever the core count."""
+    from oracle import oracle
+    return min(B, 256 * oracle.max_threads())
 
 
 def run_reference(args, rank, world):
@@ -151,12 +162,13 @@ def run_reference(args, rank, world):
     W, B = w["window"], w["batch"]
     stream = workloads.rmat20_stream()
     qs = workloads.rmat20_queries()
-    times, edges = [], 0
+    sample = args.ref_sample or oracle_sample_size(B)
+    times, edges, threads = [], 0, 1
     for k in range(args.warmup + args.steps):
-        dt, _ = oracle_sample(stream, qs, W, B, k, args.ref_sample)
+        dt, _, threads = oracle_sample(stream, qs, W, B, k, sample)
         if k >= args.warmup:
             times.append(dt)
-            edges += args.ref_sample
+            edges += sample
     total = sum(times)
     value = edges / total
     line = {
@@ -166,10 +178,10 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": w["name"], "vertices": 1 << w["scale"], "window": W, "batch": B,
                    "queries": workloads.QUERY_NAMES},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.ref_sample} random inserted edges per batch (dS+ of all 4 "
-                                   f"queries, adjacency rebuild included), batches {args.warmup}.."
-                                   f"{args.warmup + args.steps - 1} of the window stream"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} random inserted edges per batch (|dS+| of all 4 queries, "
+                                   f"seeds over {threads} OpenMP threads, adjacency rebuild included), "
+                                   f"batches {args.warmup}..{args.warmup + args.steps - 1} of the window stream"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -253,8 +265,8 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-sample", type=int, default=256)
-    ap.add_argument("--cpu-sample", type=int, default=512)
+    ap.add_argument("--ref-sample", type=int, default=0, help="edges per batch (0: 256 per core)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="edges (0: 256 per core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--train-epochs", type=int, default=300)
@@ -436,22 +448,39 @@ def main():
     peak, peak_kind = measured_peaks()
     stage_ms = {"enumerate": st["ms_enumerate"], "adjacency": st["ms_adjacency"],
                 "ingest": st["ms_ingest"], "seeds": st["ms_seeds"], "expire": st["ms_expire"]}
-    rec_bytes = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
-    enum_bytes = (st["entries_scanned"] * 12 + st["records"] * (sum(rec_bytes) / len(rec_bytes))
-                  + st["seeds"] * 16)
+    # Algorithmic bytes of the enumerator (the method's traffic, counted from
+    # the device work counters): per tested adjacency entry 8 B (neighbour,
+    # seq) + 4 B DEBI word + 8 B timestamp when the query is temporal; per
+    # record 4 n_q + 8 k_q; per seed 8 B seed word + 8 B ring endpoints.
+    temporal = all(q["temporal"] != "none" for q in qs)
+    entry_bytes = 20 if temporal else 12
+    rec_alg = [4 * q["nv"] + 8 * len(q["edges"]) for q in qs]
+    rec_layout = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
+    rec_sum_alg = sum(sum((a[i] + b[i]) * rec_alg[i] for i in range(len(qs))) for a, b in per_q)
+    rec_sum_layout = sum(sum((a[i] + b[i]) * rec_layout[i] for i in range(len(qs))) for a, b in per_q)
     launches = max(1, st["enumerate_launches"])
+    enum_bytes = st["entries_scanned"] * entry_bytes + rec_sum_alg + st["seeds"] * 16
     enum_ms_per = st["ms_enumerate"] / launches
     roof = {"kernel": "k_enumerate", "bound": "hbm",
             "achieved": (enum_bytes / launches) / (enum_ms_per / 1e3) / 1e9 if enum_ms_per else None,
             "peak": peak, "unit": "GB/s", "traffic": enum_traffic(),
-            "peak_source": f"{peak_kind} HBM copy bandwidth",
-            "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per}
+            "peak_source": f"{peak_kind} HBM copy bandwidth (burst figure: the kernel is timed alone per launch)",
+            "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per,
+            "entry_bytes": entry_bytes,
+            "launches_per_batch": st["enumerate_launches"] / K,
+            "rerun_launches_per_batch": st.get("rerun_launches", 0) / K,
+            "counting": (f"entries tested x {entry_bytes} B (8 B entry + 4 B DEBI word"
+                         f"{' + 8 B timestamp: every query is temporal' if temporal else ''}) + records x "
+                         f"(4 n_q + 8 k_q) + seeds x 16 B")}
     roof["frac"] = roof["achieved"] / peak if roof["achieved"] else None
+    # the same with the device's own layout (12 B per entry: neighbour, seq32,
+    # DEBI word; records padded to 8 bytes), for comparison
+    layout_bytes = st["entries_scanned"] * 12 + rec_sum_layout + st["seeds"] * 16
+    roof["layout_bytes_per_launch"] = layout_bytes / launches
     # sector-granular variant: every random touch rounded up to a 32-byte
     # sector (an upper estimate: each tested entry's DEBI word as one touch,
     # each seed's ring endpoints as two)
-    sector_bytes = (st["entries_scanned"] * (8 + 32) + st["records"] * (sum(rec_bytes) / len(rec_bytes))
-                    + st["seeds"] * (8 + 64))
+    sector_bytes = st["entries_scanned"] * (8 + 32) + rec_sum_layout + st["seeds"] * (8 + 64)
     roof["sector_bytes_per_launch"] = sector_bytes / launches
     roof["sector_achieved"] = ((sector_bytes / launches) / (enum_ms_per / 1e3) / 1e9
                                if enum_ms_per else None)
@@ -459,11 +488,16 @@ def main():
     tu = learned.get("tuning_used") or {}
     enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * ENUM_WARPS_PER_BLOCK
                   * max(1, tu.get("blocks_per_sm", 2)))
-    adj_bytes_per_batch = 2 * (2 * (W + B) * 12)     # read + write of both directions' entries
+    # adjacency update: the method's bytes are 2 x 8 B per inserted edge (one
+    # entry per direction); the implementation rewrites the live window's
+    # four sorted orders (out/in x by neighbour/by arrival, 12 B per entry),
+    # read and written once per batch
+    adj_alg = 16 * B
+    adj_layout = 4 * 2 * (W + B) * 12
     adj = {"kernel": "adjacency update (sort+compact+merge+offsets)",
            "ms_per_batch": st["ms_adjacency"] / K,
-           "achieved": adj_bytes_per_batch / (st["ms_adjacency"] / K / 1e3) / 1e9 if st["ms_adjacency"] else None,
-           "unit": "GB/s", "bytes_per_batch": adj_bytes_per_batch}
+           "achieved_layout": adj_layout / (st["ms_adjacency"] / K / 1e3) / 1e9 if st["ms_adjacency"] else None,
+           "unit": "GB/s", "algorithmic_bytes_per_batch": adj_alg, "layout_bytes_per_batch": adj_layout}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": WU,
@@ -510,12 +544,14 @@ def main():
     }
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, rows = oracle_sample(stream, qs, W, B, (pos - W) // B - 1, args.cpu_sample)
+        sample = args.cpu_sample or oracle_sample_size(B)
+        bi = (pos - W) // B - 1
+        dt, rows, threads = oracle_sample(stream, qs, W, B, bi, sample)
         line["cpu_baseline"] = {
-            "value": args.cpu_sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{args.cpu_sample} random inserted edges of one batch, dS+ of all {nq} "
-                      f"queries on the {W}-edge window (adjacency rebuild included), "
-                      f"single-threaded C oracle; {rows} embeddings, {dt:.1f} s"}
+            "value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sample} random inserted edges of batch {bi}, |dS+| of all {nq} queries on the "
+                      f"{W}-edge window (adjacency rebuild included), C oracle with the seeds over "
+                      f"{threads} OpenMP threads; {rows} embeddings, {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

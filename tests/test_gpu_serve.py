@@ -97,3 +97,42 @@ def test_results_same_alone_and_in_the_mix():
     # the other tenants' requests all completed too
     assert all(not r.error for name in ("b", "c") for _, _, r in mixed[name])
     assert srv.latency_ms()["n"] == sum(len(v) for v in mixed.values())
+
+
+def test_merged_requests_equal_the_oracle_for_the_concatenated_batch():
+    """merge=True (the mode the serving benchmark runs): requests that queue
+    while the tenant's previous batch is on the GPU are admitted together as
+    one device batch; every request of a merged group reports that batch's
+    result, which must equal the oracle's dS+ / dS- for the concatenated
+    edges under the count window."""
+    s, qs, W = tenant_a()
+    g = make(s, qs, W)
+    srv = Server(mem_budget_bytes=64 << 20, merge=True, max_batch=1500)
+    srv.add_tenant("a", g, keep_rows=True)
+    plan = [(lo, min(len(s["src"]), lo + 150)) for lo in range(0, len(s["src"]), 150)]
+    reqs = [srv.submit("a", M.edges_from_stream(s, lo, hi)) for lo, hi in plan]
+    srv.drain()
+    srv.close()
+    g.close()
+    assert all(not r.error for r in reqs)
+    assert max(r.merged_with for r in reqs) > 1, "no requests were merged"
+    # device batches: consecutive requests sharing a batch id, in arrival order
+    groups = []
+    for (lo, hi), r in zip(plan, reqs):
+        if groups and groups[-1][2].batch_id == r.batch_id:
+            groups[-1][1] = hi
+            groups[-1][3] += 1
+        else:
+            groups.append([lo, hi, r, 1])
+    assert sum(gr[3] for gr in groups) == len(reqs)
+    lo_w = 0
+    for lo, hi, r, n_req in groups:
+        assert r.merged_with == n_req
+        x = max(0, hi - lo_w - W)
+        for qi, q in enumerate(qs):
+            pos = oracle.delta(s, lo_w, hi, lo, hi, q)
+            neg = oracle.delta(s, lo_w, hi, lo_w, lo_w + x, q)
+            assert r.count_pos[qi] == len(pos) and r.count_neg[qi] == len(neg)
+            assert len(r.rows_pos[qi]) == len(pos) and (r.rows_pos[qi] == pos).all()
+            assert len(r.rows_neg[qi]) == len(neg) and (r.rows_neg[qi] == neg).all()
+        lo_w += x
