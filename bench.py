@@ -273,6 +273,10 @@ def main():
     ap.add_argument("--plain-only", action="store_true", help="time only the plain arm (diagnostics)")
     ap.add_argument("--tuning", default="", help="blocks_per_sm,split_min,split_depth for both arms")
     ap.add_argument("--mode", default="bench", choices=["bench", "serve"])
+    ap.add_argument("--workload", default="rmat20_window", choices=["rmat20_window", "rmat20_uneven"])
+    ap.add_argument("--with-uneven", dest="with_uneven", action="store_true", default=True,
+                    help="also time the 36-query batched workload on the same stream (the default)")
+    ap.add_argument("--no-uneven", dest="with_uneven", action="store_false")
     ap.add_argument("--serve-rate", type=float, default=4.0e5, help="offered load, edges/s")
     ap.add_argument("--serve-edges", type=int, default=6_000_000)
     ap.add_argument("--serve-order", default="learned", choices=["learned", "paper"])
@@ -303,18 +307,55 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    w = workloads.RMAT20
-    W, B = w["window"], w["batch"]
-    K, WU = args.steps, max(3, args.warmup)
-    need = W + B * (2 * (WU + K) + 2 + 16)   # warm-up, autotuning, timed, end-to-end batches
     stream = workloads.rmat20_stream()
-    n = len(stream["src"])
-    assert n >= need, "stream too short for the requested steps"
-    packed = M.edges_from_stream(stream, 0, n)
+    packed = M.edges_from_stream(stream, 0, len(stream["src"]))
     d_edges = torch.from_numpy(packed.view(np.uint8)).to(dev)
-    base_ptr = d_edges.data_ptr()
-    qs = workloads.rmat20_queries()
-    cur_stream = torch.cuda.current_stream(dev)
+    ctx = dict(torch=torch, M=M, dev=dev, local=local, rank=rank, world=world, stream=stream,
+               packed=packed, base_ptr=d_edges.data_ptr(), cur_stream=torch.cuda.current_stream(dev))
+    main_wl = workloads.WORKLOADS[args.workload]
+    res = run_workload(args, ctx, main_wl, with_e2e=not args.no_e2e)
+    line = res["line"]
+    if args.with_uneven and args.workload != "rmat20_uneven":
+        # the batched-uneven-queries workload on the same stream, both arms
+        extra = run_workload(args, ctx, workloads.WORKLOADS["rmat20_uneven"], with_e2e=False)["line"]
+        line["batched_uneven"] = {k: extra[k] for k in (
+            "value", "unit", "ms_per_step", "config", "plain", "learned_vs_plain", "latency_ms",
+            "embeddings_per_step", "stage_ms_per_step", "work_per_step", "roofline", "tuning", "train",
+            "clocks")}
+        line["gpu_launches"] += extra["gpu_launches"]
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        W, B = main_wl["window"], main_wl["batch"]
+        qs = main_wl["queries"]()
+        sample = args.cpu_sample or oracle_sample_size(B) * 4 // max(4, len(qs))
+        bi = (res["pos"] - W) // B - 1
+        dt, rows, threads = oracle_sample(stream, qs, W, B, bi, sample)
+        line["cpu_baseline"] = {
+            "value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{sample} random inserted edges of batch {bi}, |dS+| of all {len(qs)} queries on the "
+                      f"{W}-edge window (adjacency rebuild included), C oracle with the seeds over "
+                      f"{threads} OpenMP threads; {rows} embeddings, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_workload(args, ctx, wl, with_e2e):
+    """Both arms of one workload on the shared device-resident stream: the
+    learned + autotuned arm (timed first; its end-to-end leg through host
+    memory) and the plain GPU path (paper order, default launch parameters)
+    on the same batches.  Returns the bench line of the learned arm with the
+    plain arm beside it."""
+    torch, M, dev, local = ctx["torch"], ctx["M"], ctx["dev"], ctx["local"]
+    rank, world, stream, packed = ctx["rank"], ctx["world"], ctx["stream"], ctx["packed"]
+    base_ptr, cur_stream = ctx["base_ptr"], ctx["cur_stream"]
+    W, B = wl["window"], wl["batch"]
+    K, WU = args.steps, max(3, args.warmup)
+    qs = wl["queries"]()
+    names = wl["query_names"]()
+    n = len(stream["src"])
 
     def barrier():
         if world > 1:
@@ -327,13 +368,12 @@ def main():
         timed batches, then the end-to-end run."""
         g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
                     window=W, max_batch=B, max_queries=len(qs), device=local,
-                    stream=cur_stream.cuda_stream, out_capacity=1 << 21)
+                    stream=cur_stream.cuda_stream, out_capacity=wl["out_capacity"])
         if world > 1:
             g.set_shard(rank, world)                             # this rank's part of the seeds
         res = {}
         if args.tuning:
             g.set_tuning(*[int(x) for x in args.tuning.split(",")])
-        res["tuning"] = g.get_tuning()
         for lo in range(0, W, B):                               # preload the window
             g.insert(None, device_ptr=base_ptr + 24 * lo, n=B, count_only=True)
         for q in qs:
@@ -359,6 +399,7 @@ def main():
             for _ in range(skip):                                # same batches as the learned arm
                 g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
                 pos += B
+        assert pos + B * (K + (WU + K if with_e2e else 0)) <= n, "stream too short for the requested steps"
         g.set_timing(True)
         g.reset_stats()
         barrier()
@@ -417,14 +458,14 @@ def main():
         return res
 
     if args.plain_only:
-        plain = learned = arm("paper", with_e2e=not args.no_e2e)
+        plain = learned = arm("paper", with_e2e=with_e2e)
     else:
-        learned = arm("learned", with_e2e=not args.no_e2e)
+        learned = arm("learned", with_e2e=with_e2e)
         plain = arm("paper", with_e2e=False, skip=learned.get("tune_batches", 0))
     for k in range(K):                                  # exact counts: both arms agree
         assert plain["per_q"][k] == learned["per_q"][k], "learned and plain counts differ"
     dev_ms, lat, counts, per_q, st = (learned[k] for k in ("dev_ms", "lat", "counts", "per_q", "st"))
-    clocks, e2e, pos = learned["clocks"], learned["e2e"], learned["pos"]
+    clocks, e2e = learned["clocks"], learned["e2e"]
 
     # ---- aggregate over ranks (max time)
     dev_s = dev_ms / 1e3
@@ -463,7 +504,7 @@ def main():
     enum_ms_per = st["ms_enumerate"] / launches
     roof = {"kernel": "k_enumerate", "bound": "hbm",
             "achieved": (enum_bytes / launches) / (enum_ms_per / 1e3) / 1e9 if enum_ms_per else None,
-            "peak": peak, "unit": "GB/s", "traffic": enum_traffic(),
+            "peak": peak, "unit": "GB/s", "traffic": enum_traffic() if wl["name"] == "rmat20_window" else None,
             "peak_source": f"{peak_kind} HBM copy bandwidth (burst figure: the kernel is timed alone per launch)",
             "bytes_per_launch": enum_bytes / launches, "ms_per_launch": enum_ms_per,
             "entry_bytes": entry_bytes,
@@ -484,7 +525,6 @@ def main():
     roof["sector_bytes_per_launch"] = sector_bytes / launches
     roof["sector_achieved"] = ((sector_bytes / launches) / (enum_ms_per / 1e3) / 1e9
                                if enum_ms_per else None)
-    nq = len(qs)
     tu = learned.get("tuning_used") or {}
     enum_warps = (torch.cuda.get_device_properties(dev).multi_processor_count * ENUM_WARPS_PER_BLOCK
                   * max(1, tu.get("blocks_per_sm", 2)))
@@ -503,17 +543,18 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": WU,
         "ms_per_step": 1e3 * dev_s / K, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": w["name"], "vertices": 1 << w["scale"], "edges": w["num_edges"],
-                   "window": W, "batch": B, "queries": workloads.QUERY_NAMES,
+        "config": {"workload": wl["name"], "vertices": stream["num_vertices"], "edges": n,
+                   "window": W, "batch": B, "queries": names if len(names) <= 8 else f"{len(names)} queries",
                    "semantics": "isomorphism, increasing timestamps", "l2": CTRL_NOTE,
                    "parallelism": (f"seed-sharded over {world} GPUs (each ingests the whole stream)"
                                    if world > 1 else "1 GPU"),
-                   "path": "learned matching order (value) vs plain GPU path with the paper's order"},
+                   "path": "learned matching order + learned splits + autotuned launch (value) vs plain "
+                           "GPU path with the paper's order"},
         "plain": {"value": K * B / (plain["dev_ms"] / 1e3), "unit": UNIT,
                   "ms_per_step": plain["dev_ms"] / K,
                   "latency_ms": {"p50": 1e3 * statistics.median(plain["lat"]),
                                  "p99": 1e3 * float(np.percentile(plain["lat"], 99))},
-                  "work_per_step": {k: plain["st"][k] / K for k in ("entries_scanned", "binds")},
+                  "work_per_step": {k: plain["st"][k] / K for k in ("entries_scanned", "binds", "tasks_split")},
                   "stage_ms_per_step": {"enumerate": plain["st"]["ms_enumerate"] / K,
                                         "adjacency": plain["st"]["ms_adjacency"] / K},
                   "clocks": plain["clocks"]},
@@ -527,7 +568,7 @@ def main():
         "embeddings_per_step_by_query": {
             name: {"new": float(np.mean([c[0][i] for c in per_q])),
                    "removed": float(np.mean([c[1][i] for c in per_q]))}
-            for i, name in enumerate(workloads.QUERY_NAMES)},
+            for i, name in enumerate(names)},
         "stage_ms_per_step": {k: v / K for k, v in stage_ms.items()},
         "work_per_step": {k: st[k] / K for k in ("seeds", "entries_scanned", "binds", "records",
                                                   "tasks_split")},
@@ -542,22 +583,7 @@ def main():
         "clocks": clocks,
         "e2e": e2e,
     }
-
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = args.cpu_sample or oracle_sample_size(B)
-        bi = (pos - W) // B - 1
-        dt, rows, threads = oracle_sample(stream, qs, W, B, bi, sample)
-        line["cpu_baseline"] = {
-            "value": sample / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{sample} random inserted edges of batch {bi}, |dS+| of all {nq} queries on the "
-                      f"{W}-edge window (adjacency rebuild included), C oracle with the seeds over "
-                      f"{threads} OpenMP threads; {rows} embeddings, {dt:.1f} s"}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    return 0
+    return {"line": line, "pos": learned["pos"]}
 
 
 if __name__ == "__main__":

@@ -65,3 +65,76 @@ def rmat20_queries(labels: dict | None = None) -> list:
 
 
 QUERY_NAMES = ["path4", "cycle4", "star5", "tree6"]
+
+
+def c3_query(nv, edges, elabels, vlabels):
+    """One query of the batched-queries workload: the given shape and labels,
+    isomorphism, timestamps increasing along the query edges."""
+    return gen.make_query(nv, [(s, d, int(l)) for (s, d), l in zip(edges, elabels)], _vm(vlabels),
+                          iso=True, temporal="chain")
+
+
+# The 32 uneven queries of the batched-queries workload (index, n_q, edges,
+# edge labels, vertex labels; the comment is the oracle's exact |dS+| of the
+# first batch after the preloaded window), from the oracle-driven search in
+# tests/golden/calibrate_rmat20_c3.py: random trees (even index) and cycles
+# with 1-2 chords (odd index) of 3-8 vertices, labels drawn so that the first
+# batch's |dS+| lies in [2^11, 2^17].  Every tree reached that range; under
+# the temporal chain the chorded cycles either explode or have very few
+# embeddings, and the search kept the largest count it could certify (0 to
+# 5,997 new embeddings per batch): uneven queries by construction.
+RMAT20_C3_QUERIES = [
+    (0, 6, [(1, 0), (1, 2), (3, 0), (4, 0), (5, 0)], [7, 7, 6, 7, 7], [0, 3, 0, 0, 3, 3]),  # 10442
+    (1, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (0, 4), (2, 5)], [6, 5, 6, 1, 3, 4, 6, 6, 1], [None, 1, 1, 2, 1, 2, 2]),  # 0
+    (2, 4, [(0, 1), (0, 2), (2, 3)], [0, 7, 5], [1, 3, 1, 2]),  # 9118
+    (3, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (2, 0)], [2, 4, 0, 0, 0], [None, None, 3, 2]),  # 4637
+    (4, 7, [(0, 1), (2, 1), (1, 3), (0, 4), (1, 5), (6, 3)], [7, 2, 7, 5, 7, 5], [1, 1, 2, 1, 1, 0, 3]),  # 68644
+    (5, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2), (3, 1)], [2, 1, 0, 4, 4, 3], [2, 0, 3, 0]),  # 3
+    (6, 7, [(1, 0), (1, 2), (0, 3), (4, 3), (3, 5), (4, 6)], [5, 6, 7, 5, 5, 2], [0, 2, 3, 2, 2, 0, 1]),  # 70543
+    (7, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (3, 1)], [3, 5, 0, 0, 1], [2, None, 0, 2]),  # 77
+    (8, 5, [(0, 1), (2, 0), (3, 1), (2, 4)], [4, 2, 2, 2], [3, 0, 3, 2, 2]),  # 108316
+    (9, 8, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (7, 0), (6, 3)], [2, 7, 4, 4, 6, 0, 5, 7, 2], [2, 2, 2, 1, 1, 0, 0, 0]),  # 0
+    (10, 6, [(0, 1), (0, 2), (3, 2), (4, 1), (1, 5)], [6, 1, 7, 3, 4], [1, 1, 1, 3, 3, 2]),  # 49974
+    (11, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (2, 0), (3, 6)], [6, 6, 7, 1, 4, 6, 0, 7, 7], [3, 1, 0, 3, 2, 1, 2]),  # 0
+    (12, 8, [(1, 0), (2, 0), (3, 2), (3, 4), (5, 0), (6, 1), (7, 0)], [6, 6, 4, 7, 4, 6, 4], [2, 1, 1, 0, 3, 3, 0, 3]),  # 88714
+    (13, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (2, 0), (1, 3)], [4, 2, 2, 0, 3, 3], [None, 2, 2, 0]),  # 4
+    (14, 4, [(0, 1), (2, 0), (3, 2)], [5, 6, 1], [2, 2, None, 0]),  # 40888
+    (15, 5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 3), (4, 1)], [7, 2, 1, 5, 6, 0, 2], [3, 1, 2, 1, 2]),  # 4
+    (16, 7, [(1, 0), (2, 0), (1, 3), (4, 3), (5, 4), (6, 0)], [7, 6, 7, 5, 7, 2], [3, 1, 1, 1, 1, 1, 2]),  # 81793
+    (17, 5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (3, 0)], [3, 7, 5, 0, 4, 6], [3, 2, 3, 2, None]),  # 182
+    (18, 4, [(0, 1), (1, 2), (3, 0)], [5, 1, 3], [1, 1, 3, 1]),  # 9266
+    (19, 3, [(0, 1), (1, 2), (2, 0)], [-1, 0, 0], [None, 1, 2]),  # 5997
+    (20, 4, [(0, 1), (2, 1), (3, 2)], [3, 7, 5], [1, None, None, 1]),  # 58778
+    (21, 8, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (7, 0), (6, 2)], [1, 7, 4, 5, 3, 1, 5, 6, 2], [1, 3, 1, 0, 2, 0, 1, 3]),  # 1
+    (22, 6, [(1, 0), (0, 2), (1, 3), (0, 4), (5, 4)], [7, 5, 2, 4, 2], [1, 2, 1, 2, 2, 0]),  # 108162
+    (23, 5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 3)], [4, 2, 3, 3, 1, 0], [2, None, 0, 0, None]),  # 314
+    (24, 4, [(1, 0), (2, 1), (3, 0)], [3, 3, 4], [2, 3, 3, None]),  # 49379
+    (25, 3, [(0, 1), (1, 2), (2, 0)], [1, 0, 0], [2, None, None]),  # 5227
+    (26, 3, [(0, 1), (0, 2)], [1, 1], [3, 0, 3]),  # 21793
+    (27, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (3, 6), (5, 1)], [7, 1, 5, 6, 5, 6, 3, 7, 5], [1, 1, 3, 0, 3, 1, None]),  # 0
+    (28, 6, [(1, 0), (2, 0), (2, 3), (4, 0), (2, 5)], [5, 7, 5, 6, 7], [1, 0, 3, 3, 0, 3]),  # 105042
+    (29, 3, [(0, 1), (1, 2), (2, 0)], [0, 0, 0], [3, 0, None]),  # 3993
+    (30, 5, [(1, 0), (1, 2), (2, 3), (4, 3)], [3, 3, 3, 6], [1, 3, None, 0, 1]),  # 96870
+    (31, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (2, 5), (3, 0)], [7, 4, 7, 7, 5, 1, 7, 6, 1], [None, 3, 2, 1, 2, 3, 0]),  # 0
+]
+
+
+def rmat20_c3_queries() -> list:
+    return [c3_query(nv, edges, el, vl) for _, nv, edges, el, vl in RMAT20_C3_QUERIES]
+
+
+def rmat20_c3_names() -> list:
+    return [f"q{i}_{'tree' if i % 2 == 0 else 'cycle'}{nv}" for i, nv, *_ in RMAT20_C3_QUERIES]
+
+
+# Benchmark workloads on the rmat20 stream: the four config-2 queries, and
+# the batched uneven queries (the 32 above plus the four) in one graph.
+WORKLOADS = {
+    "rmat20_window": dict(name="rmat20_window", window=RMAT20["window"], batch=RMAT20["batch"],
+                          queries=rmat20_queries, query_names=lambda: list(QUERY_NAMES),
+                          out_capacity=1 << 21),
+    "rmat20_uneven": dict(name="rmat20_uneven", window=RMAT20["window"], batch=RMAT20["batch"],
+                          queries=lambda: rmat20_c3_queries() + rmat20_queries(),
+                          query_names=lambda: rmat20_c3_names() + list(QUERY_NAMES),
+                          out_capacity=1 << 18),
+}

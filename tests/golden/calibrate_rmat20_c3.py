@@ -1,0 +1,165 @@
+"""Seeded rejection search for the labels of the 32 uneven queries of the
+batched-queries workload on the rmat20_window stream.
+
+Runs only the CPU oracle.  Query i (0..31) has n_q = U{3..8} vertices; even i
+is a random tree (random attachment, random directions), odd i a directed
+cycle of length n_q with 1-2 chords (no chords below 4 vertices); all under
+isomorphism with timestamps increasing along the query edges.  The shape of
+query i is drawn from its own seeded generator; its labels (edge labels from
+the stream's Zipf(1.2) frequencies over 8 labels, and per query vertex either
+one of the 4 vertex labels or "any", at a density that rises after a draw with
+too few embeddings and falls after one with too many: see draw_labels) are
+then redrawn until the oracle's
+|dS+| of the first batch after the preloaded window lies in [2^11, 2^17]:
+first estimated from 1,024 and 8,192 sampled batch edges (embeddings that
+contain a sampled edge, scaled to the batch), then counted exactly over the
+whole batch, each stage under a DFS node budget so that explosive draws are
+dropped early.  If no draw lands in range, the draw with the largest exact
+count below 2^17 is kept (at full density, the whole batch is counted
+exactly even when the samples found nothing).
+
+Usage: python tests/golden/calibrate_rmat20_c3.py [--jobs 8] [--redo-unaccepted]
+Prints the query table (paste into workloads.RMAT20_C3_QUERIES) and writes
+tests/golden/rmat20_c3_calibration.json (per query: shape, labels, exact
+first-batch count, trials).
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+from oracle import oracle                                  # noqa: E402
+from paper_2206_09983_b300 import gen, workloads          # noqa: E402
+
+LO_T, HI_T = 1 << 11, 1 << 17
+NQ = 32
+_S = None
+
+
+def shape(i):
+    rng = np.random.default_rng((0x4D4E0003, i))
+    nv = int(rng.integers(3, 9))
+    kind = "tree" if i % 2 == 0 else "cycle"
+    chords = int(rng.integers(1, 3)) if kind == "cycle" and nv >= 4 else 0
+    return nv, kind, gen.random_shape(rng, nv, kind, chords)
+
+
+def _init():
+    global _S
+    _S = workloads.rmat20_stream()
+
+
+def _count(q, W, B, sample, rng, budget):
+    if sample >= B:
+        pick = np.arange(B)
+    else:
+        pick = rng.choice(B, size=sample, replace=False)
+    mask = np.zeros(W + B, dtype=np.uint8)
+    mask[W + pick] = 1
+    cnt, complete = oracle.delta_count_budget(_S, 0, W + B, q, mask, budget)
+    return (cnt * B / len(pick) if complete else None), cnt, complete
+
+
+def draw_labels(rng, w, ne, nv, temp):
+    """Edge and vertex labels at density temp in [-1, 1]: edge labels from
+    weights (k + 1)^(-1.2 a) with a = 1 + 2 min(0, temp) (the stream's own
+    Zipf frequencies at temp >= 0, rare labels first as temp -> -1), a
+    wildcard edge label with probability max(0, temp), and an "any" vertex
+    label with probability (1 + temp) / 2."""
+    a = 1.0 + 2.0 * min(0.0, temp)
+    p = np.arange(1, w["elabels"] + 1, dtype=np.float64) ** (-w["label_zipf"] * a)
+    p /= p.sum()
+    el = [int(x) if rng.random() >= max(0.0, temp) else -1
+          for x in rng.choice(w["elabels"], size=ne, p=p)]
+    vl = [int(x) if rng.random() >= (1.0 + temp) / 2 else None
+          for x in rng.integers(0, w["vlabels"], size=nv)]
+    return el, vl
+
+
+def search(i, max_trials=400):
+    w = workloads.RMAT20
+    W, B = w["window"], w["batch"]
+    nv, kind, edges = shape(i)
+    rng = np.random.default_rng((0x4D4E0C03, i))
+    best = None
+    temp = 0.0
+    last = None
+    t0 = time.time()
+    for trial in range(max_trials):
+        el, vl = draw_labels(rng, w, len(edges), nv, temp)
+        q = workloads.c3_query(nv, edges, el, vl)
+        est, exact, verdict = None, None, "sparse"
+        for sample, budget in ((1024, 2 * 10**7), (8192, 2 * 10**8), (B, 2 * 10**9)):
+            est, cnt, complete = _count(q, W, B, sample, rng, budget)
+            if est is None or est > 8 * HI_T:
+                verdict = "dense"
+                break
+            if est == 0:
+                # as dense as labels go, or just below a draw that was too
+                # dense for the samples' budget: count the batch exactly
+                if temp >= 1.0 or last == "dense":
+                    est, cnt, complete = _count(q, W, B, B, rng, 5 * 10**8)
+                    if complete:
+                        exact = cnt
+                        verdict = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
+                break
+            if sample == B:
+                exact = cnt
+                verdict = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
+        if verdict == "ok":
+            return dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
+                        first_batch_new=exact, trials=trial + 1, accepted=True,
+                        seconds=time.time() - t0)
+        if exact is not None and exact <= HI_T and (best is None or exact > best["first_batch_new"]):
+            best = dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
+                        first_batch_new=exact, trials=trial + 1, accepted=False)
+        # move the label density toward the target range
+        temp = min(1.0, temp + 0.04) if verdict == "sparse" else max(-1.0, temp - 0.04)
+        last = verdict
+    if best is None:                     # nothing countable: keep the last draw, uncounted
+        best = dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
+                    first_batch_new=-1, trials=max_trials, accepted=False)
+    best["seconds"] = time.time() - t0
+    return best
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--jobs", type=int, default=os.cpu_count())
+    ap.add_argument("--out", default=None, help="calibration file (default: beside this script)")
+    ap.add_argument("--redo-unaccepted", action="store_true",
+                    help="search again only the queries not accepted in the stored calibration")
+    args = ap.parse_args()
+    out = args.out or os.path.join(os.path.dirname(os.path.abspath(__file__)), "rmat20_c3_calibration.json")
+    todo, keep = list(range(NQ)), []
+    if args.redo_unaccepted:
+        prev = json.load(open(out))["queries"]
+        keep = [r for r in prev if r["accepted"]]
+        todo = [r["index"] for r in prev if not r["accepted"]]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(args.jobs, initializer=_init) as pool:
+        res = list(keep)
+        for r in pool.imap_unordered(search, todo):
+            print(f"query {r['index']}: {r['kind']} nv={r['nv']} edges={r['edges']} el={r['elabels']} "
+                  f"vl={r['vlabels']} |dS+| batch 0 = {r['first_batch_new']} "
+                  f"({'accepted' if r['accepted'] else 'best'} after {r['trials']} draws, "
+                  f"{r['seconds']:.0f}s)", flush=True)
+            res.append(r)
+    res.sort(key=lambda r: r["index"])
+    with open(out, "w") as f:
+        json.dump({"target": [LO_T, HI_T], "queries": res}, f, indent=1)
+    print("RMAT20_C3_QUERIES = [")
+    for r in res:
+        print(f"    ({r['nv']}, {r['edges']}, {r['elabels']}, {r['vlabels']}),")
+    print("]")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,6 +1,8 @@
-"""Parity at the benchmark's full size (rmat20_window: 2^20 vertices, window
-2^22 edges, batches of 65,536, the four calibrated queries), in the same
-launch configuration as bench.py (device-resident batches, count-only
+"""Parity at the benchmark's full size (the rmat20 stream: 2^20 vertices,
+window 2^22 edges, batches of 65,536), for both benchmark workloads -- the
+four calibrated queries (rmat20_window) and the 36 batched uneven queries
+(rmat20_uneven: 32 random trees and chorded cycles plus the four) -- in the
+same launch configuration as bench.py (device-resident batches, count-only
 preload, queries registered on the full window).
 
 The oracle cannot list a whole batch quickly, so per batch and query:
@@ -21,20 +23,25 @@ from paper_2206_09983_b300 import mnemonic as M
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def run():
+_STREAM = {}
+
+
+@pytest.fixture(scope="module", params=["rmat20_window", "rmat20_uneven"])
+def run(request):
     import torch
     from paper_2206_09983_b300 import build
     build.build()
-    w = workloads.RMAT20
-    W, B = w["window"], w["batch"]
-    s = workloads.rmat20_stream()
+    wl = workloads.WORKLOADS[request.param]
+    W, B = wl["window"], wl["batch"]
+    if "s" not in _STREAM:
+        _STREAM["s"] = workloads.rmat20_stream()
+    s = _STREAM["s"]
     packed = M.edges_from_stream(s, 0, W + 2 * B)
     d = torch.from_numpy(packed.view(np.uint8)).cuda()
-    qs = workloads.rmat20_queries()
+    qs = wl["queries"]()
     g = M.Graph(s["num_vertices"], s["num_edge_labels"], vmask=s["vmask"], window=W, max_batch=B,
                 max_queries=len(qs), stream=torch.cuda.current_stream().cuda_stream,
-                out_capacity=1 << 21)
+                out_capacity=wl["out_capacity"])
     for lo in range(0, W, B):
         g.insert(None, device_ptr=d.data_ptr() + 24 * lo, n=B, count_only=True)
     qids = [g.register_query(q) for q in qs]
@@ -93,7 +100,14 @@ def test_fullsize_sampled_exact(run, k):
     B = hi_new - hi
     rng = np.random.default_rng(1234 + k)
     for sign, base in ((+1, hi), (-1, lo)):
-        pick = np.sort(rng.choice(B, size=48, replace=False)) + base
+        pick = rng.choice(B, size=48 if len(qs) <= 8 else 24, replace=False) + base
+        # plus the 8 batch edges with the highest-degree endpoints (the hub
+        # tail, where subtrees are split and donated)
+        deg = np.bincount(s["src"][lo:hi_new], minlength=s["num_vertices"]) + \
+            np.bincount(s["dst"][lo:hi_new], minlength=s["num_vertices"])
+        bsl = np.arange(base, base + B)
+        hub = bsl[np.argsort(-(deg[s["src"][bsl]] + deg[s["dst"][bsl]]), kind="stable")[:8]]
+        pick = np.unique(np.concatenate([pick, hub]))
         mask = np.zeros(hi_new - lo, dtype=np.uint8)
         mask[pick - lo] = 1
         for qi, q in enumerate(qs):
