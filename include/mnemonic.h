@@ -335,6 +335,17 @@ typedef struct {
  * the count); *n gets the count; MN_ERR_INVALID_ARG if out is too small. */
 mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out, uint32_t *n);
 
+/* What the last mn_autotune measured per candidate: enumeration time (ms,
+ * CUDA events on the graph's stream) and work (adjacency entries tested +
+ * candidates bound) summed over its batches; zeros for candidates not yet
+ * run.  *n gets the count; out (NULL: count only) must hold it. */
+typedef struct {
+    mn_tune_config config;
+    double enumerate_ms;
+    double work;
+} mn_tune_result;
+mn_status mn_autotune_results(const mn_graph *g, uint32_t cap, mn_tune_result *out, uint32_t *n);
+
 /* Largest live window mn_count_static_noalloc accepts: its seed scratch
  * holds one 8-byte work unit per live edge. */
 #define MN_NOALLOC_MAX_SEEDS (1u << 22)
@@ -359,9 +370,38 @@ mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out,
  *     MN_ERR_INVALID_ARG before any work is queued. */
 mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *count);
 
+/* DEBI neighbourhood filtering (Sec. V-A "Batch Processing", Sec. IV-A):
+ * on each query's tree (root = the most selective query vertex: fewest data
+ * vertices carrying its labels per unit of query degree, ties to the smaller
+ * id; BFS tree, neighbours in ascending (vertex, edge) order), the top-down
+ * sets TD(u) (f1: reached from a root candidate along matching tree edges;
+ * f2/f3 under isomorphism: at least as many live edges and distinct
+ * neighbours per edge label and direction as u has query edges) and the
+ * bottom-up sets BU(u) (f4: the subtree of u has matching edges into BU of
+ * every child), one pass each, on the live graph.  The filtered DEBI bit of
+ * a tree edge is its edgeMatcher bit with the parent side in TD and the child
+ * side in BU; the enumerator binds query vertex u only to vertices of BU(u).
+ * Results are unchanged (every embedding lies in the sets).  Enabling builds
+ * the sets of every registered query (and of each one registered later);
+ * afterwards they are maintained from the endpoints of the inserted, expired
+ * and deleted edges (the unified frontier), before each enumeration.  The
+ * state costs, per query, 3 bitmaps and one frontier list of num_vertices
+ * entries per query vertex.  0 turns it off.  MN_ERR_STATE while a queued
+ * batch is pending. */
+mn_status mn_set_filtering(mn_graph *g, int32_t enable);
+
+/* Test hook of the filtering: the query tree (root, parent[u] and the tree
+ * edge into u, -1 at the root; nv entries each) and, with filtering on, the
+ * bitmaps TD and BU (host arrays of nv * ceil(num_vertices / 32) words; bit
+ * v of word u * ceil(V / 32) + v / 32).  Any pointer may be NULL; asking for
+ * bitmaps with filtering off is MN_ERR_STATE. */
+mn_status mn_read_filter(mn_graph *g, uint32_t query_id, uint32_t *td, uint32_t *bu, int32_t *root,
+                         int32_t *parent, int32_t *tree_edge);
+
 /* Copy the DEBI words (Sec. IV-A; bit e = the edge matches query edge e) of
  * the edges with seq in [seq_lo, seq_hi) to host memory `words` (uint32
- * each); edges not live read 0. */
+ * each); edges not live read 0.  With filtering on, tree-edge bits are the
+ * filtered ones (mn_set_filtering). */
 mn_status mn_read_debi(mn_graph *g, uint32_t query_id, uint64_t seq_lo, uint64_t seq_hi,
                        uint32_t *words);
 
@@ -426,6 +466,9 @@ typedef struct {
     uint64_t d2h_bytes;            /* bytes copied device -> host (counts, status) */
     uint64_t rerun_launches;       /* enumerator launches that re-ran the seeds of overflowed lists */
     uint64_t dualsim_passes;       /* refinement passes run by mn_dual_simulation */
+    double   ms_filter;            /* DEBI filtering passes (mn_set_filtering) */
+    uint64_t seeds_filtered;       /* seeds skipped because an endpoint is outside the filtered sets */
+    uint64_t filter_changes;       /* vertex-set memberships the filtering passes changed */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

@@ -667,7 +667,8 @@ struct EnumParams {
     uint32_t count_only;
     unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
     uint32_t *status;
-    unsigned long long *work;           // [seeds, entries tested, binds, records, busy cycles, tasks]
+    unsigned long long *work;           // [seeds, entries tested, binds, records, busy cycles, tasks,
+                                        //  seeds whose endpoints the filtering excludes]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
     // optional second seed set, enumerated in the same launch after the first
     // (the other phase of the same batch): its seeds, avoid interval, sign and
@@ -679,6 +680,8 @@ struct EnumParams {
     unsigned long long *seed_work1;
     uint32_t split_min;                 // smallest range handed to an idle warp
     uint32_t split_depth;               // deepest search depth that may be split
+    uint32_t *const *bu;                // DEBI filtering on: per query its BU bitmaps [nv][W32]
+    uint32_t W32;
     uint32_t wait_polls;                // idle wait bound (WAIT_POLLS)
     uint32_t wait_hold;                 // test: holders neither take nor give up their slot
     unsigned long long qrun[2];         // per seed set: bit q set = enumerate query q's seeds
@@ -800,6 +803,9 @@ __device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi,
 // large range, the pending candidates of a chunk, or whole last-depth
 // ranges.  Embeddings are staged per warp in shared memory and written out in
 // contiguous blocks.
+// FILTER: the DEBI filtering is on (p.bu set); a separate instantiation, so
+// that the unfiltered kernel carries none of its code.
+template <bool FILTER>
 __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(EnumParams p)
 {
     __shared__ __align__(16) unsigned char stage_all[ENUM_WARPS][STAGE_BYTES];
@@ -818,7 +824,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
     const uint32_t many_idle = gridDim.x * ENUM_WARPS / 4;
     bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
-    unsigned long long w_tasks = 0;
+    unsigned long long w_tasks = 0, w_pruned = 0;
     uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0, st_sign = 0;
 
     // write the staged records of query st_q to its list
@@ -914,6 +920,15 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
             if (pl->iso && vs == vd) skip = true;
             const unsigned long long qr = set ? p.qrun[1] : p.qrun[0];
             if (!((qr >> (q & 63)) & 1ull)) skip = true;   // this query's seeds are not run
+            if (FILTER && !skip) {                         // filtering: both endpoints in BU
+                const uint32_t *bq = p.bu[q];
+                const uint32_t ss = pl->seed_src, sd = pl->seed_dst;
+                if (!((bq[ss * p.W32 + (vs >> 5)] >> (vs & 31)) & 1u) ||
+                    !((bq[sd * p.W32 + (vd >> 5)] >> (vd & 31)) & 1u)) {
+                    skip = true;
+                    w_pruned++;
+                }
+            }
             if (lane == (int)pl->seed_src) f = vs;
             if (lane == (int)pl->seed_dst) f = vd;
             if (lane == (int)j) g = seed32 - p.base32;
@@ -947,6 +962,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
         uint4 sw = make_uint4(0, 0, 0, 0);
         if (lane < MN_MAX_QE) sw = reinterpret_cast<const uint4 *>(pl->step)[lane];
         const uint32_t *__restrict__ debi = p.debi[q];
+        const uint32_t *__restrict__ buq = FILTER ? p.bu[q] : nullptr;   // filtering: BU bitmaps
         const uint32_t sign = set ? p.sign1 : p.sign;       // this unit's output lists
         const uint32_t av_lo = set ? p.av_lo1 : p.av_lo, av_hi = set ? p.av_hi1 : p.av_hi;
         unsigned long long warp_count = 0;
@@ -1254,6 +1270,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                         if (ok2 && avoid_l && p.batch_flag) ok2 = p.batch_flag[sv & p.cap_mask] == 0;
                         if (kind_l == K_CLOSE) ok2 = ok2 && nb2 == otg;
                     }
+                    if (FILTER && ok2 && kind_l == K_EXTEND)
+                        ok2 = (buq[to_l * p.W32 + (nb2 >> 5)] >> (nb2 & 31)) & 1u;
                     if (kind_l == K_EXTEND && iso) {
                         for (uint32_t bv = bv_l; bv; bv &= bv - 1) {
                             const uint32_t wv = __ffs(bv) - 1;
@@ -1360,6 +1378,8 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                         if (ok) ok = (debi[sv & p.cap_mask] >> qe) & 1u;
                         if (ok && avoid && p.batch_flag) ok = p.batch_flag[sv & p.cap_mask] == 0;
                         if (kind_s == K_CLOSE) ok = ok && nb == tgt;
+                        if (FILTER && ok && kind_s == K_EXTEND)
+                            ok = (buq[to * p.W32 + (nb >> 5)] >> (nb & 31)) & 1u;
                     }
                     if (kind_s == K_EXTEND && iso) {
                         for (uint32_t bv = bound_v; bv; bv &= bv - 1) {
@@ -1418,6 +1438,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
         atomicAdd(&p.work[3], w_records);
         atomicAdd(&p.work[4], w_busy);
         atomicAdd(&p.work[5], w_tasks);
+        atomicAdd(&p.work[6], w_pruned);
     }
 }
 

@@ -25,6 +25,7 @@
 #include "mn_device.cuh"
 #include "mn_learned.cuh"
 #include "mn_dualsim.cuh"
+#include "mn_filter.cuh"
 
 using namespace mn;
 
@@ -42,12 +43,12 @@ struct Ctrl {
     uint32_t next_seed[3];
     uint32_t pad_;
     long long last_ts;
-    unsigned long long work[6];
+    unsigned long long work[7];
     unsigned long long counts[64 * 3];
     unsigned long long time_cut;        // edges a time window expires after this batch
 };
 
-enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_COUNT };
+enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_FILTER, S_COUNT };
 
 struct QueryHost {
     uint32_t nv = 0, ne = 0, iso = 0, temporal = 0;
@@ -57,6 +58,11 @@ struct QueryHost {
     std::vector<std::pair<uint32_t, uint32_t>> prec;
     Plan plans[MN_MAX_QE][NCAND];   // [seed edge][candidate order]
     QueryDev dev;
+    FilterQuery fq;                 // query tree and degree needs of the DEBI filtering
+    // filtering state (mn_set_filtering): TD / BU / queued bitmaps [nv][W32],
+    // frontier lists [nv][V], their lengths and snapshots
+    uint32_t *td = nullptr, *bu = nullptr, *queued = nullptr, *front = nullptr;
+    uint32_t *nfront = nullptr, *nsnap = nullptr;
     uint32_t *debi = nullptr;
     uint8_t *out[2] = {nullptr, nullptr};
     unsigned long long out_cap[2] = {0, 0};
@@ -110,6 +116,16 @@ struct mn_graph {
     bool have_ts = false;
 
     uint32_t *d_vmask = nullptr;
+    // DEBI filtering (mn_set_filtering): dirty vertices since the last pass
+    bool filter = false, filter_dirty = false;
+    uint32_t W32 = 0;
+    uint32_t *d_dmap = nullptr, *d_dirty = nullptr, *d_ndirty = nullptr;
+    FilterQuery *d_fq = nullptr;
+    uint32_t **d_bu_ptrs = nullptr;  // per query: its BU bitmaps (the enumerator's vertex test)
+    unsigned long long *d_fchanges = nullptr, fchanges_base = 0;
+    FilterParams *d_fparams = nullptr;   // per query, copied before each pass
+    uint32_t *d_fitems = nullptr;        // (query << 8 | query vertex) items of every level
+    unsigned char *h_fstage = nullptr;   // pinned staging of both (reused: every batch ends with a sync)
     uint32_t *r_src = nullptr, *r_dst = nullptr;
     uint8_t *r_label = nullptr, *r_dead = nullptr, *batch_flag = nullptr;
     int32_t *r_attr = nullptr;
@@ -304,7 +320,7 @@ void collect_timing(mn_graph *g)
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p.second.first, p.second.second);
         double *dst[S_COUNT] = {&g->stats.ms_ingest, &g->stats.ms_adjacency, &g->stats.ms_seeds,
-                                &g->stats.ms_enumerate, &g->stats.ms_expire};
+                                &g->stats.ms_enumerate, &g->stats.ms_expire, &g->stats.ms_filter};
         *dst[p.first] += ms;
         g->ev_pool.push_back(p.second.first);
         g->ev_pool.push_back(p.second.second);
@@ -320,6 +336,7 @@ void collect_work(mn_graph *g)
     g->stats.records += g->h_ctrl->work[3];
     g->stats.busy_cycles += g->h_ctrl->work[4];
     g->stats.tasks_split += g->h_ctrl->work[5];
+    g->stats.seeds_filtered += g->h_ctrl->work[6];
     collect_timing(g);
 }
 
@@ -340,7 +357,7 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
     for (uint32_t u = 0; u < nv; u++)
         for (auto &kv : g->vmask_hist)
             if ((kv.first & Q.vmask[u]) == Q.vmask[u]) cand[u] += kv.second;
-    std::vector<uint32_t> deg(nv, 0);
+    std::vector<uint64_t> deg(nv, 0);
     std::vector<std::vector<std::pair<uint32_t, uint32_t>>> adj(nv);   // (nbr, edge)
     for (uint32_t e = 0; e < ne; e++) {
         deg[Q.edges[e].src]++;
@@ -351,7 +368,7 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
     for (auto &a : adj) std::sort(a.begin(), a.end());
     uint32_t root = 0;
     for (uint32_t u = 1; u < nv; u++)
-        if ((double)cand[u] / deg[u] < (double)cand[root] / deg[root]) root = u;
+        if (cand[u] * deg[root] < cand[root] * deg[u]) root = u;   // cand/deg smaller, exactly
     std::vector<int> parent(nv, -1), tedge(nv, -1), bfs;
     std::vector<char> seen(nv, 0);
     bfs.push_back((int)root);
@@ -367,6 +384,50 @@ mn_status compile_query(mn_graph *g, QueryHost &Q)
             }
     }
     if (bfs.size() != nv) return fail(g, MN_ERR_INVALID_ARG, "query graph is not connected");
+    {   // the filtering's view of the tree (Sec. V-A): BFS order, parents, tree edges, degree needs
+        FilterQuery &F = Q.fq;
+        memset(&F, 0, sizeof(F));
+        F.nv = nv;
+        F.root = root;
+        F.iso = Q.iso;
+        F.root_qmask = Q.vmask[root];
+        for (uint32_t u = 0; u < nv; u++) F.qmask[u] = Q.vmask[u];
+        uint32_t nlev = 0;
+        for (size_t h = 0; h < bfs.size(); h++) {
+            const uint32_t u = (uint32_t)bfs[h];
+            F.order[h] = (uint8_t)u;
+            F.parent[u] = (int8_t)parent[u];
+            F.tedge[u] = (int8_t)tedge[u];
+            F.depth[u] = h == 0 ? 0 : (uint8_t)(F.depth[parent[u]] + 1);
+            nlev = std::max<uint32_t>(nlev, F.depth[u] + 1u);
+            if (parent[u] >= 0) {
+                const mn_qedge &te = Q.edges[tedge[u]];
+                F.p_is_src[u] = te.src == (uint32_t)parent[u] ? 1 : 0;
+                F.tlabel[u] = (int16_t)te.label;
+                F.children[parent[u]] |= 1u << u;
+            } else {
+                F.tlabel[u] = -1;
+            }
+        }
+        F.nlev = nlev;
+        for (uint32_t e = 0; e < ne; e++) {
+            const mn_qedge &x = Q.edges[e];
+            F.need_out[x.src]++;
+            F.need_in[x.dst]++;
+            if (x.label < 0) continue;
+            for (int side = 0; side < 2; side++) {
+                const uint32_t u = side ? x.dst : x.src;
+                uint32_t k = 0;
+                while (k < F.nl[u] && F.lab[u][k] != x.label) k++;
+                if (k == F.nl[u]) {
+                    if (k == FQ_MAXL) continue;      // more labels than kept: a weaker (still sound) check
+                    F.lab[u][k] = (int16_t)x.label;
+                    F.nl[u]++;
+                }
+                if (side) F.lin[u][k]++; else F.lout[u][k]++;
+            }
+        }
+    }
     std::vector<char> is_tree(ne, 0);
     std::vector<int> bfs_edges;
     for (size_t h = 1; h < bfs.size(); h++) {
@@ -640,6 +701,158 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
     return MN_OK;
 }
 
+// ---------------------------------------------------------------- DEBI filtering
+
+mn_status filter_globals(mn_graph *g)
+{
+    if (g->d_dmap) return MN_OK;
+    g->W32 = (g->V + 31) / 32;
+    TRY(dalloc(g, &g->d_dmap, g->W32));
+    TRY(dalloc(g, &g->d_dirty, g->V, false));
+    TRY(dalloc(g, &g->d_ndirty, 1));
+    TRY(dalloc(g, &g->d_fq, g->max_queries));
+    TRY(dalloc(g, &g->d_bu_ptrs, g->max_queries));
+    TRY(dalloc(g, &g->d_fchanges, 1));
+    TRY(dalloc(g, &g->d_fparams, g->max_queries));
+    TRY(dalloc(g, &g->d_fitems, (uint64_t)g->max_queries * MN_MAX_QV * 2));
+    CK(cudaMallocHost((void **)&g->h_fstage, sizeof(FilterParams) * g->max_queries +
+                                             sizeof(uint32_t) * g->max_queries * MN_MAX_QV * 2));
+    return MN_OK;
+}
+
+mn_status filter_alloc(mn_graph *g, size_t q)
+{
+    QueryHost &Q = g->queries[q];
+    if (Q.td) return MN_OK;
+    const uint64_t bw = (uint64_t)Q.nv * g->W32;
+    TRY(dalloc(g, &Q.td, bw));
+    TRY(dalloc(g, &Q.bu, bw));
+    TRY(dalloc(g, &Q.queued, bw));
+    TRY(dalloc(g, &Q.front, (uint64_t)Q.nv * g->V, false));
+    TRY(dalloc(g, &Q.nfront, Q.nv));
+    TRY(dalloc(g, &Q.nsnap, Q.nv));
+    CK(cudaMemcpyAsync(g->d_fq + q, &Q.fq, sizeof(FilterQuery), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_bu_ptrs + q, &Q.bu, sizeof(uint32_t *), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return MN_OK;
+}
+
+FilterParams filter_params(mn_graph *g, size_t q, int buf, uint64_t base, uint64_t vis_hi, bool full)
+{
+    QueryHost &Q = g->queries[q];
+    FilterParams p;
+    memset(&p, 0, sizeof(p));
+    p.fq = g->d_fq + q;
+    p.qi = (uint32_t)q;
+    p.V = g->V;
+    p.L = g->L;
+    p.W32 = g->W32;
+    p.cap_mask = g->cap_mask;
+    for (int t = 0; t < NPROB; t++) { p.nbr[t] = g->base[buf][t].nbr; p.s32[t] = g->base[buf][t].s32; }
+    p.offs[0] = g->offs[0];
+    p.offs[1] = g->offs[1];
+    p.base32 = (uint32_t)base;
+    p.vis_lo = (uint32_t)(g->lo - base);
+    p.vis_hi = (uint32_t)(vis_hi - base);
+    p.debi = Q.debi;
+    p.r_dead = g->r_dead;
+    p.vmask = g->d_vmask;
+    p.td = Q.td;
+    p.bu = Q.bu;
+    p.queued = Q.queued;
+    p.front = Q.front;
+    p.nfront = Q.nfront;
+    p.nsnap = Q.nsnap;
+    p.dirty = g->d_dirty;
+    p.ndirty = g->d_ndirty;
+    p.full = full ? 1u : 0u;
+    p.changes = g->d_fchanges;
+    return p;
+}
+
+// Mark both endpoints of the edges at seqs [seq_lo, seq_lo + n) (or of the
+// listed seqs) dirty for the next filtering pass.
+mn_status filter_mark(mn_graph *g, uint64_t seq_lo, uint64_t n, const unsigned long long *seqs)
+{
+    if (!g->filter || n == 0) return MN_OK;
+    k_filter_dirty<<<cdiv(n, 256), 256, 0, g->stream>>>(seq_lo, (uint32_t)n, seqs, g->cap_mask, g->r_src,
+                                                        g->r_dst, g->d_dmap, g->d_dirty, g->d_ndirty, g->V,
+                                                        &g->d_ctrl->status);
+    CKL();
+    g->filter_dirty = true;
+    return MN_OK;
+}
+
+// One filtering pass (top-down then bottom-up over the query trees' levels)
+// for every query, or only query `only`, on adjacency buffer `buf` (lowest
+// seq `base`) with visible seqs [lo, vis_hi).  full: every vertex is a
+// candidate (building the sets); else the dirty vertices and the frontiers.
+// All queries' items of one level run in one launch (blockIdx.y = item).
+mn_status filter_pass(mn_graph *g, int buf, uint64_t base, uint64_t vis_hi, bool full, int only = -1)
+{
+    if (!g->filter || g->queries.empty()) return MN_OK;
+    const uint32_t *st = &g->d_ctrl->status;
+    std::vector<FilterParams> P;
+    std::vector<std::vector<uint32_t>> lev;
+    for (size_t q = 0; q < g->queries.size(); q++) {
+        if (only >= 0 && (int)q != only) continue;
+        const FilterQuery &F = g->queries[q].fq;
+        const uint32_t pi = (uint32_t)P.size();
+        P.push_back(filter_params(g, q, buf, base, vis_hi, full));
+        if (lev.size() < F.nlev) lev.resize(F.nlev);
+        for (uint32_t h = 0; h < F.nv; h++) {
+            const uint32_t u = F.order[h];
+            lev[F.depth[u]].push_back(pi << 8 | u);
+        }
+    }
+    std::vector<uint32_t> flat;
+    std::vector<size_t> off;
+    for (auto &l : lev) { off.push_back(flat.size()); flat.insert(flat.end(), l.begin(), l.end()); }
+    FilterParams *hp = reinterpret_cast<FilterParams *>(g->h_fstage);
+    uint32_t *hi_ = reinterpret_cast<uint32_t *>(g->h_fstage + sizeof(FilterParams) * g->max_queries);
+    std::copy(P.begin(), P.end(), hp);
+    std::copy(flat.begin(), flat.end(), hi_);
+    CK(cudaMemcpyAsync(g->d_fparams, hp, P.size() * sizeof(FilterParams), cudaMemcpyHostToDevice, g->stream));
+    CK(cudaMemcpyAsync(g->d_fitems, hi_, flat.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, g->stream));
+    stage_begin(g);
+    const uint32_t bx = 64;                       // blocks per item
+    auto run_level = [&](size_t d, bool td) -> mn_status {
+        const uint32_t n = (uint32_t)lev[d].size();
+        if (!n) return MN_OK;
+        FilterItems it{g->d_fparams, g->d_fitems + off[d]};
+        k_filter_snap<<<1, 256, 0, g->stream>>>(it, n);
+        CKL();
+        if (td) k_filter_td<<<dim3(bx, n), 256, 0, g->stream>>>(it, st);
+        else    k_filter_bu<<<dim3(bx, n), 256, 0, g->stream>>>(it, st);
+        CKL();
+        return MN_OK;
+    };
+    for (size_t d = 0; d < lev.size(); d++) TRY(run_level(d, true));
+    for (size_t d = lev.size(); d-- > 0;) TRY(run_level(d, false));
+    if (!full) {
+        const uint32_t np = (uint32_t)P.size();
+        k_filter_reset<<<dim3(bx, np), 256, 0, g->stream>>>(g->d_fparams, st);
+        CKL();
+        k_filter_zero_fronts<<<np, 32, 0, g->stream>>>(g->d_fparams, st);
+        CKL();
+        k_filter_dirty_clear<<<(uint32_t)g->nsm * 8, 256, 0, g->stream>>>(g->d_dmap, g->d_dirty, g->d_ndirty, g->V, st);
+        CKL();
+        k_filter_zero<<<1, 32, 0, g->stream>>>(g->d_ndirty, 1, st);
+        CKL();
+        g->filter_dirty = false;
+    }
+    stage_end(g, S_FILTER);
+    return MN_OK;
+}
+
+// Bring the sets up to date with the current graph before an enumeration
+// outside an insert (deletes, static counts): only when edges changed.
+mn_status filter_refresh(mn_graph *g)
+{
+    if (!g->filter || !g->filter_dirty) return MN_OK;
+    return filter_pass(g, g->cur, g->merged_lo, g->hi, false);
+}
+
 // One enumerator launch over the seeds of one or two phases (dS+ and dS- of
 // one batch share the adjacency buffer and visibility; a single launch has
 // one tail instead of two).  The first phase's seeds are taken first.
@@ -692,6 +905,8 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     p.qrun[1] = qrun ? qrun[1] : ~0ull;
     p.wait_polls = g->wait_polls;
     p.wait_hold = g->wait_hold;
+    p.bu = g->filter ? g->d_bu_ptrs : nullptr;
+    p.W32 = g->W32;
     if (nph > 1) {
         const Phase &b = ph[1];
         if (b.buf != a.buf || b.base != a.base || b.vis_hi != a.vis_hi || b.flags != a.flags)
@@ -707,9 +922,11 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     p.split_min = g->split_min;
     p.split_depth = g->split_depth;
     CK(cudaMemsetAsync(g->d_sched + a.phase, 0, sizeof(Sched), g->stream));
-    CK(cudaFuncSetAttribute(k_enumerate, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
+    CK(cudaFuncSetAttribute(k_enumerate<false>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
+    CK(cudaFuncSetAttribute(k_enumerate<true>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
     stage_begin(g);
-    k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
+    if (p.bu) k_enumerate<true><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
+    else      k_enumerate<false><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     stage_end(g, S_ENUM);
     g->stats.enumerate_launches++;
@@ -1021,6 +1238,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     g->hi = hi_new;
     const uint64_t ex_lo = g->lo;
     if (x) {
+        TRY(filter_mark(g, g->lo, x, nullptr));
         stage_begin(g);
         k_expire<<<cdiv(x, 256), 256, 0, g->stream>>>(g->lo, (uint32_t)x, g->cap_mask, g->L,
                                                       (uint32_t)g->queries.size(), g->d_debi_ptrs,
@@ -1182,7 +1400,7 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate, ENUM_WARPS * 32, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<false>, ENUM_WARPS * 32, 0);
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
         g->nsm = nsm;
         g->enum_max_per_sm = std::max(per_sm, 1);
@@ -1213,6 +1431,7 @@ void mn_destroy_graph(mn_graph *g)
     if (g->tune_e0) cudaEventDestroy(g->tune_e0);
     if (g->tune_e1) cudaEventDestroy(g->tune_e1);
     if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
+    if (g->h_fstage) cudaFreeHost(g->h_fstage);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1293,6 +1512,12 @@ mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query
     CK(cudaStreamSynchronize(g->stream));
     g->queries.push_back(Q);
     *query_id = qid;
+    if (g->filter) {
+        TRY(filter_alloc(g, qid));
+        CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+        TRY(filter_pass(g, g->cur, g->merged_lo, g->hi, true, (int)qid));
+        CK(cudaStreamSynchronize(g->stream));
+    }
     return MN_OK;
 }
 
@@ -1340,6 +1565,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         stage_begin(g);
         TRY(launch_adjacency_update(g, n, src, g->hi));
         stage_end(g, S_ADJ);
+        TRY(filter_mark(g, g->hi, n, nullptr));
         if (g->time_window > 0) {
             // time window: the oldest edges up to newest - window expire now
             k_time_cut<<<1, 1, 0, g->stream>>>(g->lo, hi_new, g->cap_mask, g->r_ts, &g->d_ctrl->last_ts,
@@ -1353,6 +1579,8 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
             x = g->h_ctrl->time_cut;
         }
     }
+    // DEBI filtering on G1 (the new adjacency, the expiring edges still visible)
+    if (n) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
     // autotuning: run this batch's enumeration under the next candidate
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
     if (tune_now) {
@@ -1450,6 +1678,7 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
                                                            g->r_dead, g->batch_flag, &g->d_ctrl->status);
         CKL();
     }
+    TRY(filter_refresh(g));
     Phase ph[1] = {Phase{1, g->cur, g->merged_lo, g->hi, g->lo, g->hi, true}};
     int nph = 0;
     if (n && nq) {
@@ -1472,6 +1701,7 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
                                                             g->d_debi_ptrs, g->r_dead, g->batch_flag,
                                                             &g->d_ctrl->status);
         CKL();
+        TRY(filter_mark(g, 0, n, ds));
         CK(cudaStreamSynchronize(g->stream));
     }
     if (st != MN_OK) return st;
@@ -1528,6 +1758,7 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
     if (!count || query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     CK(cudaSetDevice(g->device));
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
+    TRY(filter_refresh(g));
     const uint64_t live = g->hi - g->lo;
     TRY(launch_seeds_range(g, 2, g->lo, live, query_id, 1u));
     const Phase ps{2, g->cur, g->merged_lo, g->hi, g->lo, g->hi, false};
@@ -1545,11 +1776,11 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count)
 namespace {
 
 // Scratch of mn_count_static_noalloc, in 8-byte words: [0, 4) status and seed
-// count (u32 each), [4, 10) the enumerator's six work counters, [16, 208)
+// count (u32 each), [4, 11) the enumerator's seven work counters, [16, 208)
 // counts (3 per query, 64 queries), [256, 336) scheduler words (one 128-byte
 // line each), [384, 384 + MN_NOALLOC_MAX_SEEDS) seeds.
 constexpr uint32_t NA_WORK = 4, NA_COUNTS = 16, NA_SCHED = 256, NA_SEEDS = 384;
-static_assert(NA_WORK + 6 <= NA_COUNTS, "work counters overlap the counts");
+static_assert(NA_WORK + 7 <= NA_COUNTS, "work counters overlap the counts");
 static_assert(NA_COUNTS + 3 * 64 <= NA_SCHED, "counts overlap the scheduler words");
 static_assert(NA_SCHED * 8 + sizeof(Sched) <= NA_SEEDS * 8, "scheduler words overlap the seeds");
 constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
@@ -1633,8 +1864,8 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     p.work = base + NA_WORK;
     p.wait_polls = g->wait_polls;
     p.qrun[0] = p.qrun[1] = ~0ull;
-    CK(cudaFuncSetAttribute(k_enumerate, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
-    k_enumerate<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
+    CK(cudaFuncSetAttribute(k_enumerate<false>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
+    k_enumerate<false><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     uint32_t st = 0;
     unsigned long long c = 0;
@@ -1656,8 +1887,25 @@ mn_status mn_read_debi(mn_graph *g, uint32_t query_id, uint64_t seq_lo, uint64_t
         return fail(g, MN_ERR_INVALID_ARG, "bad argument");
     CK(cudaSetDevice(g->device));
     std::vector<uint32_t> all(g->C);
-    CK(cudaMemcpyAsync(all.data(), g->queries[query_id].debi, g->C * sizeof(uint32_t),
-                       cudaMemcpyDeviceToHost, g->stream));
+    const uint32_t *src = g->queries[query_id].debi;
+    uint32_t *tmp = nullptr;
+    if (g->filter && g->hi > g->lo) {          // filtered words of the live window
+        TRY(filter_refresh(g));
+        CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+        TRY(dalloc(g, &tmp, g->C));
+        const FilterParams fp = filter_params(g, query_id, g->cur, g->merged_lo, g->hi, false);
+        const uint64_t live = g->hi - g->lo;
+        std::vector<uint32_t> part(live);
+        k_filtered_words<<<cdiv(live, 256), 256, 0, g->stream>>>(fp, g->lo, (uint32_t)live, g->r_src, g->r_dst,
+                                                                 tmp);
+        CKL();
+        CK(cudaMemcpyAsync(part.data(), tmp, live * sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        dfree(g, tmp, g->C * sizeof(uint32_t));
+        for (uint64_t s = g->lo; s < g->hi; s++) all[s & g->cap_mask] = part[s - g->lo];
+        src = nullptr;
+    }
+    if (src) CK(cudaMemcpyAsync(all.data(), src, g->C * sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     for (uint64_t s = seq_lo; s < seq_hi; s++)
         words[s - seq_lo] = (s >= g->lo && s < g->hi) ? all[s & g->cap_mask] : 0u;
@@ -1699,6 +1947,52 @@ mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *k
     return MN_OK;
 }
 
+mn_status mn_set_filtering(mn_graph *g, int32_t enable)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    CK(cudaSetDevice(g->device));
+    if (!enable) {
+        g->filter = false;
+        return MN_OK;
+    }
+    if (g->filter) return MN_OK;
+    TRY(filter_globals(g));
+    for (size_t q = 0; q < g->queries.size(); q++) TRY(filter_alloc(g, q));
+    g->filter = true;
+    // build every query's sets on the current graph; nothing is pending then
+    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+    TRY(filter_pass(g, g->cur, g->merged_lo, g->hi, true));
+    CK(cudaMemsetAsync(g->d_dmap, 0, sizeof(uint32_t) * g->W32, g->stream));
+    CK(cudaMemsetAsync(g->d_ndirty, 0, sizeof(uint32_t), g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->filter_dirty = false;
+    return MN_OK;
+}
+
+mn_status mn_read_filter(mn_graph *g, uint32_t query_id, uint32_t *td, uint32_t *bu, int32_t *root,
+                         int32_t *parent, int32_t *tree_edge)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "no such query");
+    const QueryHost &Q = g->queries[query_id];
+    if (root) *root = (int32_t)Q.fq.root;
+    for (uint32_t u = 0; u < Q.nv; u++) {
+        if (parent) parent[u] = Q.fq.parent[u];
+        if (tree_edge) tree_edge[u] = Q.fq.tedge[u];
+    }
+    if (!td && !bu) return MN_OK;
+    if (!g->filter) return fail(g, MN_ERR_STATE, "filtering is off");
+    CK(cudaSetDevice(g->device));
+    TRY(filter_refresh(g));
+    const uint64_t bytes = sizeof(uint32_t) * (uint64_t)Q.nv * g->W32;
+    if (td) CK(cudaMemcpyAsync(td, Q.td, bytes, cudaMemcpyDeviceToHost, g->stream));
+    if (bu) CK(cudaMemcpyAsync(bu, Q.bu, bytes, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return MN_OK;
+}
+
 mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi, uint32_t *num_queries)
 {
     if (!g) return MN_ERR_INVALID_ARG;
@@ -1722,6 +2016,11 @@ mn_status mn_get_stats(const mn_graph *cg, mn_stats *out)
     CK(cudaSetDevice(g->device));
     CK(cudaStreamSynchronize(g->stream));
     collect_timing(g);
+    if (g->d_fchanges) {
+        unsigned long long c = 0;
+        CK(cudaMemcpy(&c, g->d_fchanges, sizeof(c), cudaMemcpyDeviceToHost));
+        g->stats.filter_changes = c - g->fchanges_base;
+    }
     *out = g->stats;
     return MN_OK;
 }
@@ -1733,6 +2032,8 @@ mn_status mn_reset_stats(mn_graph *g)
     CK(cudaStreamSynchronize(g->stream));
     collect_timing(g);
     g->stats = mn_stats{};
+    if (g->d_fchanges) CK(cudaMemcpy(&g->fchanges_base, g->d_fchanges, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost));
     return MN_OK;
 }
 
@@ -1852,6 +2153,13 @@ mn_status mn_reset_index(mn_graph *g)
                 g->r_dead, g->d_vmask, g->d_queries + q, Q.debi);
             CKL();
         }
+    }
+    if (g->filter) {                       // the filtered sets follow the rebuilt words
+        CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+        TRY(filter_pass(g, g->cur, g->merged_lo, g->hi, true));
+        CK(cudaMemsetAsync(g->d_dmap, 0, sizeof(uint32_t) * g->W32, g->stream));
+        CK(cudaMemsetAsync(g->d_ndirty, 0, sizeof(uint32_t), g->stream));
+        g->filter_dirty = false;
     }
     CK(cudaStreamSynchronize(g->stream));
     return MN_OK;
@@ -1983,6 +2291,24 @@ mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out,
         out[k].presplit_log2 = std::isinf(c.presplit_log2) ? 0.f : c.presplit_log2;
     }
     if (out && cap < *n) return fail(g, MN_ERR_INVALID_ARG, "array too small");
+    return MN_OK;
+}
+
+mn_status mn_autotune_results(const mn_graph *g, uint32_t cap, mn_tune_result *out, uint32_t *n)
+{
+    if (!g || !n) return MN_ERR_INVALID_ARG;
+    *n = (uint32_t)std::min(g->tune_cfgs.size(), g->tune_ms.size());
+    if (!out) return MN_OK;
+    if (cap < *n) return MN_ERR_INVALID_ARG;
+    for (uint32_t k = 0; k < *n; k++) {
+        const auto &c = g->tune_cfgs[k];
+        out[k].config.blocks_per_sm = c.bps;
+        out[k].config.split_min = c.split_min;
+        out[k].config.split_depth = c.split_depth;
+        out[k].config.presplit_log2 = std::isinf(c.presplit_log2) ? 0.f : c.presplit_log2;
+        out[k].enumerate_ms = g->tune_ms[k];
+        out[k].work = g->tune_work[k];
+    }
     return MN_OK;
 }
 

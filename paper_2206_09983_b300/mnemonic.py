@@ -42,7 +42,8 @@ EXPORTS = [
     "mn_mlp_gradient", "mn_set_tuning", "mn_get_tuning", "mn_autotune", "mn_autotune_state",
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
-    "mn_autotune_candidates", "mn_last_error",
+    "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
+    "mn_last_error",
 ]
 MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
@@ -83,7 +84,8 @@ class Stats(C.Structure):
                 ("seeds", C.c_uint64), ("entries_scanned", C.c_uint64),
                 ("binds", C.c_uint64), ("records", C.c_uint64), ("busy_cycles", C.c_uint64), ("tasks_split", C.c_uint64),
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64)]
+                ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64),
+                ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -92,6 +94,10 @@ class Stats(C.Structure):
 class _TuneConfig(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_uint32), ("split_min", C.c_uint32), ("split_depth", C.c_uint32),
                 ("presplit_log2", C.c_float)]
+
+
+class _TuneResult(C.Structure):
+    _fields_ = [("config", _TuneConfig), ("enumerate_ms", C.c_double), ("work", C.c_double)]
 
 
 class _BatchResult(C.Structure):
@@ -153,8 +159,11 @@ def load(path: str | None = None):
         "mn_set_work_budget": (S, [P, U64]),
         "mn_set_wait_limit": (S, [P, C.c_uint32, C.c_uint32]),
         "mn_set_presplit": (S, [P, C.c_float]),
+        "mn_set_filtering": (S, [P, C.c_int32]),
+        "mn_read_filter": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_int32), P, P]),
         "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
+        "mn_autotune_results": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_set_timing": (S, [P, C.c_int32]),
         "mn_get_stats": (S, [P, C.POINTER(Stats)]),
         "mn_reset_stats": (S, [P]),
@@ -453,6 +462,34 @@ class Graph:
     def autotune(self, batches_per_config: int = 1):
         self._check(self._lib.mn_autotune(self._h, batches_per_config))
 
+    def set_filtering(self, on: bool):
+        """DEBI neighbourhood filtering on or off (mn_set_filtering)."""
+        self._check(self._lib.mn_set_filtering(self._h, 1 if on else 0))
+
+    def read_filter(self, qid: int, sets: bool = True):
+        """(root, parent[], tree_edge[], TD, BU) of query qid; TD / BU are bool
+        arrays [nv][num_vertices] (None with sets=False)."""
+        nv = self.layouts[qid][0]
+        V = self._num_vertices
+        w32 = (V + 31) // 32
+        root = C.c_int32()
+        par = np.zeros(nv, dtype=np.int32)
+        ted = np.zeros(nv, dtype=np.int32)
+        td = bu = None
+        if sets:
+            td = np.zeros(nv * w32, dtype=np.uint32)
+            bu = np.zeros(nv * w32, dtype=np.uint32)
+        self._check(self._lib.mn_read_filter(self._h, qid, None if td is None else td.ctypes.data,
+                                             None if bu is None else bu.ctypes.data, C.byref(root),
+                                             par.ctypes.data, ted.ctypes.data))
+
+        def unpack(a):
+            if a is None:
+                return None
+            bits = np.unpackbits(a.view(np.uint8), bitorder="little").reshape(nv, w32 * 32)
+            return bits[:, :V].astype(bool)
+        return root.value, par.tolist(), ted.tolist(), unpack(td), unpack(bu)
+
     def set_presplit(self, log2_cycles: float):
         """Learned pre-splitting threshold in log2 predicted SM cycles (0 = off)."""
         self._check(self._lib.mn_set_presplit(self._h, log2_cycles))
@@ -469,6 +506,16 @@ class Graph:
         arr = (_TuneConfig * max(1, n.value))()
         self._check(self._lib.mn_autotune_candidates(self._h, n.value, arr, C.byref(n)))
         return [(c.blocks_per_sm, c.split_min, c.split_depth, c.presplit_log2) for c in arr[:n.value]]
+
+    def autotune_results(self):
+        """Per autotuner candidate: (blocks_per_sm, split_min, split_depth,
+        presplit_log2, enumerate_ms, work) as measured on live batches."""
+        n = C.c_uint32()
+        self._check(self._lib.mn_autotune_results(self._h, 0, None, C.byref(n)))
+        arr = (_TuneResult * max(1, n.value))()
+        self._check(self._lib.mn_autotune_results(self._h, n.value, arr, C.byref(n)))
+        return [(r.config.blocks_per_sm, r.config.split_min, r.config.split_depth, r.config.presplit_log2,
+                 r.enumerate_ms, r.work) for r in arr[:n.value]]
 
     def autotune_state(self):
         a, left = C.c_int32(), C.c_uint32()
