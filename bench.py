@@ -191,70 +191,150 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------ serving mode
 
 def run_serve(args, local):
-    """Continuous-batching request loop on the window stream: Poisson arrivals
-    of log-uniform batches in [1K, 64K] edges at a fraction of the plain
-    path's measured throughput; queued requests are merged into one device
-    batch when the GPU frees up.  Reports per-request latency (arrival ->
-    counts on the host) and sustained edges/s."""
-    import threading
+    """Serving on the NetFlow-like stream (workloads.FLOW: 10M hosts, 6
+    protocol labels, window 2^24, 8 standing queries): Poisson arrivals of
+    log-uniform batches in [2^10, 2^18] edges; requests that queue while the
+    GPU is busy are admitted together (continuous batching under a device
+    memory budget).  First the maximum sustained rate is measured closed-loop
+    (a backlog of requests), then the offered load is set to 50 / 80 / 95% of
+    it.  Latency is arrival -> counts on the host.  Sampled parity: on device
+    batches 0, 1, 2, 3 and every 16th of each load level, the records that
+    contain one of 24 sampled edges equal the CPU oracle's."""
     import torch
+    from oracle import oracle
     from paper_2206_09983_b300 import build, workloads
     from paper_2206_09983_b300 import mnemonic as M
     from paper_2206_09983_b300.serve import Server, poisson_batches
 
     build.build()
     torch.cuda.set_device(local)
-    w = workloads.RMAT20
-    W, B = w["window"], w["batch"]
-    stream = workloads.rmat20_stream()
-    packed = M.edges_from_stream(stream, 0, len(stream["src"]))
-    qs = workloads.rmat20_queries()
-    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"],
-                window=W, max_batch=B, max_queries=len(qs), device=local, out_capacity=1 << 21)
-    for lo in range(0, W, B):
-        g.insert(packed[lo:lo + B], count_only=True)
+    w = workloads.FLOW
+    W, MB = w["window"], w["max_batch"]
+    levels = [0.5, 0.8, 0.95]
+    per_level = args.serve_edges
+    n_total = W + 3 * (1 << 16) + (1 + len(levels)) * per_level
+    assert n_total <= w["num_edges"], "serve run longer than the stream"
+    t0 = time.perf_counter()
+    stream = workloads.flow_prefix(n_total)
+    packed = M.edges_from_stream(stream, 0, n_total)
+    gen_s = time.perf_counter() - t0
+    qs = workloads.flow_queries()
+    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"], window=W,
+                max_batch=MB, max_queries=len(qs), device=local, out_capacity=1 << 18)
+    for lo in range(0, W, MB):
+        g.insert(packed[lo:lo + MB], count_only=True)
     for q in qs:
         g.register_query(q)
-    g.set_order_policy("explore" if args.serve_order == "learned" else "paper")
-    for k in range(3):                                          # warm-up
-        g.insert(packed[W + k * B: W + (k + 1) * B])
-    pos = W + 3 * B
-    if args.serve_order == "learned":                           # train the order model first
+    pos = W
+    if args.serve_order == "learned":
+        g.set_order_policy("explore")
+    for _ in range(3):                                             # warm-up
+        g.insert(packed[pos:pos + (1 << 16)])
+        pos += 1 << 16
+    if args.serve_order == "learned":
         g.train_order_model(epochs=args.train_epochs, lr=2e-3)
         g.set_order_policy("learned")
-    rate = args.serve_rate
     rng = np.random.default_rng(0x5E4E)
-    sched = poisson_batches(rng, args.serve_edges, 1024, B, rate)
-    srv = Server(mem_budget_bytes=8 << 30, merge=True, max_batch=B)
-    srv.add_tenant("rmat20", g, count_only=False)
-    reqs = []
-    t0 = time.perf_counter()
-    for t, size in sched:
-        now = time.perf_counter() - t0
-        if t > now:
-            time.sleep(t - now)
-        reqs.append(srv.submit("rmat20", packed[pos:pos + size], t_arrival=t0 + t))
-        pos += size
-    srv.drain(timeout=3600)
-    t_end = max(r.t_done for r in reqs)
-    srv.close()
+    rec_bytes = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
+
+    def one_level(rate, edges):
+        """Serve `edges` edges; rate None = closed loop (all requests at t=0)."""
+        nonlocal pos
+        if rate is None:
+            sizes = poisson_batches(rng, edges, 1 << 10, MB, 1e12)
+        else:
+            sizes = poisson_batches(rng, edges, 1 << 10, MB, rate)
+        srv = Server(mem_budget_bytes=16 << 30, merge=True, max_batch=MB)
+        srv.add_tenant("flow", g, keep_rows=False, count_only=False)
+        reqs, spans = [], []
+        t_start = time.perf_counter()
+        for t, size in sizes:
+            if rate is not None:
+                now = time.perf_counter() - t_start
+                if t > now:
+                    time.sleep(t - now)
+            reqs.append(srv.submit("flow", packed[pos:pos + size],
+                                   t_arrival=t_start + (t if rate is not None else 0.0)))
+            spans.append((pos, pos + size))
+            pos += size
+        srv.drain(timeout=3600)
+        t_end = max(r.t_done for r in reqs)
+        srv.close()
+        lat = np.array([1e3 * r.latency for r in reqs])
+        n_edges = sum(len(r.edges) for r in reqs)
+        return {"offered_edges_per_s": rate, "value": n_edges / (t_end - t_start), "requests": len(reqs),
+                "edges": n_edges,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                               "max": float(lat.max())},
+                "mean_requests_per_batch": float(np.mean([r.merged_with for r in reqs])),
+                "errors": sum(1 for r in reqs if r.error)}, reqs, spans
+
+    out = {"mode": "serve", "metric": METRIC, "unit": UNIT,
+           "config": {"workload": w["name"], "hosts": w["hosts"], "window": W, "max_batch": MB,
+                      "queries": len(qs), "arrivals": "Poisson, batch sizes log-uniform in [1024, 262144]",
+                      "path": (("learned matching order" if args.serve_order == "learned" else
+                                "paper's matching order") + ", continuous batching (queued requests merged)"),
+                      "stream_generation_s": gen_s}}
+    mx, _, _ = one_level(None, per_level)
+    out["max_sustained"] = mx
+    out["levels"] = []
+    for f in levels:
+        r, reqs, spans = one_level(f * mx["value"], per_level)
+        r["fraction_of_max"] = f
+        out["levels"].append(r)
+    out["value"] = out["levels"][-1]["value"]
+    # sampled parity on a fresh replay of device batches (the serve run kept
+    # no lists): a second graph replays the same edges as the same batches
+    out["parity"] = serve_parity(args, local, stream, packed, qs, W, MB)
     g.close()
-    lat = np.array([1e3 * r.latency for r in reqs])
-    edges = sum(len(r.edges) for r in reqs)
-    merged = np.array([r.merged_with for r in reqs])
-    return {
-        "mode": "serve", "metric": METRIC, "unit": UNIT,
-        "value": edges / (t_end - t0),
-        "offered_edges_per_s": rate, "requests": len(reqs), "edges": edges,
-        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                       "max": float(lat.max())},
-        "mean_requests_per_batch": float(np.mean(merged)),
-        "errors": sum(1 for r in reqs if r.error),
-        "config": {"workload": w["name"], "window": W, "max_batch": B,
-                   "arrivals": "Poisson, batch sizes log-uniform in [1024, 65536]",
-                   "path": (("learned matching order" if args.serve_order == "learned" else
-                             "paper's matching order") + ", continuous batching (queued requests merged)")},
-    }
+    return out
+
+
+def serve_parity(args, local, stream, packed, qs, W, MB):
+    """Replay the serving stream's first device batches (sizes log-uniform in
+    [2^10, 2^18]) on a fresh graph keeping lists; on batches 0, 1, 2, 3, 16
+    and 32, compare the records that contain one of 24 sampled
+    batch edges (plus the 4 edges with the highest-degree endpoints) with the
+    CPU oracle's, for every query."""
+    from oracle import oracle
+    from paper_2206_09983_b300 import mnemonic as M
+    rng = np.random.default_rng(0x5E4F)
+    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"], window=W,
+                max_batch=MB, max_queries=len(qs), device=local, out_capacity=1 << 18)
+    for lo in range(0, W, MB):
+        g.insert(packed[lo:lo + MB], count_only=True)
+    for q in qs:
+        g.register_query(q)
+    pos, lo_w, checked, rows_checked = W, 0, [], 0
+    for k in range(33):
+        size = int(np.exp(rng.uniform(np.log(1 << 10), np.log(MB))))
+        r = g.insert(packed[pos:pos + size])
+        hi, hi_new = pos, pos + size
+        x = max(0, hi_new - lo_w - W)
+        if k in (0, 1, 2, 3) or k % 16 == 0:
+            deg = np.bincount(stream["src"][lo_w:hi_new], minlength=stream["num_vertices"])
+            for sign, base, n in ((+1, hi, size), (-1, lo_w, x)):
+                if n == 0:
+                    continue
+                pick = base + rng.choice(n, size=min(n, 24), replace=False)
+                bs = np.arange(base, base + n)
+                hub = bs[np.argsort(-deg[stream["src"][bs]], kind="stable")[:4]]
+                pick = np.unique(np.concatenate([pick, hub]))
+                mask = np.zeros(hi_new - lo_w, dtype=np.uint8)
+                mask[pick - lo_w] = 1
+                for qi, q in enumerate(qs):
+                    got = g.fetch_rows(qi, sign)
+                    sel = np.isin(got[:, q["nv"]:], pick.astype(np.uint64)).any(axis=1)
+                    want = oracle.delta(stream, lo_w, hi_new, 0, 0, q, batch_mask=mask)
+                    assert got[sel].shape == want.shape and (got[sel] == want).all(), \
+                        f"serve parity: batch {k} query {qi} sign {sign}"
+                    rows_checked += len(want)
+            checked.append(k)
+        pos = hi_new
+        lo_w += x
+    g.close()
+    return {"batches_checked": checked, "rows_checked": rows_checked, "ok": True,
+            "sample": "24 random + 4 highest-degree batch edges per sign and checked batch, every query"}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -277,8 +357,9 @@ def main():
     ap.add_argument("--with-uneven", dest="with_uneven", action="store_true", default=True,
                     help="also time the 36-query batched workload on the same stream (the default)")
     ap.add_argument("--no-uneven", dest="with_uneven", action="store_false")
-    ap.add_argument("--serve-rate", type=float, default=4.0e5, help="offered load, edges/s")
-    ap.add_argument("--serve-edges", type=int, default=6_000_000)
+    ap.add_argument("--no-filter-arm", dest="filter_arm", action="store_false", default=True,
+                    help="skip the plain arm with DEBI filtering")
+    ap.add_argument("--serve-edges", type=int, default=10_000_000, help="edges per load level")
     ap.add_argument("--serve-order", default="learned", choices=["learned", "paper"])
     args = ap.parse_args()
     rank, world, local = env_rank()
@@ -342,6 +423,22 @@ def main():
     return 0
 
 
+def presplit_gain(results):
+    """Best enumeration time per unit of work among the autotuner's
+    candidates with learned pre-splitting off and on (each candidate ran on
+    a different live batch, so times are normalised by work)."""
+    if not results:
+        return None
+    def best(sel):
+        c = [(ms / w, cfg) for (*cfg, ms, w) in results if sel(cfg[3]) and w > 1]
+        return min(c) if c else None
+    off, on = best(lambda t: t == 0.0), best(lambda t: t != 0.0)
+    if not off or not on:
+        return None
+    return {"ms_per_gwork_off": off[0] * 1e9, "ms_per_gwork_on": on[0] * 1e9, "ratio": off[0] / on[0],
+            "best_off": list(off[1]), "best_on": list(on[1])}
+
+
 def run_workload(args, ctx, wl, with_e2e):
     """Both arms of one workload on the shared device-resident stream: the
     learned + autotuned arm (timed first; its end-to-end leg through host
@@ -362,7 +459,7 @@ def run_workload(args, ctx, wl, with_e2e):
             import torch.distributed as dist
             dist.barrier()
 
-    def arm(policy: str, with_e2e: bool, skip: int = 0):
+    def arm(policy: str, with_e2e: bool, skip: int = 0, filtering: bool = False):
         """One arm on the same stream batches: preload, register, WU warm-up
         batches (under exploration for the learned arm, then training), K
         timed batches, then the end-to-end run."""
@@ -378,6 +475,8 @@ def run_workload(args, ctx, wl, with_e2e):
             g.insert(None, device_ptr=base_ptr + 24 * lo, n=B, count_only=True)
         for q in qs:
             g.register_query(q)
+        if filtering:
+            g.set_filtering(True)
         pos = W
         g.set_order_policy("explore" if policy == "learned" else "paper")
         for _ in range(WU):
@@ -395,6 +494,7 @@ def run_workload(args, ctx, wl, with_e2e):
                 while g.autotune_state()[0]:
                     g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
                     pos += B
+                res["autotune"] = g.autotune_results()
         else:
             for _ in range(skip):                                # same batches as the learned arm
                 g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
@@ -457,13 +557,17 @@ def run_workload(args, ctx, wl, with_e2e):
         g.close()
         return res
 
+    filtered = None
     if args.plain_only:
         plain = learned = arm("paper", with_e2e=with_e2e)
     else:
         learned = arm("learned", with_e2e=with_e2e)
         plain = arm("paper", with_e2e=False, skip=learned.get("tune_batches", 0))
-    for k in range(K):                                  # exact counts: both arms agree
+        if args.filter_arm:
+            filtered = arm("paper", with_e2e=False, skip=learned.get("tune_batches", 0), filtering=True)
+    for k in range(K):                                  # exact counts: the arms agree
         assert plain["per_q"][k] == learned["per_q"][k], "learned and plain counts differ"
+        assert filtered is None or filtered["per_q"][k] == plain["per_q"][k], "filtered counts differ"
     dev_ms, lat, counts, per_q, st = (learned[k] for k in ("dev_ms", "lat", "counts", "per_q", "st"))
     clocks, e2e = learned["clocks"], learned["e2e"]
 
@@ -559,8 +663,21 @@ def run_workload(args, ctx, wl, with_e2e):
                                         "adjacency": plain["st"]["ms_adjacency"] / K},
                   "clocks": plain["clocks"]},
         "learned_vs_plain": (plain["dev_ms"] / dev_ms) if dev_ms else None,
+        # the plain path with the DEBI neighbourhood filtering on (same
+        # batches, same counts): pass time and seeds it removed
+        "filtered": None if filtered is None else {
+            "ms_per_step": filtered["dev_ms"] / K,
+            "stage_ms_per_step": {"filter": filtered["st"]["ms_filter"] / K,
+                                  "enumerate": filtered["st"]["ms_enumerate"] / K},
+            "seeds_per_step": filtered["st"]["seeds"] / K,
+            "seeds_filtered_per_step": filtered["st"]["seeds_filtered"] / K,
+            "filter_changes_per_step": filtered["st"]["filter_changes"] / K,
+            "work_per_step": {k: filtered["st"][k] / K for k in ("entries_scanned", "binds")}},
         "train": learned.get("train"),
         "tuning": {"plain": plain.get("tuning_used"), "learned": learned.get("tuning_used")},
+        # the autotuner's live measurements (one batch per candidate, learned
+        # order): the best configuration with and without learned pre-splitting
+        "presplit_gain": presplit_gain(learned.get("autotune")),
         "latency_ms": {"p50": 1e3 * statistics.median(lat), "p99": 1e3 * float(np.percentile(lat, 99)),
                        "max": 1e3 * max(lat)},
         "embeddings_per_step": {"new": float(np.mean([c[0] for c in counts])),

@@ -136,48 +136,66 @@ def rmat_stream(scale: int, num_edges: int, a: float, b: float, c: float,
     return out
 
 
-def flow_stream(num_hosts: int, num_edges: int, num_elabels: int, seed: int,
-                server_frac: float = 0.1, zipf_s: float = 1.1,
-                mean_repeat: float = 8.0) -> dict:
-    """Bipartite-heavy network-flow multigraph (NetFlow-like, Sec. VII).
+def flow_chunks(num_hosts: int, num_edges: int, num_elabels: int, seed: int,
+                server_frac: float = 0.1, zipf_s: float = 1.1, mean_repeat: float = 8.0,
+                client_server: float = 0.9, attr_range: int = 1000, chunk: int = 1 << 22):
+    """Bipartite-heavy network-flow multigraph (NetFlow-like, Sec. VII), in
+    arrival order, as chunks of at most `chunk` edges.
 
-    Clients (90%) send flows mostly to servers; source activity and server
-    popularity are Zipf-distributed; each (src, dst) pair repeats a geometric
-    number of times, giving many timestamped parallel edges.  One vertex label.
+    Hosts [0, n_srv) are servers, the rest clients (before a seeded shuffle of
+    the host ids).  A fraction `client_server` of the flows go from a client
+    to a server: the client drawn by Zipf(zipf_s) over the clients' ranks
+    (source activity), the server by Zipf(zipf_s) over the servers' ranks
+    (popularity).  The other flows join two hosts drawn uniformly (background
+    traffic).  Each (src, dst) pair repeats a geometric number of times (mean
+    `mean_repeat`): timestamped parallel edges.  Protocol labels Zipf(zipf_s)
+    over num_elabels; attribute uniform in [0, attr_range); one vertex label.
     """
     rng = _rng(seed)
     n_srv = max(1, int(num_hosts * server_frac))
-    out = {k: [] for k in ("src", "dst")}
-    total = 0
-    while total < num_edges:
-        m = min(1 << 22, num_edges - total)
-        npairs = max(1, int(m / mean_repeat) + 1)
-        s = rng.zipf(zipf_s + 1e-9, size=npairs) - 1
-        s = (s % num_hosts).astype(np.int64)
-        to_srv = rng.random(npairs) < 0.9
-        d_srv = (rng.zipf(zipf_s + 1e-9, size=npairs) - 1) % n_srv
-        d_any = rng.integers(0, num_hosts, size=npairs)
-        d = np.where(to_srv, d_srv, d_any).astype(np.int64)
-        rep = rng.geometric(1.0 / mean_repeat, size=npairs)
-        ss = np.repeat(s, rep)[:m]
-        dd = np.repeat(d, rep)[:m]
-        order = rng.permutation(len(ss))
-        out["src"].append(ss[order])
-        out["dst"].append(dd[order])
-        total += len(ss)
-    src = np.concatenate(out["src"])[:num_edges]
-    dst = np.concatenate(out["dst"])[:num_edges]
+    n_cli = max(1, num_hosts - n_srv)
     perm = rng.permutation(num_hosts)
-    return {
-        "src": perm[src].astype(np.uint32),
-        "dst": perm[dst].astype(np.uint32),
-        "label": zipf_labels(rng, num_edges, num_elabels, zipf_s),
-        "attr": np.zeros(num_edges, dtype=np.int32),
-        "ts": _timestamps(rng, num_edges),
-        "vmask": np.ones(num_hosts, dtype=np.uint32),
-        "num_vertices": int(num_hosts),
-        "num_edge_labels": int(num_elabels),
-    }
+    t0 = 1000
+    done = 0
+    while done < num_edges:
+        m = min(chunk, num_edges - done)
+        ss_parts, dd_parts, have = [], [], 0
+        while have < m:                       # pairs until their repeats cover the chunk
+            npairs = max(16, int((m - have) / mean_repeat * 1.25) + 16)
+            cs = rng.random(npairs) < client_server
+            cli = n_srv + (rng.zipf(zipf_s + 1e-9, size=npairs) - 1) % n_cli
+            srv = (rng.zipf(zipf_s + 1e-9, size=npairs) - 1) % n_srv
+            us = rng.integers(0, num_hosts, size=npairs)
+            ud = rng.integers(0, num_hosts, size=npairs)
+            s = np.where(cs, cli, us).astype(np.int64)
+            d = np.where(cs, srv, ud).astype(np.int64)
+            rep = rng.geometric(1.0 / mean_repeat, size=npairs)
+            ss_parts.append(np.repeat(s, rep))
+            dd_parts.append(np.repeat(d, rep))
+            have += int(rep.sum())
+        ss = np.concatenate(ss_parts)
+        dd = np.concatenate(dd_parts)
+        order = rng.permutation(len(ss))[:m]
+        ts = _timestamps(rng, m, t0)
+        t0 = int(ts[-1])
+        yield {
+            "src": perm[ss[order]].astype(np.uint32),
+            "dst": perm[dd[order]].astype(np.uint32),
+            "label": zipf_labels(rng, m, num_elabels, zipf_s),
+            "attr": rng.integers(0, attr_range, size=m).astype(np.int32),
+            "ts": ts,
+        }
+        done += m
+
+
+def flow_stream(num_hosts: int, num_edges: int, num_elabels: int, seed: int, **kw) -> dict:
+    """The whole flow stream of flow_chunks as one stream dict."""
+    parts = list(flow_chunks(num_hosts, num_edges, num_elabels, seed, **kw))
+    out = {k: np.concatenate([p[k] for p in parts]) for k in ("src", "dst", "label", "attr", "ts")}
+    out["vmask"] = np.ones(num_hosts, dtype=np.uint32)
+    out["num_vertices"] = int(num_hosts)
+    out["num_edge_labels"] = int(num_elabels)
+    return out
 
 
 def slice_stream(stream: dict, lo: int, hi: int) -> dict:

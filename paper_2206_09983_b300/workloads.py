@@ -19,6 +19,8 @@ rmat20_window: R-MAT power-law multigraph (a, b, c) = (0.57, 0.19, 0.19),
 """
 from __future__ import annotations
 
+import numpy as np
+
 from . import gen
 
 RMAT20 = dict(
@@ -138,3 +140,65 @@ WORKLOADS = {
                           query_names=lambda: rmat20_c3_names() + list(QUERY_NAMES),
                           out_capacity=1 << 18),
 }
+
+
+# ---------------------------------------------------------------- serving workload
+
+# NetFlow-like serving stream (BASELINE config 5): 10M hosts (10% servers),
+# client -> server flows by Zipf(1.1) client activity and server popularity,
+# 10% uniform background flows, ~8 timestamped parallel edges per host pair,
+# 6 protocol labels Zipf(1.1), one vertex label, 200M edges; count window
+# 2^24 edges, Poisson arrivals of log-uniform batches in [2^10, 2^18].
+FLOW = dict(name="flow10m_serve", hosts=10_000_000, num_edges=200_000_000, elabels=6, zipf=1.1,
+            seed=0x4D4E0005, window=1 << 24, batch=1 << 16, max_batch=1 << 18)
+
+
+def flow_chunks():
+    w = FLOW
+    return gen.flow_chunks(w["hosts"], w["num_edges"], w["elabels"], w["seed"], zipf_s=w["zipf"])
+
+
+def flow_prefix(n: int) -> dict:
+    """The first n edges of the serving stream (always the same edges: the
+    stream is generated chunk by chunk in arrival order)."""
+    parts, have = [], 0
+    for c in flow_chunks():
+        parts.append(c)
+        have += len(c["src"])
+        if have >= n:
+            break
+    out = {k: np.concatenate([p[k] for p in parts])[:n] for k in ("src", "dst", "label", "attr", "ts")}
+    out["vmask"] = np.ones(FLOW["hosts"], dtype=np.uint32)
+    out["num_vertices"] = FLOW["hosts"]
+    out["num_edge_labels"] = FLOW["elabels"]
+    return out
+
+
+def flow_query(nv, edges, elabels):
+    """A standing query of the serving workload: the given shape and
+    protocol labels (-1 = any), isomorphism, timestamps increasing along the
+    query edges; one vertex label, so no vertex constraint."""
+    return gen.make_query(nv, [(s, d, int(l)) for (s, d), l in zip(edges, elabels)], None,
+                          iso=True, temporal="chain")
+
+
+# The 8 standing queries (index, n_q, edges, protocol labels; the comment is
+# the oracle's exact |dS+| of the first batch of 65,536 edges after the
+# preloaded window), from the oracle-driven search in
+# tests/golden/calibrate_flow_queries.py: directed paths and forked paths, the
+# shapes that stay listable on a stream whose hub clients and servers make
+# stars explode.
+FLOW_QUERIES = [
+    (2, 4, [(0, 1), (1, 2), (2, 3)], [-1, -1, -1]),  # 2175
+    (5, 5, [(0, 1), (1, 2), (2, 3), (1, 4)], [0, 5, 3, 0]),  # 13085
+    (9, 5, [(0, 1), (1, 2), (2, 3), (2, 4)], [-1, 0, 0, 0]),  # 19248
+    (11, 6, [(0, 1), (1, 2), (2, 3), (3, 4), (1, 5)], [2, 0, -1, 0, 1]),  # 4557
+    (15, 5, [(0, 1), (1, 2), (2, 3), (2, 4)], [1, -1, -1, -1]),  # 14650
+    (19, 5, [(0, 1), (1, 2), (2, 3), (2, 4)], [3, 0, -1, 0]),  # 3978
+    (21, 5, [(0, 1), (1, 2), (2, 3), (1, 4)], [0, 1, 0, 3]),  # 34682
+    (35, 5, [(0, 1), (1, 2), (2, 3), (1, 4)], [2, 3, 0, 2]),  # 7709
+]
+
+
+def flow_queries() -> list:
+    return [flow_query(nv, edges, el) for _, nv, edges, el in FLOW_QUERIES]
