@@ -245,7 +245,9 @@ def run_serve(args, local):
         else:
             sizes = poisson_batches(rng, edges, 1 << 10, MB, rate)
         srv = Server(mem_budget_bytes=16 << 30, merge=True, max_batch=MB)
-        srv.add_tenant("flow", g, keep_rows=False, count_only=False)
+        ten = srv.add_tenant("flow", g, keep_rows=False, count_only=False)
+        g.set_timing(True)
+        g.reset_stats()
         reqs, spans = [], []
         t_start = time.perf_counter()
         for t, size in sizes:
@@ -262,8 +264,18 @@ def run_serve(args, local):
         srv.close()
         lat = np.array([1e3 * r.latency for r in reqs])
         n_edges = sum(len(r.edges) for r in reqs)
+        st = g.stats()
+        g.set_timing(False)
+        nb = max(1, len(ten.batches))
+        ins = np.array([1e3 * b[2] for b in ten.batches])
+        dev = {"batches": len(ten.batches), "mean_edges": float(np.mean([b[0] for b in ten.batches])),
+               "insert_ms": {"mean": float(ins.mean()), "p50": float(np.percentile(ins, 50)),
+                             "p99": float(np.percentile(ins, 99))},
+               "stage_ms_per_batch": {k: st["ms_" + k] / nb for k in ("ingest", "adjacency", "seeds",
+                                                                      "enumerate", "expire")},
+               "rerun_launches": st["rerun_launches"]}
         return {"offered_edges_per_s": rate, "value": n_edges / (t_end - t_start), "requests": len(reqs),
-                "edges": n_edges,
+                "edges": n_edges, "device": dev,
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                                "max": float(lat.max())},
                 "mean_requests_per_batch": float(np.mean([r.merged_with for r in reqs])),
@@ -285,7 +297,7 @@ def run_serve(args, local):
     out["value"] = out["levels"][-1]["value"]
     # sampled parity on a fresh replay of device batches (the serve run kept
     # no lists): a second graph replays the same edges as the same batches
-    out["parity"] = serve_parity(args, local, stream, packed, qs, W, MB)
+    out["parity"] = None if args.no_serve_parity else serve_parity(args, local, stream, packed, qs, W, MB)
     g.close()
     return out
 
@@ -359,7 +371,8 @@ def main():
     ap.add_argument("--no-uneven", dest="with_uneven", action="store_false")
     ap.add_argument("--no-filter-arm", dest="filter_arm", action="store_false", default=True,
                     help="skip the plain arm with DEBI filtering")
-    ap.add_argument("--serve-edges", type=int, default=10_000_000, help="edges per load level")
+    ap.add_argument("--serve-edges", type=int, default=30_000_000, help="edges per load level")
+    ap.add_argument("--no-serve-parity", action="store_true", help="skip the sampled parity replay")
     ap.add_argument("--serve-order", default="learned", choices=["learned", "paper"])
     args = ap.parse_args()
     rank, world, local = env_rank()
@@ -402,7 +415,7 @@ def main():
         line["batched_uneven"] = {k: extra[k] for k in (
             "value", "unit", "ms_per_step", "config", "plain", "learned_vs_plain", "latency_ms",
             "embeddings_per_step", "stage_ms_per_step", "work_per_step", "roofline", "tuning", "train",
-            "clocks")}
+            "clocks", "filtered", "presplit_gain")}
         line["gpu_launches"] += extra["gpu_launches"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         W, B = main_wl["window"], main_wl["batch"]

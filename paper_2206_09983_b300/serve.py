@@ -58,6 +58,7 @@ class _Tenant:
         self.count_only = count_only
         self.bytes_per_edge = 64.0      # running estimate of result bytes per inserted edge
         self.thread = None
+        self.batches = []               # per device batch: (edges, requests, seconds in the insert call)
 
 
 class Server:
@@ -139,10 +140,12 @@ class Server:
             edges = reqs[0].edges if len(reqs) == 1 else np.concatenate([r.edges for r in reqs])
             err = ""
             res = None
+            t_ins = time.perf_counter()
             try:
                 res = t.graph.insert(edges, count_only=t.count_only)
             except M.MnError as e:                     # reported per request
                 err = str(e)
+            t.batches.append((len(edges), len(reqs), time.perf_counter() - t_ins))
             rows = ([], [])
             if res is not None and t.keep_rows and not t.count_only:
                 for qi in range(len(res.count_pos)):
