@@ -369,6 +369,8 @@ def main():
     ap.add_argument("--with-uneven", dest="with_uneven", action="store_true", default=True,
                     help="also time the 36-query batched workload on the same stream (the default)")
     ap.add_argument("--no-uneven", dest="with_uneven", action="store_false")
+    ap.add_argument("--no-graph-probe", dest="graph_probe", action="store_false", default=True,
+                    help="skip the CUDA-graph launch-overhead probe")
     ap.add_argument("--no-filter-arm", dest="filter_arm", action="store_false", default=True,
                     help="skip the plain arm with DEBI filtering")
     ap.add_argument("--serve-edges", type=int, default=30_000_000, help="edges per load level")
@@ -409,6 +411,8 @@ def main():
     main_wl = workloads.WORKLOADS[args.workload]
     res = run_workload(args, ctx, main_wl, with_e2e=not args.no_e2e)
     line = res["line"]
+    if args.graph_probe and world == 1:
+        line["graph_capture"] = graph_probe(ctx, main_wl, res["pos"])
     if args.with_uneven and args.workload != "rmat20_uneven":
         # the batched-uneven-queries workload on the same stream, both arms
         extra = run_workload(args, ctx, workloads.WORKLOADS["rmat20_uneven"], with_e2e=False)["line"]
@@ -434,6 +438,47 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def graph_probe(ctx, wl, pos, small=4096, steps=40):
+    """Launch overhead of the batch chain: batches of `small` edges on the
+    same window and queries (paper order), kernel by kernel and then each as
+    one CUDA graph (mn_set_graph_capture); CUDA-event time per batch."""
+    torch, M, local = ctx["torch"], ctx["M"], ctx["local"]
+    stream, base_ptr, cur_stream = ctx["stream"], ctx["base_ptr"], ctx["cur_stream"]
+    W = wl["window"]
+    qs = wl["queries"]()
+    g = M.Graph(stream["num_vertices"], stream["num_edge_labels"], vmask=stream["vmask"], window=W,
+                max_batch=wl["batch"], max_queries=len(qs), device=local, stream=cur_stream.cuda_stream,
+                out_capacity=wl["out_capacity"])
+    B0 = wl["batch"]
+    for lo in range(0, W, B0):
+        g.insert(None, device_ptr=base_ptr + 24 * lo, n=B0, count_only=True)
+    for q in qs:
+        g.register_query(q)
+    out = {"batch": small}
+    p = pos
+    for mode in ("kernels", "graph"):
+        g.set_graph_capture(mode == "graph")
+        for _ in range(4):
+            g.insert(None, device_ptr=base_ptr + 24 * p, n=small)
+            p += small
+        st0 = g.stats()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur_stream)
+        for _ in range(steps):
+            g.insert(None, device_ptr=base_ptr + 24 * p, n=small)
+            p += small
+        e1.record(cur_stream)
+        torch.cuda.synchronize()
+        st1 = g.stats()
+        out[mode] = {"ms_per_batch": e0.elapsed_time(e1) / steps,
+                     "kernel_launches_per_batch": (st1["kernel_launches"] - st0["kernel_launches"]) / steps,
+                     "graph_launches_per_batch": (st1["graph_launches"] - st0["graph_launches"]) / steps}
+    g.close()
+    out["speedup"] = out["kernels"]["ms_per_batch"] / out["graph"]["ms_per_batch"]
+    return out
 
 
 def presplit_gain(results):

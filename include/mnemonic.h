@@ -416,6 +416,19 @@ mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *k
 mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi,
                         uint32_t *num_queries);
 
+/* Record each insert batch's kernel chain (ingest, adjacency update,
+ * filtering, work units, order choice, enumeration of dS- and dS+) as one
+ * CUDA graph and launch it as a whole: one launch instead of a few dozen.
+ * The graph is captured per batch and updated in place (cudaGraphExecUpdate),
+ * so batch sizes and positions may change; a change of the chain's shape
+ * (e.g. another number of merge passes) instantiates it again.  Buffers the
+ * chain could grow are sized before recording.  Batches with a time window
+ * (a host wait inside the chain), with edges in pageable host memory, or
+ * run under autotuning are launched kernel by kernel as before.  Results are
+ * unchanged.  0 turns it off (the default); MN_ERR_STATE while a queued batch
+ * is pending. */
+mn_status mn_set_graph_capture(mn_graph *g, int32_t enable);
+
 /* Bound the enumerator's work: each device warp gives up after max_iters
  * backtracking steps, sets a status word and returns (no spin, no trap).  The
  * batch is still applied to the graph, its counts are partial and the call
@@ -469,6 +482,8 @@ typedef struct {
     double   ms_filter;            /* DEBI filtering passes (mn_set_filtering) */
     uint64_t seeds_filtered;       /* seeds skipped because an endpoint is outside the filtered sets */
     uint64_t filter_changes;       /* vertex-set memberships the filtering passes changed */
+    uint64_t graph_launches;       /* insert batches launched as one CUDA graph (mn_set_graph_capture) */
+    uint64_t graph_instantiations; /* graph instantiations (the rest were updated in place) */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

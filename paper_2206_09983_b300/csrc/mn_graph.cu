@@ -199,6 +199,8 @@ struct mn_graph {
     uint64_t n_samples = 0, explore_round = 0;
     uint32_t *d_temporal = nullptr;
     unsigned long long *d_nsamples = nullptr;   // samples ever logged (ring position)
+    bool use_graph = false;              // record each eligible insert batch as a CUDA graph
+    cudaGraphExec_t gexec = nullptr;     // updated in place batch after batch
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
     cudaEvent_t ev_open = nullptr;
@@ -1428,6 +1430,7 @@ void mn_destroy_graph(mn_graph *g)
     for (auto &p : g->ev_pending) { cudaEventDestroy(p.second.first); cudaEventDestroy(p.second.second); }
     for (auto e : g->ev_pool) cudaEventDestroy(e);
     if (g->ev_open) cudaEventDestroy(g->ev_open);
+    if (g->gexec) cudaGraphExecDestroy(g->gexec);
     if (g->tune_e0) cudaEventDestroy(g->tune_e0);
     if (g->tune_e1) cudaEventDestroy(g->tune_e1);
     if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
@@ -1521,18 +1524,16 @@ mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query
     return MN_OK;
 }
 
-mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags,
-                          mn_batch_result *out)
+// The kernels of one insert batch, queued on the graph's stream: ingest and
+// edgeMatcher, adjacency update, time cut, filtering, work units, order
+// choice and the enumeration of dS- and dS+.  On return *x, ph and *nph
+// describe the queued phases.  With capture the same calls are recorded in a
+// CUDA graph (nothing here may then allocate or wait: the callers size every
+// buffer first).
+static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags, uint64_t hi_new,
+                             uint64_t *x_io, Phase *ph, int *nph_out, bool count_only, bool tune_now)
 {
-    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
-    TRY(refuse_if_pending(g));
-    if (n && !edges) return fail(g, MN_ERR_INVALID_ARG, "edges is NULL");
-    if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
-    if (!g->W && g->hi + n - g->lo > g->C) return fail(g, MN_ERR_ADMISSION, "edge ring is full");
-    CK(cudaSetDevice(g->device));
-    const bool count_only = (flags & MN_COUNT_ONLY) != 0;
-    const uint64_t hi_new = g->hi + n;
-    uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
+    uint64_t x = *x_io;
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
     if (n) {
         const mn_edge *src = edges;
@@ -1581,22 +1582,12 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     }
     // DEBI filtering on G1 (the new adjacency, the expiring edges still visible)
     if (n) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
-    // autotuning: run this batch's enumeration under the next candidate
-    const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
-    if (tune_now) {
-        const auto &c = g->tune_cfgs[g->tune_idx];
-        g->enum_grid = g->nsm * (int)c.bps;
-        g->split_min = c.split_min;
-        g->split_depth = c.split_depth;
-        g->presplit_log2 = c.presplit_log2;
-        CK(cudaEventRecord(g->tune_e0, g->stream));
-    }
+    if (tune_now) CK(cudaEventRecord(g->tune_e0, g->stream));
     // the adjacency enumerated holds seqs from `base` on: the new buffer was
     // merged at lo; without new edges the current one was merged at merged_lo
     const int nbuf = n ? 1 - g->cur : g->cur;
     const uint64_t nbase = n ? g->lo : g->merged_lo;
     // dS- first: its seeds (the oldest edges) start the longest searches
-    Phase ph[2];
     int nph = 0;
     if (x && !g->queries.empty()) {
         // dS-: query edges before the seed edge avoid the expiring [lo, lo + x)
@@ -1615,6 +1606,97 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
     for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
     if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
+    *x_io = x;
+    *nph_out = nph;
+    return MN_OK;
+}
+
+// A batch may be recorded as a CUDA graph: no host wait inside its chain (no
+// time window), its edges on the device or in pinned host memory, and no
+// autotuning in progress.
+static bool graph_eligible(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags, bool tune_now)
+{
+    if (!g->use_graph || g->time_window > 0 || tune_now) return false;
+    if (n && !(flags & MN_DEVICE_PTR)) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, edges) != cudaSuccess) { cudaGetLastError(); return false; }
+        if (a.type != cudaMemoryTypeHost) return false;          // pageable: not capturable
+    }
+    return true;
+}
+
+mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags,
+                          mn_batch_result *out)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (n && !edges) return fail(g, MN_ERR_INVALID_ARG, "edges is NULL");
+    if (n > g->max_batch) return fail(g, MN_ERR_ADMISSION, "batch larger than max_batch");
+    if (!g->W && g->hi + n - g->lo > g->C) return fail(g, MN_ERR_ADMISSION, "edge ring is full");
+    CK(cudaSetDevice(g->device));
+    const bool count_only = (flags & MN_COUNT_ONLY) != 0;
+    const uint64_t hi_new = g->hi + n;
+    uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
+    // autotuning: run this batch's enumeration under the next candidate
+    const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
+    if (tune_now) {
+        const auto &c = g->tune_cfgs[g->tune_idx];
+        g->enum_grid = g->nsm * (int)c.bps;
+        g->split_min = c.split_min;
+        g->split_depth = c.split_depth;
+        g->presplit_log2 = c.presplit_log2;
+    }
+    Phase ph[2];
+    int nph = 0;
+    if (graph_eligible(g, edges, n, flags, tune_now)) {
+        // size everything the chain would grow, then record it
+        if (!g->queries.empty()) {
+            uint64_t total_ne = 0;
+            for (auto &Q : g->queries) total_ne += Q.ne;
+            TRY(ensure_seed_cap(g, 1, std::max<uint64_t>(1, x * total_ne)));
+            TRY(ensure_seed_cap(g, 0, std::max<uint64_t>(1, n * total_ne)));
+            if (g->policy != MN_ORDER_PAPER) {
+                TRY(ensure_model(g));
+                TRY(ensure_learn_rows(g, std::max(g->seed_cap[0], g->seed_cap[1])));
+                if (g->policy == MN_ORDER_LEARNED) TRY(pack_model(g));
+            }
+            if (!count_only) TRY(presize_outputs(g, n, x));
+        }
+        const bool timing = g->timing;
+        g->timing = false;                         // stage events stay out of the graph
+        CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed));
+        const mn_status qs = queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, false);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(g->stream, &graph);
+        g->timing = timing;
+        if (qs != MN_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return qs;
+        }
+        if (ec != cudaSuccess) return fail(g, MN_ERR_DEVICE, std::string("capture: ") + cudaGetErrorString(ec));
+        if (g->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(g->gexec, graph, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(g->gexec);
+                g->gexec = nullptr;
+            }
+        }
+        if (!g->gexec) {
+            const cudaError_t ei = cudaGraphInstantiate(&g->gexec, graph, 0);
+            if (ei != cudaSuccess) {
+                cudaGraphDestroy(graph);
+                g->gexec = nullptr;
+                return fail(g, MN_ERR_DEVICE, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+            }
+            g->stats.graph_instantiations++;
+        }
+        cudaGraphDestroy(graph);
+        CK(cudaGraphLaunch(g->gexec, g->stream));
+        g->stats.graph_launches++;
+    } else {
+        TRY(queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, tune_now));
+    }
     PendingBatch &pd = g->pending;
     pd.active = true;
     pd.id = g->batch_id + 1;
@@ -2349,6 +2431,14 @@ mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *ma
 
 // Test hook: per-warp loop budget of the enumerator (0 restores no limit).
 // A tiny budget makes a bounded device loop give up and report MN_ERR_TIMEOUT.
+mn_status mn_set_graph_capture(mn_graph *g, int32_t enable)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    g->use_graph = enable != 0;
+    return MN_OK;
+}
+
 mn_status mn_set_work_budget(mn_graph *g, uint64_t max_iters)
 {
     if (!g) return MN_ERR_INVALID_ARG;

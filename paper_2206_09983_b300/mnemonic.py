@@ -43,6 +43,7 @@ EXPORTS = [
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
+    "mn_set_graph_capture",
     "mn_last_error",
 ]
 MN_WAIT_HOLD = 0x1
@@ -85,7 +86,8 @@ class Stats(C.Structure):
                 ("binds", C.c_uint64), ("records", C.c_uint64), ("busy_cycles", C.c_uint64), ("tasks_split", C.c_uint64),
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64),
-                ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64)]
+                ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64),
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -160,6 +162,7 @@ def load(path: str | None = None):
         "mn_set_wait_limit": (S, [P, C.c_uint32, C.c_uint32]),
         "mn_set_presplit": (S, [P, C.c_float]),
         "mn_set_filtering": (S, [P, C.c_int32]),
+        "mn_set_graph_capture": (S, [P, C.c_int32]),
         "mn_read_filter": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_int32), P, P]),
         "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
@@ -461,6 +464,10 @@ class Graph:
 
     def autotune(self, batches_per_config: int = 1):
         self._check(self._lib.mn_autotune(self._h, batches_per_config))
+
+    def set_graph_capture(self, on: bool):
+        """Launch each eligible insert batch as one CUDA graph (mn_set_graph_capture)."""
+        self._check(self._lib.mn_set_graph_capture(self._h, 1 if on else 0))
 
     def set_filtering(self, on: bool):
         """DEBI neighbourhood filtering on or off (mn_set_filtering)."""
