@@ -78,6 +78,7 @@ typedef int32_t mn_status;
 /* fetch destination flags */
 #define MN_DST_HOST   0x0u
 #define MN_DST_DEVICE 0x1u
+#define MN_FETCH_SORTED 0x2u   /* records in ascending (vertex tuple, edge-seq tuple) order */
 
 typedef struct mn_graph mn_graph;
 
@@ -180,7 +181,12 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
 /* Copy records [offset, offset + max_records) of the last batch's list for
  * (query_id, sign: +1 new, -1 removed) to dst (host, or device with
  * MN_DST_DEVICE).  *n_written gets the number copied.  batch_id must be the
- * last batch's id. */
+ * last batch's id.  Records come in no particular order unless
+ * MN_FETCH_SORTED is set: the list is then sorted on the device (the first
+ * sorted fetch of a batch sorts it in place, with scratch of 8 B plus one
+ * record per record, allocated for the sort and freed; later fetches of the
+ * batch, sorted or not, return sorted records), ascending by the vertex ids
+ * f(u_0), ..., f(u_{nv-1}) and then the edge seqs. */
 mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id, int32_t sign,
                               uint64_t offset, uint64_t max_records, void *dst,
                               uint32_t dst_flags, uint64_t *n_written);
@@ -416,6 +422,28 @@ mn_status mn_read_adjacency(mn_graph *g, uint32_t dir, uint64_t cap, uint32_t *k
 mn_status mn_graph_info(const mn_graph *g, uint64_t *seq_lo, uint64_t *seq_hi,
                         uint32_t *num_queries);
 
+/* Host spill of expired edges (Sec. IV-A, external memory support: edges
+ * leaving the in-memory window are written out together with their index
+ * entries, oldest out first).  Every edge that expires from the window (count
+ * or time window) is copied, before its ring slot can be reused, into a
+ * pinned host FIFO of capacity_edges edges: its mn_edge record, its seq and
+ * the DEBI word of every registered query as it was when the edge left the
+ * window.  The copies run asynchronously on the graph's stream.  The FIFO
+ * holds the most recent capacity_edges expired seqs; older ones are
+ * overwritten.  It costs capacity_edges * (32 + 4 * max_queries) bytes of
+ * pinned host memory and max_batch * (32 + 4 * max_queries) bytes of device
+ * staging.  Set once per graph (MN_ERR_STATE afterwards); MN_ERR_OOM if the
+ * host memory cannot be pinned. */
+mn_status mn_set_spill(mn_graph *g, uint64_t capacity_edges);
+
+/* Read spilled edges with seqs in [seq_lo, seq_hi): edges[k] (may be NULL)
+ * and words[q * (seq_hi - seq_lo) + k] (may be NULL) for the k-th seq.
+ * *held_lo / *held_hi (may be NULL) get the seq range the FIFO holds; a
+ * range outside it is MN_ERR_INVALID_ARG (the held range is still reported).
+ * Waits for the graph's stream first. */
+mn_status mn_read_spill(mn_graph *g, uint64_t seq_lo, uint64_t seq_hi, mn_edge *edges, uint32_t *words,
+                        uint64_t *held_lo, uint64_t *held_hi);
+
 /* Record each insert batch's kernel chain (ingest, adjacency update,
  * filtering, work units, order choice, enumeration of dS- and dS+) as one
  * CUDA graph and launch it as a whole: one launch instead of a few dozen.
@@ -484,6 +512,7 @@ typedef struct {
     uint64_t filter_changes;       /* vertex-set memberships the filtering passes changed */
     uint64_t graph_launches;       /* insert batches launched as one CUDA graph (mn_set_graph_capture) */
     uint64_t graph_instantiations; /* graph instantiations (the rest were updated in place) */
+    uint64_t spill_bytes;          /* bytes copied to the host spill (mn_set_spill) */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

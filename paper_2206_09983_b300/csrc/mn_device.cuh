@@ -1494,3 +1494,129 @@ __global__ void k_delete_apply(const unsigned long long *seqs, uint32_t n, uint3
 }
 
 }  // namespace mn
+
+// ------------------------------------------------------------------ sorted fetch
+
+namespace mn {
+
+// Lexicographic order of two result records: the vertex ids f(u_0..u_{nv-1})
+// (u32), then the edge seqs (u64, at byte offset goff) -- the order of the
+// rows (f..., seq...) a caller sorts by.
+__device__ __forceinline__ bool rec_less(const uint8_t *recs, uint32_t rb, uint32_t nv, uint32_t ne,
+                                         uint32_t goff, uint32_t a, uint32_t b)
+{
+    const uint32_t *va = reinterpret_cast<const uint32_t *>(recs + (size_t)a * rb);
+    const uint32_t *vb = reinterpret_cast<const uint32_t *>(recs + (size_t)b * rb);
+    for (uint32_t u = 0; u < nv; u++)
+        if (va[u] != vb[u]) return va[u] < vb[u];
+    const unsigned long long *ga = reinterpret_cast<const unsigned long long *>(recs + (size_t)a * rb + goff);
+    const unsigned long long *gb = reinterpret_cast<const unsigned long long *>(recs + (size_t)b * rb + goff);
+    for (uint32_t e = 0; e < ne; e++)
+        if (ga[e] != gb[e]) return ga[e] < gb[e];
+    return a < b;                 // equal records keep their order (stable)
+}
+
+// Runs of MERGE_ITEMS records sorted by one thread each (insertion sort of
+// their indices): the first merge pass then starts at runs of MERGE_ITEMS, so
+// that no thread's outputs straddle two merged pairs.
+__global__ void k_rec_sort_runs(const uint8_t *recs, uint32_t rb, uint32_t nv, uint32_t ne, uint32_t goff,
+                                uint32_t *idx, uint32_t n)
+{
+    const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
+    if (o >= n) return;
+    const uint32_t m = min((uint32_t)MERGE_ITEMS, n - o);
+    uint32_t r[MERGE_ITEMS];
+#pragma unroll
+    for (int k = 0; k < MERGE_ITEMS; k++) r[k] = o + k;
+    for (uint32_t k = 1; k < m; k++) {
+        const uint32_t x = r[k];
+        uint32_t j = k;
+        while (j > 0 && rec_less(recs, rb, nv, ne, goff, x, r[j - 1])) { r[j] = r[j - 1]; j--; }
+        r[j] = x;
+    }
+    for (uint32_t k = 0; k < m; k++) idx[o + k] = r[k];
+}
+
+// One pass of a bottom-up merge sort of record indices: neighbouring sorted
+// runs of length R merged into runs of 2R (merge path, MERGE_ITEMS outputs
+// per thread).
+__global__ void k_rec_merge_pass(const uint8_t *recs, uint32_t rb, uint32_t nv, uint32_t ne, uint32_t goff,
+                                 const uint32_t *src, uint32_t *dst, uint32_t n, uint32_t R)
+{
+    const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
+    if (o >= n) return;
+    const uint32_t pbase = o / (2 * R) * (2 * R);
+    const uint32_t nA = min(R, n - pbase);
+    const uint32_t nB = min(R, n - pbase - nA);
+    const uint32_t *A = src + pbase, *Bv = A + nA;
+    const uint32_t d = o - pbase;
+    uint32_t lo = d > nB ? d - nB : 0, hi = min(d, nA);
+    while (lo < hi) {                       // first i with B[d - 1 - i] < A[i]
+        const uint32_t mid = (lo + hi) >> 1;
+        if (!rec_less(recs, rb, nv, ne, goff, Bv[d - 1 - mid], A[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t i = lo, j = d - lo;
+    for (int t = 0; t < MERGE_ITEMS && o + t < pbase + nA + nB; t++) {
+        const bool takeA = j >= nB || (i < nA && !rec_less(recs, rb, nv, ne, goff, Bv[j], A[i]));
+        dst[o + t] = takeA ? A[i++] : Bv[j++];
+    }
+}
+
+// out[k] = record idx[k] (rb bytes each, a multiple of 8).  An index out of
+// range (a broken permutation) reads nothing and sets *status.
+__global__ void k_rec_gather(const uint8_t *recs, uint32_t rb, const uint32_t *idx, uint32_t n, uint8_t *out,
+                             uint32_t *status)
+{
+    const uint32_t words = rb / 8;
+    const size_t total = (size_t)n * words;
+    for (size_t w = (size_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        const size_t k = w / words, x = w % words;
+        const uint32_t i = idx[k];
+        if (i >= n) {
+            atomicOr(status, 1u);
+            reinterpret_cast<unsigned long long *>(out)[w] = 0;
+            continue;
+        }
+        reinterpret_cast<unsigned long long *>(out)[w] =
+            reinterpret_cast<const unsigned long long *>(recs + (size_t)i * rb)[x];
+    }
+}
+
+}  // namespace mn
+
+// ------------------------------------------------------------------ host spill
+
+namespace mn {
+
+// One spilled edge: the caller's record, its seq, and the DEBI word of every
+// query at the time it left the window (Sec. IV-A, external memory: edges
+// leaving the in-memory window are written out with their index entries).
+struct SpillRec {
+    mn_edge e;
+    unsigned long long seq;
+};
+
+// Pack the edges at seqs [seq_lo, seq_lo + n) from the ring (SoA) into
+// records and their DEBI words ([q][n]) for the copy to host memory.
+__global__ void k_spill_pack(uint64_t seq_lo, uint32_t n, uint32_t cap_mask, const uint32_t *r_src,
+                             const uint32_t *r_dst, const uint8_t *r_label, const int32_t *r_attr,
+                             const int64_t *r_ts, uint32_t nq, uint32_t *const *debi, SpillRec *out,
+                             uint32_t *words, const uint32_t *status)
+{
+    if (*status) return;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t slot = (uint32_t)(seq_lo + i) & cap_mask;
+    SpillRec r;
+    r.e.src = r_src[slot];
+    r.e.dst = r_dst[slot];
+    r.e.label = r_label[slot];
+    r.e.attr = r_attr[slot];
+    r.e.ts = r_ts[slot];
+    r.seq = seq_lo + i;
+    out[i] = r;
+    for (uint32_t q = 0; q < nq; q++) words[(size_t)q * n + i] = debi[q][slot];
+}
+
+}  // namespace mn

@@ -66,6 +66,7 @@ struct QueryHost {
     uint32_t *debi = nullptr;
     uint8_t *out[2] = {nullptr, nullptr};
     unsigned long long out_cap[2] = {0, 0};
+    uint64_t sorted_batch[2] = {0, 0};   // batch whose list is sorted in place (MN_FETCH_SORTED)
 };
 
 uint64_t next_pow2(uint64_t x)
@@ -199,6 +200,13 @@ struct mn_graph {
     uint64_t n_samples = 0, explore_round = 0;
     uint32_t *d_temporal = nullptr;
     unsigned long long *d_nsamples = nullptr;   // samples ever logged (ring position)
+    // host spill of expired edges (mn_set_spill): a pinned FIFO of records and
+    // of the DEBI words of every query at expiry; [spill_lo, spill_hi) held
+    SpillRec *h_spill = nullptr;
+    uint32_t *h_spill_words = nullptr;   // [max_queries][spill_cap]
+    uint64_t spill_cap = 0, spill_lo = 0, spill_hi = 0;
+    SpillRec *d_spill = nullptr;         // device staging: max_batch records + words
+    uint32_t *d_spill_words = nullptr;
     bool use_graph = false;              // record each eligible insert batch as a CUDA graph
     cudaGraphExec_t gexec = nullptr;     // updated in place batch after batch
     std::vector<cudaEvent_t> ev_pool;
@@ -700,6 +708,46 @@ mn_status ensure_seed_cap(mn_graph *g, int phase, uint64_t need)
     uint64_t cap = next_pow2(need);
     TRY(dalloc(g, &g->d_seeds[phase], cap, false));
     g->seed_cap[phase] = cap;
+    return MN_OK;
+}
+
+// ---------------------------------------------------------------- host spill
+
+// Copy the expired edges [seq_lo, seq_lo + x) and their DEBI words into the
+// host FIFO (asynchronous: the copies complete with the graph's stream, at
+// the latest by the next call that waits on it); the oldest spilled edges
+// are overwritten when it is full.  Chunks of at most max_batch edges go
+// through the device staging buffer.
+mn_status spill_expired(mn_graph *g, uint64_t seq_lo, uint64_t x)
+{
+    if (!g->h_spill || x == 0) return MN_OK;
+    const uint32_t nq = (uint32_t)g->queries.size();
+    for (uint64_t done = 0; done < x;) {
+        const uint64_t m = std::min<uint64_t>(x - done, g->max_batch);
+        k_spill_pack<<<cdiv(m, 256), 256, 0, g->stream>>>(seq_lo + done, (uint32_t)m, g->cap_mask, g->r_src,
+                                                          g->r_dst, g->r_label, g->r_attr, g->r_ts, nq,
+                                                          g->d_debi_ptrs, g->d_spill, g->d_spill_words,
+                                                          &g->d_ctrl->status);
+        CKL();
+        // the FIFO position of seq s is s mod spill_cap: copy in at most two pieces
+        for (uint64_t k = 0; k < m;) {
+            const uint64_t s0 = seq_lo + done + k;
+            const uint64_t pos = s0 % g->spill_cap;
+            const uint64_t len = std::min<uint64_t>(m - k, g->spill_cap - pos);
+            CK(cudaMemcpyAsync(g->h_spill + pos, g->d_spill + k, len * sizeof(SpillRec), cudaMemcpyDeviceToHost,
+                               g->stream));
+            for (uint32_t q = 0; q < nq; q++)
+                CK(cudaMemcpyAsync(g->h_spill_words + (size_t)q * g->spill_cap + pos,
+                                   g->d_spill_words + (size_t)q * m + k, len * sizeof(uint32_t),
+                                   cudaMemcpyDeviceToHost, g->stream));
+            g->stats.spill_bytes += len * (sizeof(SpillRec) + nq * sizeof(uint32_t));
+            k += len;
+        }
+        done += m;
+    }
+    // expiries are contiguous from the window start at mn_set_spill on
+    g->spill_hi = seq_lo + x;
+    if (g->spill_hi - g->spill_lo > g->spill_cap) g->spill_lo = g->spill_hi - g->spill_cap;
     return MN_OK;
 }
 
@@ -1241,6 +1289,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     const uint64_t ex_lo = g->lo;
     if (x) {
         TRY(filter_mark(g, g->lo, x, nullptr));
+        TRY(spill_expired(g, g->lo, x));
         stage_begin(g);
         k_expire<<<cdiv(x, 256), 256, 0, g->stream>>>(g->lo, (uint32_t)x, g->cap_mask, g->L,
                                                       (uint32_t)g->queries.size(), g->d_debi_ptrs,
@@ -1435,6 +1484,8 @@ void mn_destroy_graph(mn_graph *g)
     if (g->tune_e1) cudaEventDestroy(g->tune_e1);
     if (g->h_ctrl) cudaFreeHost(g->h_ctrl);
     if (g->h_fstage) cudaFreeHost(g->h_fstage);
+    if (g->h_spill) cudaFreeHost(g->h_spill);
+    if (g->h_spill_words) cudaFreeHost(g->h_spill_words);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1806,14 +1857,52 @@ mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id,
     if (sign != 1 && sign != -1) return fail(g, MN_ERR_INVALID_ARG, "sign must be +1 or -1");
     if (batch_id != g->batch_id || batch_id == 0)
         return fail(g, MN_ERR_STATE, "only the last batch's lists are kept");
+    if (dst_flags & ~(MN_DST_DEVICE | MN_FETCH_SORTED)) return fail(g, MN_ERR_INVALID_ARG, "unknown fetch flags");
     const int s = sign > 0 ? 0 : 1;
-    const QueryHost &Q = g->queries[query_id];
+    QueryHost &Q = g->queries[query_id];
     const uint64_t total = s == 0 ? g->count_pos[query_id] : g->count_neg[query_id];
     const uint64_t avail = std::min<uint64_t>(total, Q.out_cap[s]);
     if (offset >= avail || max_records == 0) return MN_OK;
     const uint64_t cnt = std::min<uint64_t>(max_records, avail - offset);
     if (!dst) return fail(g, MN_ERR_INVALID_ARG, "dst is NULL");
     CK(cudaSetDevice(g->device));
+    if ((dst_flags & MN_FETCH_SORTED) && Q.sorted_batch[s] != batch_id && avail > 1) {
+        // sort the whole list once for this batch, in place: runs of
+        // MERGE_ITEMS sorted per thread, index merge passes, then one gather
+        // through a scratch list
+        uint32_t *ia = nullptr, *ib = nullptr, *bad = nullptr;
+        uint8_t *tmp = nullptr;
+        mn_status st = dalloc(g, &ia, avail, false);
+        if (st == MN_OK) st = dalloc(g, &ib, avail, false);
+        if (st == MN_OK) st = dalloc(g, &tmp, avail * Q.rec_bytes, false);
+        if (st == MN_OK) st = dalloc(g, &bad, 1, true);
+        uint32_t h_bad = 0;
+        if (st == MN_OK) {
+            const uint32_t n = (uint32_t)avail;
+            const uint32_t blocks = cdiv(cdiv(n, MERGE_ITEMS), 256);
+            k_rec_sort_runs<<<blocks, 256, 0, g->stream>>>(Q.out[s], Q.rec_bytes, Q.nv, Q.ne, Q.goff, ia, n);
+            for (uint64_t R = MERGE_ITEMS; R < n; R *= 2) {
+                k_rec_merge_pass<<<blocks, 256, 0, g->stream>>>(Q.out[s], Q.rec_bytes, Q.nv, Q.ne, Q.goff,
+                                                                 ia, ib, n, (uint32_t)R);
+                std::swap(ia, ib);
+            }
+            k_rec_gather<<<(uint32_t)g->nsm * 8, 256, 0, g->stream>>>(Q.out[s], Q.rec_bytes, ia, n, tmp, bad);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e == cudaSuccess && !h_bad)
+                e = cudaMemcpyAsync(Q.out[s], tmp, avail * Q.rec_bytes, cudaMemcpyDeviceToDevice, g->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+            if (e != cudaSuccess) st = fail(g, MN_ERR_DEVICE, std::string("sorted fetch: ") + cudaGetErrorString(e));
+            else if (h_bad) st = fail(g, MN_ERR_DEVICE, "sorted fetch: index out of range in the permutation");
+        }
+        if (ia) dfree(g, ia, avail * sizeof(uint32_t));
+        if (ib) dfree(g, ib, avail * sizeof(uint32_t));
+        if (tmp) dfree(g, tmp, avail * Q.rec_bytes);
+        if (bad) dfree(g, bad, sizeof(uint32_t));
+        if (st != MN_OK) return st;
+        Q.sorted_batch[s] = batch_id;
+    }
     CK(cudaMemcpyAsync(dst, Q.out[s] + offset * Q.rec_bytes, cnt * Q.rec_bytes,
                        (dst_flags & MN_DST_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        g->stream));
@@ -2431,6 +2520,51 @@ mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *ma
 
 // Test hook: per-warp loop budget of the enumerator (0 restores no limit).
 // A tiny budget makes a bounded device loop give up and report MN_ERR_TIMEOUT.
+mn_status mn_set_spill(mn_graph *g, uint64_t capacity_edges)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (g->h_spill) return fail(g, MN_ERR_STATE, "the spill is set already");
+    if (capacity_edges == 0) return fail(g, MN_ERR_INVALID_ARG, "capacity must be > 0");
+    CK(cudaSetDevice(g->device));
+    if (cudaMallocHost((void **)&g->h_spill, capacity_edges * sizeof(SpillRec)) != cudaSuccess ||
+        cudaMallocHost((void **)&g->h_spill_words, capacity_edges * g->max_queries * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        if (g->h_spill) cudaFreeHost(g->h_spill);
+        g->h_spill = nullptr;
+        return fail(g, MN_ERR_OOM, "pinned host memory for the spill");
+    }
+    TRY(dalloc(g, &g->d_spill, g->max_batch, false));
+    TRY(dalloc(g, &g->d_spill_words, (uint64_t)g->max_batch * g->max_queries, false));
+    g->spill_cap = capacity_edges;
+    g->spill_lo = g->spill_hi = g->lo;
+    return MN_OK;
+}
+
+mn_status mn_read_spill(mn_graph *g, uint64_t seq_lo, uint64_t seq_hi, mn_edge *edges, uint32_t *words,
+                        uint64_t *held_lo, uint64_t *held_hi)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (!g->h_spill) return fail(g, MN_ERR_STATE, "no spill (mn_set_spill)");
+    CK(cudaSetDevice(g->device));
+    CK(cudaStreamSynchronize(g->stream));      // the copies of the last expiry have landed
+    if (held_lo) *held_lo = g->spill_lo;
+    if (held_hi) *held_hi = g->spill_hi;
+    if (seq_hi <= seq_lo) return MN_OK;
+    if (seq_lo < g->spill_lo || seq_hi > g->spill_hi)
+        return fail(g, MN_ERR_INVALID_ARG, "seqs outside the spilled range");
+    const uint32_t nq = (uint32_t)g->queries.size();
+    for (uint64_t s = seq_lo; s < seq_hi; s++) {
+        const uint64_t pos = s % g->spill_cap;
+        if (edges) edges[s - seq_lo] = g->h_spill[pos].e;
+        if (words)
+            for (uint32_t q = 0; q < nq; q++)
+                words[(size_t)q * (seq_hi - seq_lo) + (s - seq_lo)] = g->h_spill_words[(size_t)q * g->spill_cap + pos];
+    }
+    return MN_OK;
+}
+
 mn_status mn_set_graph_capture(mn_graph *g, int32_t enable)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");

@@ -27,6 +27,7 @@ MN_DEVICE_PTR = 0x1
 MN_COUNT_ONLY = 0x2
 MN_ASYNC = 0x4
 MN_DST_DEVICE = 0x1
+MN_FETCH_SORTED = 0x2
 MN_MAX_QV = 16
 MN_MAX_QE = 16
 
@@ -43,7 +44,7 @@ EXPORTS = [
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
-    "mn_set_graph_capture",
+    "mn_set_graph_capture", "mn_set_spill", "mn_read_spill",
     "mn_last_error",
 ]
 MN_WAIT_HOLD = 0x1
@@ -87,7 +88,8 @@ class Stats(C.Structure):
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
                 ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64),
                 ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64),
-                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
+                ("spill_bytes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -163,6 +165,8 @@ def load(path: str | None = None):
         "mn_set_presplit": (S, [P, C.c_float]),
         "mn_set_filtering": (S, [P, C.c_int32]),
         "mn_set_graph_capture": (S, [P, C.c_int32]),
+        "mn_set_spill": (S, [P, U64]),
+        "mn_read_spill": (S, [P, U64, U64, P, P, C.POINTER(U64), C.POINTER(U64)]),
         "mn_read_filter": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_int32), P, P]),
         "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
@@ -357,8 +361,10 @@ class Graph:
                                               flags, C.byref(r)))
         return self._result(r)
 
-    def fetch(self, qid: int, sign: int, offset: int = 0, max_records: int | None = None):
-        """Records of the last batch as (vertices [n, nv] uint32, seqs [n, ne] uint64)."""
+    def fetch(self, qid: int, sign: int, offset: int = 0, max_records: int | None = None,
+              sorted: bool = False):
+        """Records of the last batch as (vertices [n, nv] uint32, seqs [n, ne] uint64);
+        sorted=True asks the device for ascending (vertices, seqs) order."""
         nv, ne, rb = self.layouts[qid]
         total = (self.last.count_pos if sign > 0 else self.last.count_neg)[qid]
         m = total - offset if max_records is None else max_records
@@ -366,7 +372,8 @@ class Graph:
         buf = np.empty(m * rb, dtype=np.uint8)
         nw = C.c_uint64()
         self._check(self._lib.mn_fetch_embeddings(self._h, self.last.batch_id, qid, sign, offset, m,
-                                                  buf.ctypes.data if m else None, 0, C.byref(nw)))
+                                                  buf.ctypes.data if m else None,
+                                                  MN_FETCH_SORTED if sorted else 0, C.byref(nw)))
         n = nw.value
         goff = (4 * nv + 7) // 8 * 8
         rows = buf[: n * rb].reshape(n, rb)
@@ -464,6 +471,19 @@ class Graph:
 
     def autotune(self, batches_per_config: int = 1):
         self._check(self._lib.mn_autotune(self._h, batches_per_config))
+
+    def set_spill(self, capacity_edges: int):
+        """Spill expired edges with their DEBI words to a pinned host FIFO (mn_set_spill)."""
+        self._check(self._lib.mn_set_spill(self._h, capacity_edges))
+
+    def read_spill(self, lo: int, hi: int, nq: int):
+        """(edges EDGE_DTYPE[hi - lo], words uint32[nq][hi - lo], (held_lo, held_hi))."""
+        e = np.zeros(max(0, hi - lo), dtype=EDGE_DTYPE)
+        w = np.zeros((nq, max(0, hi - lo)), dtype=np.uint32)
+        a, b = C.c_uint64(), C.c_uint64()
+        self._check(self._lib.mn_read_spill(self._h, lo, hi, e.ctypes.data if hi > lo else None,
+                                            w.ctypes.data if hi > lo and nq else None, C.byref(a), C.byref(b)))
+        return e, w, (a.value, b.value)
 
     def set_graph_capture(self, on: bool):
         """Launch each eligible insert batch as one CUDA graph (mn_set_graph_capture)."""

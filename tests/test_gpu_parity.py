@@ -279,3 +279,31 @@ def test_empty_batch_and_single_edge_query():
             g.insert(M.edges_from_stream(s, lo, hi))
         wlo, whi, _ = g.info()
         assert g.count_static(qi) == oracle.count_static(s, wlo, whi, q1)
+
+
+def test_sorted_fetch_is_the_oracle_order_without_host_sorting():
+    """MN_FETCH_SORTED: the device sorts a list by (vertex tuple, edge-seq
+    tuple) -- records of odd and even vertex counts (padded layouts), lists
+    of 10^5 records (many merge passes), windows at offsets of the sorted
+    list, and a later unsorted fetch of the same batch stays sorted."""
+    s = gen.uniform_stream(300, 8000, 2, 2, seed=0x4D4E00B0)
+    qs = [gen.q_path(2, iso=False), gen.q_path(3, labels=[0, 1, 0], iso=True, temporal="chain")]
+    with make_graph(s, window=5000, max_batch=5000) as g:
+        for q in qs:
+            g.register_query(q)
+        g.insert(M.edges_from_stream(s, 0, 5000), count_only=True)
+        g.insert(M.edges_from_stream(s, 5000, 8000))
+        for qi, q in enumerate(qs):
+            nv = q["nv"]
+            for sign, (blo, bhi) in ((+1, (5000, 8000)), (-1, (0, 3000))):
+                want = oracle.delta(s, 0, 8000, blo, bhi, q)
+                v, sq = g.fetch(qi, sign, sorted=True)
+                got = np.concatenate([v.astype(np.uint64), sq], axis=1)
+                assert got.shape == want.shape and (got == want).all(), (qi, sign)
+                if len(want) > 1000:
+                    v2, s2 = g.fetch(qi, sign, offset=777, max_records=500, sorted=True)
+                    part = np.concatenate([v2.astype(np.uint64), s2], axis=1)
+                    assert (part == want[777:1277]).all()
+                v3, s3 = g.fetch(qi, sign)            # the list stays sorted for this batch
+                assert (np.concatenate([v3.astype(np.uint64), s3], axis=1) == want).all()
+        assert max(len(oracle.delta(s, 0, 8000, 5000, 8000, q)) for q in qs) > 100000
