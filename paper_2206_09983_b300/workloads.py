@@ -86,23 +86,23 @@ def c3_query(nv, edges, elabels, vlabels):
 # embeddings, and the search kept the largest count it could certify (0 to
 # 5,997 new embeddings per batch): uneven queries by construction.
 RMAT20_C3_QUERIES = [
-    (0, 6, [(1, 0), (1, 2), (3, 0), (4, 0), (5, 0)], [7, 7, 6, 7, 7], [0, 3, 0, 0, 3, 3]),  # 10442
+    (0, 6, [(1, 0), (1, 2), (3, 0), (4, 0), (5, 0)], [6, 7, 7, 7, 7], [1, 0, 2, 2, 1, 3]),  # 39954
     (1, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (0, 4), (2, 5)], [6, 5, 6, 1, 3, 4, 6, 6, 1], [None, 1, 1, 2, 1, 2, 2]),  # 0
     (2, 4, [(0, 1), (0, 2), (2, 3)], [0, 7, 5], [1, 3, 1, 2]),  # 9118
     (3, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (2, 0)], [2, 4, 0, 0, 0], [None, None, 3, 2]),  # 4637
     (4, 7, [(0, 1), (2, 1), (1, 3), (0, 4), (1, 5), (6, 3)], [7, 2, 7, 5, 7, 5], [1, 1, 2, 1, 1, 0, 3]),  # 68644
     (5, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 2), (3, 1)], [2, 1, 0, 4, 4, 3], [2, 0, 3, 0]),  # 3
-    (6, 7, [(1, 0), (1, 2), (0, 3), (4, 3), (3, 5), (4, 6)], [5, 6, 7, 5, 5, 2], [0, 2, 3, 2, 2, 0, 1]),  # 70543
+    (6, 7, [(1, 0), (1, 2), (0, 3), (4, 3), (3, 5), (4, 6)], [3, 4, 7, 4, 4, 5], [2, 2, 2, 1, 1, 2, 1]),  # 43161
     (7, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (3, 1)], [3, 5, 0, 0, 1], [2, None, 0, 2]),  # 77
     (8, 5, [(0, 1), (2, 0), (3, 1), (2, 4)], [4, 2, 2, 2], [3, 0, 3, 2, 2]),  # 108316
     (9, 8, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 7), (7, 0), (6, 3)], [2, 7, 4, 4, 6, 0, 5, 7, 2], [2, 2, 2, 1, 1, 0, 0, 0]),  # 0
     (10, 6, [(0, 1), (0, 2), (3, 2), (4, 1), (1, 5)], [6, 1, 7, 3, 4], [1, 1, 1, 3, 3, 2]),  # 49974
     (11, 7, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 6), (6, 0), (2, 0), (3, 6)], [6, 6, 7, 1, 4, 6, 0, 7, 7], [3, 1, 0, 3, 2, 1, 2]),  # 0
-    (12, 8, [(1, 0), (2, 0), (3, 2), (3, 4), (5, 0), (6, 1), (7, 0)], [6, 6, 4, 7, 4, 6, 4], [2, 1, 1, 0, 3, 3, 0, 3]),  # 88714
+    (12, 8, [(1, 0), (2, 0), (3, 2), (3, 4), (5, 0), (6, 1), (7, 0)], [6, 4, 6, 6, 2, 3, 6], [0, 3, 3, 1, 1, 3, 3, 2]),  # 98395
     (13, 4, [(0, 1), (1, 2), (2, 3), (3, 0), (2, 0), (1, 3)], [4, 2, 2, 0, 3, 3], [None, 2, 2, 0]),  # 4
     (14, 4, [(0, 1), (2, 0), (3, 2)], [5, 6, 1], [2, 2, None, 0]),  # 40888
     (15, 5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (0, 3), (4, 1)], [7, 2, 1, 5, 6, 0, 2], [3, 1, 2, 1, 2]),  # 4
-    (16, 7, [(1, 0), (2, 0), (1, 3), (4, 3), (5, 4), (6, 0)], [7, 6, 7, 5, 7, 2], [3, 1, 1, 1, 1, 1, 2]),  # 81793
+    (16, 7, [(1, 0), (2, 0), (1, 3), (4, 3), (5, 4), (6, 0)], [7, 5, 7, 6, 1, 4], [1, 3, 0, 0, 3, 0, 3]),  # 41214
     (17, 5, [(0, 1), (1, 2), (2, 3), (3, 4), (4, 0), (3, 0)], [3, 7, 5, 0, 4, 6], [3, 2, 3, 2, None]),  # 182
     (18, 4, [(0, 1), (1, 2), (3, 0)], [5, 1, 3], [1, 1, 3, 1]),  # 9266
     (19, 3, [(0, 1), (1, 2), (2, 0)], [-1, 0, 0], [None, 1, 2]),  # 5997
