@@ -7,9 +7,11 @@
 //   k_sort_tiles /    sort the batch's adjacency entries by (vertex, label,
 //   k_merge_pass      neighbour), ties by arrival
 //   k_delta_finalize  delta entries + per-(vertex,label) degree counts
-//   k_live_count /    drop entries that left the window from the base
-//   k_compact         adjacency (memory recycling, Sec. IV-A)
-//   k_merge_csr       merge base and delta into the new sorted adjacency
+//   k_live_count /    live entries per base tile, the delta entries' anchors
+//   k_delta_anchor    in the base
+//   k_merge_live      merge base and delta into the new sorted adjacency in
+//                     one pass, dropping the entries that left the window
+//                     (memory recycling, Sec. IV-A)
 //   k_scan_*          offsets of every (vertex, label) segment
 //   k_seeds_*         work units: one per (batch edge, query, query edge)
 //                     whose DEBI bit is set (Sec. VI "Work decomposition"),
@@ -150,6 +152,18 @@ struct Adj4 {
     uint32_t *key[NPROB], *nbr[NPROB], *s32[NPROB];
 };
 
+// p[t] of a kernel parameter array for a run-time t (blockIdx.y = problem),
+// by selects: indexing the parameter array itself copies it to local memory
+template <class T>
+__device__ __forceinline__ T sel4(T const (&p)[NPROB], int t)
+{
+    T r = p[0];
+#pragma unroll
+    for (int k = 1; k < NPROB; k++)
+        if (t == k) r = p[k];
+    return r;
+}
+
 struct IngestParams {
     const mn_edge *edges;
     uint32_t n, n_pad;
@@ -243,8 +257,8 @@ __global__ void __launch_bounds__(1024) k_sort_tiles(SortSet s, const uint32_t *
     if (*status) return;
     __shared__ unsigned long long sk[SORT_TILE];
     __shared__ uint32_t sv[SORT_TILE];
-    unsigned long long *key = s.k[blockIdx.y];
-    uint32_t *val = s.v[blockIdx.y];
+    unsigned long long *key = sel4(s.k, blockIdx.y);
+    uint32_t *val = sel4(s.v, blockIdx.y);
     const uint32_t base = blockIdx.x * SORT_TILE;
     for (int i = threadIdx.x; i < SORT_TILE; i += blockDim.x) {
         sk[i] = key[base + i];
@@ -281,10 +295,10 @@ __global__ void k_merge_pass(SortSet src, SortSet dst, uint32_t n, uint32_t R,
                              const uint32_t *status)
 {
     if (*status) return;
-    const unsigned long long *ks = src.k[blockIdx.y];
-    const uint32_t *vs = src.v[blockIdx.y];
-    unsigned long long *kd = dst.k[blockIdx.y];
-    uint32_t *vd = dst.v[blockIdx.y];
+    const unsigned long long *ks = sel4(src.k, blockIdx.y);
+    const uint32_t *vs = sel4(src.v, blockIdx.y);
+    unsigned long long *kd = sel4(dst.k, blockIdx.y);
+    uint32_t *vd = sel4(dst.v, blockIdx.y);
     const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
     if (o >= n) return;
     const uint32_t pbase = o / (2 * R) * (2 * R);
@@ -317,12 +331,12 @@ __global__ void k_delta_finalize(SortSet s, Adj4 d, const mn_edge *edges, uint32
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int t = blockIdx.y;
-    const unsigned long long k = s.k[t][i];
-    const uint32_t v = s.v[t][i];
+    const unsigned long long k = sel4(s.k, t)[i];
+    const uint32_t v = sel4(s.v, t)[i];
     const uint32_t key = (uint32_t)(k >> 32);
-    d.key[t][i] = key;
-    d.nbr[t][i] = t < 2 ? (uint32_t)k : ((t & 1) ? edges[v].src : edges[v].dst);
-    d.s32[t][i] = (uint32_t)(seq0 + v);
+    sel4(d.key, t)[i] = key;
+    sel4(d.nbr, t)[i] = t < 2 ? (uint32_t)k : ((t & 1) ? edges[v].src : edges[v].dst);
+    sel4(d.s32, t)[i] = (uint32_t)(seq0 + v);
     if (t == 0) atomicAdd(&cnt0[key], 1u);
     if (t == 1) atomicAdd(&cnt1[key], 1u);
 }
@@ -337,7 +351,7 @@ __global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_
                                                      const uint32_t *status)
 {
     if (*status) return;
-    const uint32_t *s = a.s32[blockIdx.y];
+    const uint32_t *s = sel4(a.s32, blockIdx.y);
     const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
     uint32_t c = 0;
 #pragma unroll
@@ -347,7 +361,7 @@ __global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_
     }
     uint32_t total;
     block_excl_scan(c, &total);
-    if (threadIdx.x == 0) blk.key[blockIdx.y][blockIdx.x] = total;
+    if (threadIdx.x == 0) sel4(blk.key, blockIdx.y)[blockIdx.x] = total;
 }
 
 // In-place exclusive scan of nb values per problem (one block per problem,
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_
 __global__ void __launch_bounds__(1024) k_scan_blocks(Adj4 b, uint32_t nb, const uint32_t *status)
 {
     if (*status) return;
-    uint32_t *a = b.key[blockIdx.x];
+    uint32_t *a = sel4(b.key, blockIdx.x);
     __shared__ uint32_t carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -371,70 +385,133 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(Adj4 b, uint32_t nb, const
     }
 }
 
-// Stable compaction of the live base entries into the merge input.
-__global__ void __launch_bounds__(CBLK) k_compact(Adj4 a, Adj4 out, uint32_t n, uint32_t lo32,
-                                                  uint32_t live_span, Adj4 blk,
-                                                  const uint32_t *status)
+// Merge of the base adjacency with the sorted delta, with the entries that
+// left the window dropped on the way (memory recycling, Sec. IV-A), in one
+// pass over the base.  With a(j) = the number of base entries (live or not)
+// ordered before delta entry j -- ties take the base first, so a(j) counts
+// base keys <= key(j) -- the merged position of a live base entry i is
+// (live entries before i) + #{j : a(j) <= i}, and that of delta entry j is
+// (live entries before a(j)) + j.  Neighbour order (problems 0, 1) compares
+// (key, nbr); arrival order (2, 3) compares key only.
+
+__device__ __forceinline__ unsigned long long adj_key(const uint32_t *K, const uint32_t *N, bool by_nbr,
+                                                      uint32_t i)
 {
-    if (*status) return;
-    const int t0 = blockIdx.y;
-    const uint32_t *K = a.key[t0], *N = a.nbr[t0], *S = a.s32[t0];
-    uint32_t *TK = out.key[t0], *TN = out.nbr[t0], *TS = out.s32[t0];
-    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
-    uint32_t sv[CITEMS];
-    uint32_t c = 0;
-#pragma unroll
-    for (int t = 0; t < CITEMS; t++) {
-        uint32_t i = base + t;
-        sv[t] = i < n ? S[i] : 0;
-        c += (i < n && (uint32_t)(sv[t] - lo32) < live_span) ? 1u : 0u;
-    }
-    uint32_t total;
-    uint32_t pos = block_excl_scan(c, &total) + blk.key[t0][blockIdx.x];
-#pragma unroll
-    for (int t = 0; t < CITEMS; t++) {
-        uint32_t i = base + t;
-        if (i < n && (uint32_t)(sv[t] - lo32) < live_span) {
-            TK[pos] = K[i];
-            TN[pos] = N[i];
-            TS[pos] = sv[t];
-            pos++;
-        }
-    }
+    return ((unsigned long long)K[i] << 32) | (by_nbr ? N[i] : 0u);
 }
 
-// Merge the compacted base A (nA entries) with the sorted delta B (nB) into
-// the new adjacency.  Neighbour order (problems 0, 1) compares (key, nbr);
-// arrival order (2, 3) compares key only; ties take the base first (older).
-__global__ void k_merge_csr(Adj4 A, Adj4 B, Adj4 O, uint32_t nA, uint32_t nB,
-                            const uint32_t *status)
+// a(j) for every delta entry, by binary search over the whole base
+// (nA entries); blockIdx.y = problem.
+__global__ void k_delta_anchor(Adj4 A, Adj4 B, uint32_t nA, uint32_t nB, Adj4 anchor,
+                               const uint32_t *status)
 {
     if (*status) return;
     const int t = blockIdx.y;
-    const uint32_t *AK = A.key[t], *AN = A.nbr[t], *AS = A.s32[t];
-    const uint32_t *BK = B.key[t], *BN = B.nbr[t], *BS = B.s32[t];
-    uint32_t *OK = O.key[t], *ON = O.nbr[t], *OS = O.s32[t];
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nB) return;
     const bool by_nbr = t < 2;
-    const uint32_t n = nA + nB;
-    const uint32_t o = (blockIdx.x * blockDim.x + threadIdx.x) * MERGE_ITEMS;
-    if (o >= n) return;
-    auto keyA = [&](uint32_t i) {
-        return ((unsigned long long)AK[i] << 32) | (by_nbr ? AN[i] : 0u);
-    };
-    auto keyB = [&](uint32_t i) {
-        return ((unsigned long long)BK[i] << 32) | (by_nbr ? BN[i] : 0u);
-    };
-    uint32_t lo = o > nB ? o - nB : 0, hi = min(o, nA);
+    const unsigned long long kb = adj_key(sel4(B.key, t), sel4(B.nbr, t), by_nbr, j);
+    const uint32_t *AK = sel4(A.key, t), *AN = sel4(A.nbr, t);
+    uint32_t lo = 0, hi = nA;
     while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (keyA(mid) <= keyB(o - 1 - mid)) lo = mid + 1;
+        const uint32_t mid = (lo + hi) >> 1;
+        if (adj_key(AK, AN, by_nbr, mid) <= kb) lo = mid + 1;
         else hi = mid;
     }
-    uint32_t i = lo, j = o - lo;
-    for (int u = 0; u < MERGE_ITEMS && o + u < n; u++) {
-        bool takeA = j >= nB || (i < nA && keyA(i) <= keyB(j));
-        if (takeA) { OK[o + u] = AK[i]; ON[o + u] = AN[i]; OS[o + u] = AS[i]; i++; }
-        else       { OK[o + u] = BK[j]; ON[o + u] = BN[j]; OS[o + u] = BS[j]; j++; }
+    sel4(anchor.key, t)[j] = lo;
+}
+
+// First k in [lo, hi) with a[k] > x (hi if none), a non-decreasing.
+__device__ __forceinline__ uint32_t upper_in(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// First k in [lo, hi) with a[k] >= x (hi if none), a non-decreasing.
+__device__ __forceinline__ uint32_t lower_in(const uint32_t *a, uint32_t lo, uint32_t hi, uint32_t x)
+{
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+constexpr uint32_t ANCHOR_SMEM = 2048;   // delta anchors of one base tile held in shared memory
+
+// One base tile of CTILE entries per block (blockIdx.y = problem): its live
+// entries and the delta entries anchored in it (a(j) in [i0, i1); the last
+// tile also takes a(j) = nA) go to their merged positions.  blk holds the
+// exclusive scan of the live counts per tile (k_live_count, k_scan_blocks).
+__global__ void __launch_bounds__(CBLK) k_merge_live(Adj4 A, Adj4 B, Adj4 O, uint32_t nA, uint32_t nB,
+                                                     uint32_t lo32, uint32_t live_span, Adj4 blk,
+                                                     Adj4 anchor, const uint32_t *status)
+{
+    if (*status) return;
+    __shared__ uint32_t rank[CTILE + 1];       // live entries before each tile position
+    __shared__ uint32_t sa[ANCHOR_SMEM];
+    __shared__ uint32_t jr[2];
+    const int t0 = blockIdx.y;
+    const uint32_t *K = sel4(A.key, t0), *N = sel4(A.nbr, t0), *S = sel4(A.s32, t0);
+    uint32_t *OK = sel4(O.key, t0), *ON = sel4(O.nbr, t0), *OS = sel4(O.s32, t0);
+    const uint32_t *an = sel4(anchor.key, t0);
+    const uint32_t i0 = blockIdx.x * CTILE;
+    const uint32_t i1 = min(i0 + (uint32_t)CTILE, nA);
+    const bool last_tile = blockIdx.x + 1 == gridDim.x;
+    // delta entries anchored in this tile: [jlo, jhi)
+    if (threadIdx.x == 0) jr[0] = lower_in(an, 0, nB, i0);
+    if (threadIdx.x == 1) jr[1] = last_tile ? nB : lower_in(an, 0, nB, i1);
+    const uint32_t base = threadIdx.x * CITEMS;
+    uint32_t sv[CITEMS];
+    uint32_t c = 0;
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) {
+        const uint32_t i = i0 + base + u;
+        sv[u] = i < i1 ? S[i] : 0;
+        c += (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
+    }
+    uint32_t total;
+    uint32_t r = block_excl_scan(c, &total);        // synchronises: jr visible
+    const uint32_t live0 = nA ? sel4(blk.key, t0)[blockIdx.x] : 0u;
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) {
+        rank[base + u] = r;
+        const uint32_t i = i0 + base + u;
+        r += (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
+    }
+    if (threadIdx.x == 0) rank[CTILE] = total;
+    const uint32_t jlo = jr[0], jhi = jr[1];
+    const bool in_smem = jhi - jlo <= ANCHOR_SMEM;
+    if (in_smem)
+        for (uint32_t k = threadIdx.x; k < jhi - jlo; k += blockDim.x) sa[k] = an[jlo + k];
+    __syncthreads();
+    // live base entries
+    uint32_t jp = jlo;                          // delta entries at or before the current position
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) {
+        const uint32_t i = i0 + base + u;
+        if (i >= i1) break;
+        jp = in_smem ? jlo + upper_in(sa, jp - jlo, jhi - jlo, i) : upper_in(an, jp, jhi, i);
+        if ((uint32_t)(sv[u] - lo32) < live_span) {
+            const uint32_t o = live0 + rank[base + u] + jp;
+            OK[o] = K[i];
+            ON[o] = N[i];
+            OS[o] = sv[u];
+        }
+    }
+    // delta entries anchored here
+    for (uint32_t j = jlo + threadIdx.x; j < jhi; j += blockDim.x) {
+        const uint32_t a = in_smem ? sa[j - jlo] : an[j];
+        const uint32_t o = live0 + rank[min(a - i0, (uint32_t)CTILE)] + j;
+        OK[o] = sel4(B.key, t0)[j];
+        ON[o] = sel4(B.nbr, t0)[j];
+        OS[o] = sel4(B.s32, t0)[j];
     }
 }
 

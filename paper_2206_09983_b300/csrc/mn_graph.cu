@@ -135,7 +135,7 @@ struct mn_graph {
     // adjacency problems: 0 out / 1 in by neighbour, 2 out / 3 in by arrival
     DirArrays base[2][NPROB];   // [buffer][problem]
     int cur = 0;
-    DirArrays tmp[NPROB], delta[NPROB];
+    DirArrays delta[NPROB];
     uint32_t *cnt[2] = {nullptr, nullptr}, *offs[2] = {nullptr, nullptr};
     unsigned long long *dkA[NPROB] = {}, *dkB[NPROB] = {};
     uint32_t *dvA[NPROB] = {}, *dvB[NPROB] = {};
@@ -1037,26 +1037,28 @@ mn_status launch_adjacency_update(mn_graph *g, uint64_t n, const mn_edge *d_edge
     CKL();
     Adj4 blk;
     for (int t = 0; t < NPROB; t++) { blk.key[t] = g->blk[t]; blk.nbr[t] = nullptr; blk.s32[t] = nullptr; }
-    // compact the live base entries
+    // merge the live base entries with the delta into the other base
+    // buffer: live counts per tile and their scan, the delta entries'
+    // anchors in the base, then one pass over the base tiles
     const uint64_t n_base = g->hi - g->merged_lo;
-    const uint64_t nA = g->hi - g->lo;
     const uint32_t lo32 = (uint32_t)g->lo;
     const uint32_t span = (uint32_t)(g->hi - g->lo);
     Adj4 Bse = adj4(g->base[g->cur]);
-    Adj4 T = adj4(g->tmp);
+    Adj4 O = adj4(g->base[1 - g->cur]);
+    Adj4 anc;                       // the sort values are free once the delta is final
+    for (int t = 0; t < NPROB; t++) { anc.key[t] = g->dvA[t]; anc.nbr[t] = nullptr; anc.s32[t] = nullptr; }
+    const uint32_t nb = cdiv(n_base, CTILE);
     if (n_base) {
-        const uint32_t nb = cdiv(n_base, CTILE);
         k_live_count<<<dim3(nb, NPROB), CBLK, 0, g->stream>>>(Bse, (uint32_t)n_base, lo32, span, blk, st);
         CKL();
         k_scan_blocks<<<NPROB, 1024, 0, g->stream>>>(blk, nb, st);
         CKL();
-        k_compact<<<dim3(nb, NPROB), CBLK, 0, g->stream>>>(Bse, T, (uint32_t)n_base, lo32, span, blk, st);
-        CKL();
     }
-    Adj4 O = adj4(g->base[1 - g->cur]);
-    const uint64_t nO = nA + n;
-    k_merge_csr<<<dim3(cdiv(cdiv(nO, MERGE_ITEMS), 256), NPROB), 256, 0, g->stream>>>(
-        T, D, O, (uint32_t)nA, (uint32_t)n, st);
+    k_delta_anchor<<<dim3(cdiv(n, 256), NPROB), 256, 0, g->stream>>>(Bse, D, (uint32_t)n_base, (uint32_t)n,
+                                                                      anc, st);
+    CKL();
+    k_merge_live<<<dim3(std::max(nb, 1u), NPROB), CBLK, 0, g->stream>>>(Bse, D, O, (uint32_t)n_base, (uint32_t)n,
+                                                                         lo32, span, blk, anc, st);
     CKL();
     // offsets of the (vertex, label) segments (shared by both orders)
     const uint64_t nvl = (uint64_t)g->V * g->L;
@@ -1417,9 +1419,6 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         }
     const uint64_t mb_pad = (uint64_t)cdiv(g->max_batch, SORT_TILE) * SORT_TILE;
     for (int t = 0; t < NPROB; t++) {
-        A(dalloc(g, &g->tmp[t].key, C, false));
-        A(dalloc(g, &g->tmp[t].nbr, C, false));
-        A(dalloc(g, &g->tmp[t].s32, C, false));
         A(dalloc(g, &g->delta[t].key, g->max_batch, false));
         A(dalloc(g, &g->delta[t].nbr, g->max_batch, false));
         A(dalloc(g, &g->delta[t].s32, g->max_batch, false));
