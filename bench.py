@@ -95,13 +95,18 @@ class ClockSampler:
 # launch, the mean of the learned arm's first two timed launches (one per batch) in
 # one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
 # enumerator code it was taken on (enum_source_sha1): null once that changed.
-ENUM_TRAFFIC = {"source_sha1": "bf5c988347bb4ec26f708c9a89b3eea0c8159104", "bytes_per_launch": 1079.2e6}
+ENUM_TRAFFIC = {"source_sha1": "c0d8f24927b8660bd5803a058df6918295909c9c", "bytes_per_launch": 1084.3e6}
 
 
 def enum_source_sha1() -> str:
-    """sha1 of the enumerator source's code: comments and blank space removed,
-    so that only a change of code makes the stored traffic stale."""
+    """sha1 of the enumerator's source code (mn_device.cuh from its launch
+    constants to the end of k_enumerate): comments and blank space removed, so
+    that only a change of the enumerator's code makes the stored traffic
+    stale."""
     src = open(os.path.join(ROOT, "paper_2206_09983_b300", "csrc", "mn_device.cuh")).read()
+    a = src.index("constexpr int ENUM_WARPS")
+    b = src.index("// ------------------------------------------------------------------ expiry / deletion")
+    src = src[a:b]
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return hashlib.sha1(" ".join(src.split()).encode()).hexdigest()
@@ -483,18 +488,26 @@ def graph_probe(ctx, wl, pos, small=4096, steps=40):
 
 def presplit_gain(results):
     """Best enumeration time per unit of work among the autotuner's
-    candidates with learned pre-splitting off and on (each candidate ran on
-    a different live batch, so times are normalised by work)."""
+    candidates with learned pre-splitting off and on, and the speed ratio of
+    shared-memory slice staging against the same split without it (each
+    candidate ran on a different live batch, so times are normalised by
+    work)."""
     if not results:
         return None
     def best(sel):
-        c = [(ms / w, cfg) for (*cfg, ms, w) in results if sel(cfg[3]) and w > 1]
+        c = [(ms / w, cfg) for (*cfg, ms, w) in results if sel(cfg) and w > 1]
         return min(c) if c else None
-    off, on = best(lambda t: t == 0.0), best(lambda t: t != 0.0)
-    if not off or not on:
-        return None
-    return {"ms_per_gwork_off": off[0] * 1e9, "ms_per_gwork_on": on[0] * 1e9, "ratio": off[0] / on[0],
-            "best_off": list(off[1]), "best_on": list(on[1])}
+    out = {}
+    # learned pre-splitting: candidates without slice staging, threshold off vs on
+    off, on = best(lambda c: c[3] == 0.0 and c[4] == 0), best(lambda c: c[3] != 0.0 and c[4] == 0)
+    if off and on:
+        out = {"ms_per_gwork_off": off[0] * 1e9, "ms_per_gwork_on": on[0] * 1e9, "ratio": off[0] / on[0],
+               "best_off": list(off[1]), "best_on": list(on[1])}
+    # shared-memory slice staging at the default split: off vs each threshold
+    base = best(lambda c: c[1] == 40 and c[2] == 16 and c[3] == 0.0 and c[4] == 0)
+    if base:
+        out["slice_staging"] = {str(c[4]): base[0] / (ms / w) for (*c, ms, w) in results if c[4] and w > 1}
+    return out or None
 
 
 def run_workload(args, ctx, wl, with_e2e):

@@ -319,6 +319,19 @@ mn_status mn_get_tuning(const mn_graph *g, uint32_t *blocks_per_sm, uint32_t *ma
 mn_status mn_set_presplit(mn_graph *g, float log2_cycles);
 mn_status mn_get_presplit(const mn_graph *g, float *log2_cycles);
 
+/* Shared-memory staging of adjacency slices in the enumerator (Sec. III
+ * enumerator, its candidate scans): a candidate range of the last two search
+ * depths -- swept 32 entries at a time with no descent in between -- that
+ * holds at least min_entries entries is read through two shared-memory
+ * windows of 128 entries per warp, each filled by bulk asynchronous copies
+ * (the TMA unit) of the range's neighbour and seq slices, the next window
+ * fetched while the current ones are tested.  min_entries = 0 turns it off
+ * (the default); 1..31 is MN_ERR_INVALID_ARG.  Results are unaffected;
+ * mn_stats.entries_staged counts the entries read this way.
+ * mn_get_slice_staging reads the setting back. */
+mn_status mn_set_slice_staging(mn_graph *g, uint32_t min_entries);
+mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries);
+
 /* Online autotuning of the launch parameters above: each of the next
  * insert batches that enumerates runs under one candidate configuration,
  * `batches_per_config` batches each; then the configuration with the least
@@ -326,15 +339,19 @@ mn_status mn_get_presplit(const mn_graph *g, float *log2_cycles);
  * bound) is kept.  Results are unaffected.  The candidates (listed by
  * mn_autotune_candidates) are: resident blocks per SM at the occupancy limit
  * x split threshold {40, 64, 128} x split depth {3, any} x pre-split
- * threshold {off, 2^20, 2^22 cycles}.  mn_autotune_state reports whether
+ * threshold {off, 2^20, 2^22 cycles}, all without slice staging, plus split
+ * threshold 40 at any depth with staging of ranges of at least {256, 1024}
+ * entries (mn_set_slice_staging).  mn_autotune_state reports whether
  * tuning is still running and how many configurations are left. */
 mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config);
 mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left);
 
-/* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off). */
+/* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off;
+ * slice_min = 0: no shared-memory staging, mn_set_slice_staging). */
 typedef struct {
     uint32_t blocks_per_sm, split_min, split_depth;
     float presplit_log2;
+    uint32_t slice_min;
 } mn_tune_config;
 
 /* Copy the autotuner's candidates to out[0..cap) (out may be NULL to ask for
@@ -513,6 +530,7 @@ typedef struct {
     uint64_t graph_launches;       /* insert batches launched as one CUDA graph (mn_set_graph_capture) */
     uint64_t graph_instantiations; /* graph instantiations (the rest were updated in place) */
     uint64_t spill_bytes;          /* bytes copied to the host spill (mn_set_spill) */
+    uint64_t entries_staged;       /* adjacency entries read through staged windows */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

@@ -88,6 +88,59 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// ---- bulk asynchronous copies (the TMA unit's non-tensor mode) and mbarriers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// make initialised barriers visible to the asynchronous proxy
+__device__ __forceinline__ void mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// order this thread's earlier shared-memory accesses before later
+// asynchronous-proxy writes to the same buffer
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of
+// 16), completion counted in bytes on *bar
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
 __device__ __forceinline__ uint32_t match_word(const QueryDev *q, uint32_t label, int32_t attr,
                                                int64_t ts, uint32_t ms, uint32_t md)
 {
@@ -345,6 +398,49 @@ __global__ void k_delta_finalize(SortSet s, Adj4 d, const mn_edge *edges, uint32
 
 constexpr int CBLK = 256, CITEMS = 8, CTILE = CBLK * CITEMS;
 
+// Tiles of CTILE items are read striped: item u of thread t sits at tile
+// position u * CBLK + t, so that each load and store of a warp covers 128
+// contiguous bytes.  Exclusive prefix sums of such a tile in position order:
+// v[u] becomes the sum of the items before it; *total gets the tile's sum.
+__device__ __forceinline__ void striped_excl_scan(uint32_t (&v)[CITEMS], uint32_t *total)
+{
+    constexpr int NW = CBLK / 32;
+    static_assert(CITEMS * NW == 64, "one warp scans the per-(item, warp) sums two per lane");
+    __shared__ uint32_t part[CITEMS * NW];
+    __shared__ uint32_t tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t incl[CITEMS];
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) {
+        uint32_t x = v[u];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, d);
+            if (lane >= d) x += y;
+        }
+        incl[u] = x;
+        if (lane == 31) part[u * NW + w] = x;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const uint32_t a = part[2 * lane], b = part[2 * lane + 1];
+        uint32_t s = a + b;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, s, d);
+            if (lane >= d) s += y;
+        }
+        part[2 * lane] = s - a - b;
+        part[2 * lane + 1] = s - b;
+        if (lane == 31) tot = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) v[u] = part[u * NW + w] + incl[u] - v[u];
+    *total = tot;
+    __syncthreads();                      // part and tot are free again
+}
+
 // Live entries (seq >= lo) per tile of the base adjacency; blockIdx.y = problem.
 __global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_t lo32,
                                                      uint32_t live_span, Adj4 blk,
@@ -352,11 +448,11 @@ __global__ void __launch_bounds__(CBLK) k_live_count(Adj4 a, uint32_t n, uint32_
 {
     if (*status) return;
     const uint32_t *s = sel4(a.s32, blockIdx.y);
-    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x;
     uint32_t c = 0;
 #pragma unroll
     for (int t = 0; t < CITEMS; t++) {
-        uint32_t i = base + t;
+        uint32_t i = base + t * CBLK;
         c += (i < n && (uint32_t)(s[i] - lo32) < live_span) ? 1u : 0u;
     }
     uint32_t total;
@@ -467,39 +563,31 @@ __global__ void __launch_bounds__(CBLK) k_merge_live(Adj4 A, Adj4 B, Adj4 O, uin
     // delta entries anchored in this tile: [jlo, jhi)
     if (threadIdx.x == 0) jr[0] = lower_in(an, 0, nB, i0);
     if (threadIdx.x == 1) jr[1] = last_tile ? nB : lower_in(an, 0, nB, i1);
-    const uint32_t base = threadIdx.x * CITEMS;
-    uint32_t sv[CITEMS];
-    uint32_t c = 0;
+    uint32_t sv[CITEMS], r[CITEMS];
 #pragma unroll
     for (int u = 0; u < CITEMS; u++) {
-        const uint32_t i = i0 + base + u;
+        const uint32_t i = i0 + u * CBLK + threadIdx.x;
         sv[u] = i < i1 ? S[i] : 0;
-        c += (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
+        r[u] = (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
     }
     uint32_t total;
-    uint32_t r = block_excl_scan(c, &total);        // synchronises: jr visible
+    striped_excl_scan(r, &total);               // synchronises: jr visible
     const uint32_t live0 = nA ? sel4(blk.key, t0)[blockIdx.x] : 0u;
 #pragma unroll
-    for (int u = 0; u < CITEMS; u++) {
-        rank[base + u] = r;
-        const uint32_t i = i0 + base + u;
-        r += (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
-    }
+    for (int u = 0; u < CITEMS; u++) rank[u * CBLK + threadIdx.x] = r[u];
     if (threadIdx.x == 0) rank[CTILE] = total;
     const uint32_t jlo = jr[0], jhi = jr[1];
     const bool in_smem = jhi - jlo <= ANCHOR_SMEM;
     if (in_smem)
         for (uint32_t k = threadIdx.x; k < jhi - jlo; k += blockDim.x) sa[k] = an[jlo + k];
     __syncthreads();
-    // live base entries
-    uint32_t jp = jlo;                          // delta entries at or before the current position
+    // live base entries: #{j : a(j) <= i} delta entries precede entry i
 #pragma unroll
     for (int u = 0; u < CITEMS; u++) {
-        const uint32_t i = i0 + base + u;
-        if (i >= i1) break;
-        jp = in_smem ? jlo + upper_in(sa, jp - jlo, jhi - jlo, i) : upper_in(an, jp, jhi, i);
-        if ((uint32_t)(sv[u] - lo32) < live_span) {
-            const uint32_t o = live0 + rank[base + u] + jp;
+        const uint32_t i = i0 + u * CBLK + threadIdx.x;
+        if (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) {
+            const uint32_t jp = in_smem ? jlo + upper_in(sa, 0, jhi - jlo, i) : upper_in(an, jlo, jhi, i);
+            const uint32_t o = live0 + r[u] + jp;
             OK[o] = K[i];
             ON[o] = N[i];
             OS[o] = sv[u];
@@ -524,10 +612,10 @@ __global__ void __launch_bounds__(CBLK) k_scan_reduce(const uint32_t *c0, const 
 {
     if (*status) return;
     const uint32_t *c = blockIdx.y ? c1 : c0;
-    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x;
     uint32_t s = 0;
 #pragma unroll
-    for (int t = 0; t < CITEMS; t++) s += base + t < n ? c[base + t] : 0u;
+    for (int t = 0; t < CITEMS; t++) s += base + t * CBLK < n ? c[base + t * CBLK] : 0u;
     uint32_t total;
     block_excl_scan(s, &total);
     if (threadIdx.x == 0) (blockIdx.y ? bs1 : bs0)[blockIdx.x] = total;
@@ -543,22 +631,22 @@ __global__ void __launch_bounds__(CBLK) k_scan_apply(const uint32_t *c0, const u
     const bool d1 = blockIdx.y != 0;
     const uint32_t *c = d1 ? c1 : c0;
     uint32_t *o = d1 ? o1 : o0;
-    const uint32_t base = blockIdx.x * CTILE + threadIdx.x * CITEMS;
-    uint32_t v[CITEMS];
-    uint32_t s = 0;
+    const uint32_t base = blockIdx.x * CTILE + threadIdx.x;
+    uint32_t v[CITEMS], cnt[CITEMS];
 #pragma unroll
     for (int t = 0; t < CITEMS; t++) {
-        v[t] = base + t < n ? c[base + t] : 0u;
-        s += v[t];
+        cnt[t] = base + t * CBLK < n ? c[base + t * CBLK] : 0u;
+        v[t] = cnt[t];
     }
     uint32_t total;
-    uint32_t run = block_excl_scan(s, &total) + (d1 ? bs1 : bs0)[blockIdx.x];
+    striped_excl_scan(v, &total);
+    const uint32_t off = (d1 ? bs1 : bs0)[blockIdx.x];
 #pragma unroll
     for (int t = 0; t < CITEMS; t++) {
-        if (base + t < n) o[base + t] = run;
-        run += v[t];
+        const uint32_t i = base + t * CBLK;
+        if (i < n) o[i] = off + v[t];
+        if (i + 1 == n) o[n] = off + v[t] + cnt[t];   // the thread holding item n-1
     }
-    if (base < n && base + CITEMS >= n) o[n] = run;   // the thread holding item n-1
 }
 
 // ------------------------------------------------------------------ seeds
@@ -704,6 +792,8 @@ constexpr int ENUM_WARPS = 4;              // warps per block
 // 16 warps at 122 registers (the few spilled bytes stay in L1).
 constexpr int ENUM_MIN_BLOCKS = 5;
 constexpr int STAGE_BYTES = 4096;          // per-warp output staging buffer
+constexpr uint32_t SLICE_WIN = 128;        // adjacency entries per staged window (two per warp)
+constexpr uint32_t SLICE_WAIT_POLLS = 1u << 20;   // bound on one window's wait
 // Idle wait of a ticket holder (polls of its task-ring slot, backing off to
 // 2 us per poll): it gives its slot up after wait_polls polls (default
 // WAIT_POLLS, ~0.13 s) even while other warps are busy, and reports
@@ -745,7 +835,8 @@ struct EnumParams {
     unsigned long long max_iters;       // per-warp loop budget (ST_TIMEOUT beyond)
     uint32_t *status;
     unsigned long long *work;           // [seeds, entries tested, binds, records, busy cycles, tasks,
-                                        //  seeds whose endpoints the filtering excludes]
+                                        //  seeds whose endpoints the filtering excludes,
+                                        //  entries read from staged windows]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
     // optional second seed set, enumerated in the same launch after the first
     // (the other phase of the same batch): its seeds, avoid interval, sign and
@@ -762,6 +853,9 @@ struct EnumParams {
     uint32_t wait_polls;                // idle wait bound (WAIT_POLLS)
     uint32_t wait_hold;                 // test: holders neither take nor give up their slot
     unsigned long long qrun[2];         // per seed set: bit q set = enumerate query q's seeds
+    uint32_t stage_min;                 // STAGE: ranges at the last two depths at least this long
+                                        // are read through shared-memory windows
+    uint32_t adj_cap;                   // entries allocated per adjacency array (a multiple of 4)
 };
 
 __device__ __forceinline__ uint32_t vload(const uint32_t *p)
@@ -882,13 +976,34 @@ __device__ __forceinline__ void warp_bounds(KeyFn key, uint32_t lo, uint32_t hi,
 // contiguous blocks.
 // FILTER: the DEBI filtering is on (p.bu set); a separate instantiation, so
 // that the unfiltered kernel carries none of its code.
-template <bool FILTER>
+// STAGE: a contiguous candidate range of the last two depths (swept chunk
+// after chunk with no descent in between) of at least p.stage_min entries is
+// read through two shared-memory windows per warp, each filled by bulk
+// asynchronous copies of its nbr and seq slices: window k + 2 is fetched while
+// windows k and k + 1 are tested.
+template <bool FILTER, bool STAGE>
 __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(EnumParams p)
 {
     __shared__ __align__(16) unsigned char stage_all[ENUM_WARPS][STAGE_BYTES];
+    __shared__ __align__(16) uint32_t win_all[STAGE ? ENUM_WARPS : 1][2][2][SLICE_WIN];
+    __shared__ __align__(8) unsigned long long wbar_all[STAGE ? ENUM_WARPS : 1][2];
     if (*p.status) return;
     const int lane = threadIdx.x & 31;
     unsigned char *stage = stage_all[threadIdx.x >> 5];
+    // staged windows: buffer b holds window k (k & 1 == b) of the range that
+    // starts at sg_ws0; sg_bits: 1 << b copy pending on buffer b, 4 << b the
+    // parity of buffer b's next phase, 16 a staged range is open
+    uint32_t (*win)[2][SLICE_WIN] = win_all[STAGE ? (threadIdx.x >> 5) : 0];
+    unsigned long long *wbar = wbar_all[STAGE ? (threadIdx.x >> 5) : 0];
+    uint32_t sg_ws0 = 0, sg_wlo = 0, sg_bits = 0;
+    if (STAGE) {
+        if (lane == 0) {
+            mbar_init(&wbar[0], 1);
+            mbar_init(&wbar[1], 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
     const uint32_t nseeds0 = min(*p.nseeds, p.seed_cap);
     const uint32_t nseeds = nseeds0 + (p.seeds1 ? min(*p.nseeds1, p.seed_cap1) : 0u);
     Sched *sc = p.sched;
@@ -901,7 +1016,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
     const uint32_t many_idle = gridDim.x * ENUM_WARPS / 4;
     bool seeds_left = true;                  // lane 0: the seed cursor may still have seeds
     unsigned long long w_seeds = 0, w_scanned = 0, w_binds = 0, w_records = 0, w_busy = 0;
-    unsigned long long w_tasks = 0, w_pruned = 0;
+    unsigned long long w_tasks = 0, w_pruned = 0, w_staged = 0;
     uint32_t st_n = 0, st_q = 0xffffffffu, st_rb = 0, st_sign = 0;
 
     // write the staged records of query st_q to its list
@@ -1180,6 +1295,40 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                 tgt = __shfl_sync(FULL, Ltgt, s);
                 dsel = __shfl_sync(FULL, Ldsel, s);
             };
+            // staged windows (STAGE): wait for buffer b's pending copy (all
+            // lanes observe the phase, so all see the data), fetch window k
+            // of the open range into buffer k & 1, drain both buffers
+            auto sg_wait = [&](uint32_t b) {
+                if (!((sg_bits >> b) & 1u)) return;
+                const uint32_t par = (sg_bits >> (2 + b)) & 1u;
+                for (uint32_t it = 0; !mbar_try_wait(&wbar[b], par); it++) {
+                    if (it == SLICE_WAIT_POLLS && lane == 0) atomicOr(p.status, ST_TIMEOUT);
+                    if (it >= 2 * SLICE_WAIT_POLLS) break;
+                }
+                sg_bits &= ~(1u << b);
+                sg_bits ^= 4u << b;
+            };
+            auto sg_issue = [&](uint32_t k) {
+                const uint32_t start = sg_ws0 + k * SLICE_WIN;
+                if (start >= end) return;
+                const uint32_t endr = min((end + 3u) & ~3u, p.adj_cap);
+                const uint32_t n = min(SLICE_WIN, endr - start);
+                const uint32_t b = k & 1u;
+                __syncwarp();                        // every lane is done with the buffer
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&wbar[b], 8u * n);
+                    bulk_load(win[b][0], p.nbr[dsel] + start, 4u * n, &wbar[b]);
+                    bulk_load(win[b][1], p.s32[dsel] + start, 4u * n, &wbar[b]);
+                }
+                sg_bits |= 1u << b;
+            };
+            auto sg_drain = [&]() {
+                if (!(sg_bits & 16u)) return;
+                sg_wait(0);
+                sg_wait(1);
+                sg_bits &= ~16u;
+            };
             // hand [mid, e) of depth l to the queue, optionally with vertex
             // fo_lane bound to fo_val and edge go_lane to go_val; false if the
             // queue is full
@@ -1387,6 +1536,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                 }
                 if (mask == 0) {
                     if (cur >= end) {               // depth exhausted: backtrack
+                        if (STAGE) sg_drain();
                         lvl--;
                         if (lvl >= root) restore(lvl);
                         continue;
@@ -1443,13 +1593,45 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                             }
                         }
                     }
+                    // a long range of the last two depths: open its windows
+                    if (STAGE && !(sg_bits & 16u) && lvl + 1 >= last && end - cur >= p.stage_min) {
+                        sg_ws0 = cur & ~3u;
+                        sg_wlo = 0;
+                        sg_bits |= 16u;
+                        sg_issue(0);
+                        sg_issue(1);
+                    }
+                    bool staged = false;
+                    if (STAGE && (sg_bits & 16u)) {
+                        // windows below the chunk are done: each buffer takes
+                        // the window two ahead of the one it held
+                        const uint32_t ka = (cur - sg_ws0) / SLICE_WIN;
+                        while (sg_wlo < ka) {
+                            sg_wait(sg_wlo & 1u);
+                            sg_issue(sg_wlo + 2);
+                            sg_wlo++;
+                        }
+                        const uint32_t kb = (min(cur + 32u, end) - 1u - sg_ws0) / SLICE_WIN;
+                        sg_wait(ka & 1u);
+                        if (kb != ka) sg_wait(kb & 1u);
+                        staged = true;
+                        w_staged += min(32u, end - cur);
+                    }
                     // test the next 32 candidates, one per lane
                     const uint32_t idx = cur + (uint32_t)lane;
                     bool ok = false;
                     uint32_t nb = 0, rel = 0;
                     if (idx < end) {
-                        nb = p.nbr[dsel][idx];
-                        const uint32_t sv = p.s32[dsel][idx];
+                        uint32_t sv;
+                        if (STAGE && staged) {
+                            const uint32_t r = idx - sg_ws0;
+                            const uint32_t b = (r / SLICE_WIN) & 1u;
+                            nb = win[b][0][r % SLICE_WIN];
+                            sv = win[b][1][r % SLICE_WIN];
+                        } else {
+                            nb = p.nbr[dsel][idx];
+                            sv = p.s32[dsel][idx];
+                        }
                         rel = sv - p.base32;
                         ok = rel >= tlo && rel < thi;
                         if (ok) ok = (debi[sv & p.cap_mask] >> qe) & 1u;
@@ -1490,6 +1672,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
                 lvl++;
                 open(lvl, false);
             }
+            if (STAGE) sg_drain();                   // a unit left early (work budget)
         }
         if (p.count_only && lane == 0 && warp_count)
             atomicAdd(&p.counts[q * 3 + sign], warp_count);
@@ -1516,6 +1699,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
         atomicAdd(&p.work[4], w_busy);
         atomicAdd(&p.work[5], w_tasks);
         atomicAdd(&p.work[6], w_pruned);
+        atomicAdd(&p.work[7], w_staged);
     }
 }
 

@@ -43,7 +43,7 @@ struct Ctrl {
     uint32_t next_seed[3];
     uint32_t pad_;
     long long last_ts;
-    unsigned long long work[7];
+    unsigned long long work[8];
     unsigned long long counts[64 * 3];
     unsigned long long time_cut;        // edges a time window expires after this batch
 };
@@ -175,8 +175,9 @@ struct mn_graph {
     uint32_t split_min = SPLIT_MIN, split_depth = MN_MAX_QE;
     float presplit_log2 = INFINITY;   // learned pre-splitting threshold (log2 predicted cycles); inf = off
     int smem_carveout = -1;     // preferred shared-memory carve-out of the enumerator (%), -1 = driver
+    uint32_t slice_min = 0;     // staged windows for last-depth ranges this long (0 = off)
     // online autotuner: candidate launch configurations tried on live batches
-    struct TuneCfg { uint32_t bps, split_min, split_depth; float presplit_log2; };
+    struct TuneCfg { uint32_t bps, split_min, split_depth; float presplit_log2; uint32_t slice_min; };
     bool tuning = false;
     std::vector<TuneCfg> tune_cfgs;
     std::vector<double> tune_ms, tune_work;
@@ -347,6 +348,7 @@ void collect_work(mn_graph *g)
     g->stats.busy_cycles += g->h_ctrl->work[4];
     g->stats.tasks_split += g->h_ctrl->work[5];
     g->stats.seeds_filtered += g->h_ctrl->work[6];
+    g->stats.entries_staged += g->h_ctrl->work[7];
     collect_timing(g);
 }
 
@@ -972,11 +974,13 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     p.split_min = g->split_min;
     p.split_depth = g->split_depth;
     CK(cudaMemsetAsync(g->d_sched + a.phase, 0, sizeof(Sched), g->stream));
-    CK(cudaFuncSetAttribute(k_enumerate<false>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
-    CK(cudaFuncSetAttribute(k_enumerate<true>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
+    p.stage_min = g->slice_min;
+    p.adj_cap = (uint32_t)std::min<uint64_t>(g->C, 0xfffffffcull);
+    void (*kern)(EnumParams) = p.bu ? (g->slice_min ? k_enumerate<true, true> : k_enumerate<true, false>)
+                                    : (g->slice_min ? k_enumerate<false, true> : k_enumerate<false, false>);
+    CK(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
     stage_begin(g);
-    if (p.bu) k_enumerate<true><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
-    else      k_enumerate<false><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
+    kern<<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     stage_end(g, S_ENUM);
     g->stats.enumerate_launches++;
@@ -1236,7 +1240,9 @@ void build_tune_candidates(mn_graph *g)
     const uint32_t b = (uint32_t)g->enum_max_per_sm;
     for (uint32_t sm : {40u, 64u, 128u})
         for (uint32_t sd : {3u, (uint32_t)MN_MAX_QE})
-            for (float th : {INFINITY, 20.f, 22.f}) g->tune_cfgs.push_back({b, sm, sd, th});
+            for (float th : {INFINITY, 20.f, 22.f}) g->tune_cfgs.push_back({b, sm, sd, th, 0u});
+    // shared-memory staging of long last-depth ranges, at the default split
+    for (uint32_t sl : {256u, 1024u}) g->tune_cfgs.push_back({b, 40u, (uint32_t)MN_MAX_QE, INFINITY, sl});
 }
 
 }  // namespace
@@ -1270,6 +1276,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
                 g->split_min = c.split_min;
                 g->split_depth = c.split_depth;
                 g->presplit_log2 = c.presplit_log2;
+                g->slice_min = c.slice_min;
                 g->tuning = false;
             }
         }
@@ -1450,7 +1457,7 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
         int nsm = 0, per_sm = 0;
         e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<false>, ENUM_WARPS * 32, 0);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_enumerate<false, false>, ENUM_WARPS * 32, 0);
         if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
         g->nsm = nsm;
         g->enum_max_per_sm = std::max(per_sm, 1);
@@ -1695,6 +1702,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         g->split_min = c.split_min;
         g->split_depth = c.split_depth;
         g->presplit_log2 = c.presplit_log2;
+        g->slice_min = c.slice_min;
     }
     Phase ph[2];
     int nph = 0;
@@ -1950,7 +1958,7 @@ namespace {
 // counts (3 per query, 64 queries), [256, 336) scheduler words (one 128-byte
 // line each), [384, 384 + MN_NOALLOC_MAX_SEEDS) seeds.
 constexpr uint32_t NA_WORK = 4, NA_COUNTS = 16, NA_SCHED = 256, NA_SEEDS = 384;
-static_assert(NA_WORK + 7 <= NA_COUNTS, "work counters overlap the counts");
+static_assert(NA_WORK + 8 <= NA_COUNTS, "work counters overlap the counts");
 static_assert(NA_COUNTS + 3 * 64 <= NA_SCHED, "counts overlap the scheduler words");
 static_assert(NA_SCHED * 8 + sizeof(Sched) <= NA_SEEDS * 8, "scheduler words overlap the seeds");
 constexpr uint64_t NA_WORDS = NA_SEEDS + (uint64_t)MN_NOALLOC_MAX_SEEDS;
@@ -2034,8 +2042,9 @@ mn_status mn_count_static_noalloc(mn_graph *g, uint32_t query_id, uint64_t *coun
     p.work = base + NA_WORK;
     p.wait_polls = g->wait_polls;
     p.qrun[0] = p.qrun[1] = ~0ull;
-    CK(cudaFuncSetAttribute(k_enumerate<false>, cudaFuncAttributePreferredSharedMemoryCarveout, g->smem_carveout));
-    k_enumerate<false><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
+    CK(cudaFuncSetAttribute(k_enumerate<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                            g->smem_carveout));
+    k_enumerate<false, false><<<g->enum_grid, ENUM_WARPS * 32, 0, g->stream>>>(p);
     CKL();
     uint32_t st = 0;
     unsigned long long c = 0;
@@ -2459,6 +2468,7 @@ mn_status mn_autotune_candidates(mn_graph *g, uint32_t cap, mn_tune_config *out,
         out[k].split_min = c.split_min;
         out[k].split_depth = c.split_depth;
         out[k].presplit_log2 = std::isinf(c.presplit_log2) ? 0.f : c.presplit_log2;
+        out[k].slice_min = c.slice_min;
     }
     if (out && cap < *n) return fail(g, MN_ERR_INVALID_ARG, "array too small");
     return MN_OK;
@@ -2476,6 +2486,7 @@ mn_status mn_autotune_results(const mn_graph *g, uint32_t cap, mn_tune_result *o
         out[k].config.split_min = c.split_min;
         out[k].config.split_depth = c.split_depth;
         out[k].config.presplit_log2 = std::isinf(c.presplit_log2) ? 0.f : c.presplit_log2;
+        out[k].config.slice_min = c.slice_min;
         out[k].enumerate_ms = g->tune_ms[k];
         out[k].work = g->tune_work[k];
     }
@@ -2487,6 +2498,21 @@ mn_status mn_set_presplit(mn_graph *g, float log2_cycles)
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
     if (std::isnan(log2_cycles)) return fail(g, MN_ERR_INVALID_ARG, "threshold is NaN");
     g->presplit_log2 = log2_cycles > 0.f ? log2_cycles : INFINITY;
+    return MN_OK;
+}
+
+mn_status mn_set_slice_staging(mn_graph *g, uint32_t min_entries)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (min_entries && min_entries < 32) return fail(g, MN_ERR_INVALID_ARG, "min_entries below one chunk (32)");
+    g->slice_min = min_entries;
+    return MN_OK;
+}
+
+mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries)
+{
+    if (!g || !min_entries) return MN_ERR_INVALID_ARG;
+    *min_entries = g->slice_min;
     return MN_OK;
 }
 

@@ -44,8 +44,8 @@ EXPORTS = [
     "mn_batch_wait", "mn_set_shard", "mn_set_time_window", "mn_memory_info", "mn_reset_index",
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
-    "mn_set_graph_capture", "mn_set_spill", "mn_read_spill",
-    "mn_last_error",
+    "mn_set_graph_capture", "mn_set_spill", "mn_read_spill", "mn_set_slice_staging",
+    "mn_get_slice_staging", "mn_last_error",
 ]
 MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
@@ -89,7 +89,7 @@ class Stats(C.Structure):
                 ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64),
                 ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
-                ("spill_bytes", C.c_uint64)]
+                ("spill_bytes", C.c_uint64), ("entries_staged", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -97,7 +97,7 @@ class Stats(C.Structure):
 
 class _TuneConfig(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_uint32), ("split_min", C.c_uint32), ("split_depth", C.c_uint32),
-                ("presplit_log2", C.c_float)]
+                ("presplit_log2", C.c_float), ("slice_min", C.c_uint32)]
 
 
 class _TuneResult(C.Structure):
@@ -169,6 +169,8 @@ def load(path: str | None = None):
         "mn_read_spill": (S, [P, U64, U64, P, P, C.POINTER(U64), C.POINTER(U64)]),
         "mn_read_filter": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_int32), P, P]),
         "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
+        "mn_set_slice_staging": (S, [P, C.c_uint32]),
+        "mn_get_slice_staging": (S, [P, C.POINTER(C.c_uint32)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_autotune_results": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_set_timing": (S, [P, C.c_int32]),
@@ -526,23 +528,32 @@ class Graph:
         self._check(self._lib.mn_get_presplit(self._h, C.byref(v)))
         return v.value
 
+    def set_slice_staging(self, min_entries: int):
+        """Staged shared-memory windows for last-depth ranges of at least min_entries (0 = off)."""
+        self._check(self._lib.mn_set_slice_staging(self._h, min_entries))
+
+    def get_slice_staging(self) -> int:
+        v = C.c_uint32()
+        self._check(self._lib.mn_get_slice_staging(self._h, C.byref(v)))
+        return v.value
+
     def autotune_candidates(self):
-        """The autotuner's candidates: (blocks_per_sm, split_min, split_depth, presplit_log2)."""
+        """The autotuner's candidates: (blocks_per_sm, split_min, split_depth, presplit_log2, slice_min)."""
         n = C.c_uint32()
         self._check(self._lib.mn_autotune_candidates(self._h, 0, None, C.byref(n)))
         arr = (_TuneConfig * max(1, n.value))()
         self._check(self._lib.mn_autotune_candidates(self._h, n.value, arr, C.byref(n)))
-        return [(c.blocks_per_sm, c.split_min, c.split_depth, c.presplit_log2) for c in arr[:n.value]]
+        return [(c.blocks_per_sm, c.split_min, c.split_depth, c.presplit_log2, c.slice_min) for c in arr[:n.value]]
 
     def autotune_results(self):
         """Per autotuner candidate: (blocks_per_sm, split_min, split_depth,
-        presplit_log2, enumerate_ms, work) as measured on live batches."""
+        presplit_log2, slice_min, enumerate_ms, work) as measured on live batches."""
         n = C.c_uint32()
         self._check(self._lib.mn_autotune_results(self._h, 0, None, C.byref(n)))
         arr = (_TuneResult * max(1, n.value))()
         self._check(self._lib.mn_autotune_results(self._h, n.value, arr, C.byref(n)))
         return [(r.config.blocks_per_sm, r.config.split_min, r.config.split_depth, r.config.presplit_log2,
-                 r.enumerate_ms, r.work) for r in arr[:n.value]]
+                 r.config.slice_min, r.enumerate_ms, r.work) for r in arr[:n.value]]
 
     def autotune_state(self):
         a, left = C.c_int32(), C.c_uint32()
@@ -555,6 +566,7 @@ class Graph:
         d = dict(zip(("blocks_per_sm", "max_blocks_per_sm", "split_min", "split_depth",
                       "smem_carveout"), [x.value for x in v]))
         d["presplit_log2"] = self.get_presplit()
+        d["slice_min"] = self.get_slice_staging()
         return d
 
     def reset_stats(self):

@@ -1,7 +1,8 @@
 """Launch configurations and result-list sizing against the CPU oracle.
 
 * Every configuration the autotuner tries (resident blocks per SM x split
-  threshold x split depth) gives the oracle's lists, on an R-MAT window where
+  threshold x split depth x pre-split threshold, and shared-memory staging
+  of long last-depth ranges) gives the oracle's lists, on an R-MAT window where
   busy warps do hand subtrees to idle ones; both set explicitly and walked by
   the online autotuner on live batches.
 * Multi-label data vertices with query label masks that are proper subsets
@@ -75,10 +76,11 @@ def test_autotune_candidate_list():
     with fresh(s, qs) as g:
         cands = g.autotune_candidates()
         mx = g.get_tuning()["max_blocks_per_sm"]
-    assert len(cands) == 18 and len(set(cands)) == 18
+    assert len(cands) == 20 and len(set(cands)) == 20
     assert {c[0] for c in cands} == {mx}
     assert {c[1] for c in cands} == {40, 64, 128}
     assert {c[3] for c in cands} == {0.0, 20.0, 22.0}
+    assert sorted(c[4] for c in cands if c[4]) == [256, 1024]
 
 
 def test_every_autotune_configuration_set_explicitly():
@@ -88,16 +90,17 @@ def test_every_autotune_configuration_set_explicitly():
     with fresh(s, qs) as g0:
         cands = g0.autotune_candidates()
     split = 0
-    for bps, smin, sdep, th in cands:
+    for bps, smin, sdep, th, sl in cands:
         with fresh(s, qs) as g:
             g.set_tuning(bps, smin, sdep)
             g.set_presplit(th)
+            g.set_slice_staging(sl)
             t = g.get_tuning()
             assert (t["blocks_per_sm"], t["split_min"], t["presplit_log2"]) == (bps, smin, th)
             g.reset_stats()
             for k in (0, 1):
                 r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
-                check(g, s, qs, k, r, f"bps {bps} split_min {smin} depth {sdep} presplit {th}")
+                check(g, s, qs, k, r, f"bps {bps} split_min {smin} depth {sdep} presplit {th} staging {sl}")
             split += g.stats()["tasks_split"]
     assert split > 0, "no configuration split any work"
 
@@ -192,3 +195,33 @@ def test_only_overflowing_lists_run_again_then_presized():
             assert r.count_pos[0] > 64
         assert reruns[0] == 1, reruns
         assert sum(reruns[1:]) == 0, reruns
+
+
+@pytest.mark.parametrize("min_entries", [32, 100])
+def test_slice_staging_is_exact(min_entries):
+    """Last-depth candidate ranges read through shared-memory windows filled
+    by bulk asynchronous copies (mn_set_slice_staging): the oracle's lists,
+    with ranges that span several 128-entry windows and ragged ends, with
+    work handed between warps, and with the DEBI filtering on."""
+    s, qs = split_stream(), split_queries()
+    with fresh(s, qs) as g:
+        with pytest.raises(M.MnError):
+            g.set_slice_staging(5)
+        g.set_slice_staging(min_entries)
+        assert g.get_slice_staging() == min_entries
+        g.reset_stats()
+        for k in (0, 1):
+            r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
+            check(g, s, qs, k, r, f"staged >= {min_entries}")
+        st = g.stats()
+        assert st["entries_staged"] > 0 and st["tasks_split"] > 0
+        g.set_filtering(True)
+        g.reset_stats()
+        r = g.insert(M.edges_from_stream(s, W + 2 * B, W + 3 * B))
+        check(g, s, qs, 2, r, f"staged >= {min_entries}, filtered")
+        assert g.stats()["entries_staged"] > 0
+        g.set_slice_staging(0)
+        g.reset_stats()
+        r = g.insert(M.edges_from_stream(s, W + 3 * B, W + 4 * B))
+        check(g, s, qs, 3, r, "staging off")
+        assert g.stats()["entries_staged"] == 0
