@@ -189,6 +189,7 @@ struct mn_graph {
     uint32_t policy = 0;                 // MN_ORDER_*
     float *d_P = nullptr, *d_G = nullptr, *d_M1 = nullptr, *d_M2 = nullptr, *d_loss = nullptr;
     __nv_bfloat16 *d_w1t = nullptr, *d_w2t = nullptr;
+    uint32_t *d_train_status = nullptr;   // training kernels' wait status (ST_TIMEOUT)
     uint64_t adam_step = 0;
     bool packed = false;
     __nv_bfloat16 *d_X = nullptr;        // features, seed_cap x NCAND rows
@@ -592,6 +593,7 @@ mn_status ensure_model(mn_graph *g)
     TRY(dalloc(g, &g->d_SX, (uint64_t)g->ring * NF, false));
     TRY(dalloc(g, &g->d_ST, g->ring, false));
     TRY(dalloc(g, &g->d_nsamples, 1));
+    TRY(dalloc(g, &g->d_train_status, 1));
     std::vector<float> P;
     init_params(P);
     CK(cudaMemcpyAsync(g->d_P, P.data(), sizeof(float) * P_COUNT, cudaMemcpyHostToDevice, g->stream));
@@ -671,8 +673,10 @@ mn_status choose_orders(mn_graph *g, int phase)
         TRY(pack_model(g));
         k_features<<<grid, 256, 0, g->stream>>>(feat_params(g, phase, true));
         CKL();
-        k_mlp_forward<<<grid, MLP_WARPS * 32, 0, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND,
-                                                              0, g->d_w1t, g->d_w2t, g->d_P, g->d_y);
+        CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        k_mlp_forward_tc<<<g->nsm, TC_M, TC_SMEM, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND, 0,
+                                                               g->d_w1t, g->d_w2t, g->d_P, g->d_y,
+                                                               &g->d_ctrl->status);
         CKL();
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
                                             1.0f, g->presplit_log2);
@@ -1158,7 +1162,9 @@ mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
         const uint64_t edges = s == 0 ? n_new : n_expired;
         if (!edges) continue;
         for (size_t q = 0; q < g->queries.size() && q < g->rec_rate[s].size(); q++) {
-            const double est = g->rec_rate[s][q] * (double)edges;
+            // half again the decayed maximum: batch-to-batch swings of one
+            // query's output stay inside the list
+            const double est = 1.5 * g->rec_rate[s][q] * (double)edges;
             if (est <= (double)g->queries[q].out_cap[s]) continue;
             bool grown = false;
             TRY(ensure_out_cap(g, q, s, (uint64_t)est, &grown, &over));
@@ -2238,18 +2244,15 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
     CK(cudaStreamSynchronize(g->stream));
     if (total == 0) return fail(g, MN_ERR_STATE, "no logged samples: run batches under MN_ORDER_EXPLORE");
     const uint32_t n = (uint32_t)std::min<unsigned long long>(total, g->ring);
-    static bool attr = false;
-    if (!attr) {
-        CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
-        attr = true;
-    }
-    int nsm = 0;
-    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->device));
+    CK(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM));
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)g->nsm);
+    CK(cudaMemsetAsync(g->d_train_status, 0, sizeof(uint32_t), g->stream));
     float l0 = 0.f, l1 = 0.f;
     for (uint32_t e = 0; e <= epochs; e++) {
         CK(cudaMemsetAsync(g->d_G, 0, sizeof(float) * P_COUNT, g->stream));
         CK(cudaMemsetAsync(g->d_loss, 0, sizeof(float), g->stream));
-        k_mlp_grad<<<nsm, TR_THREADS, TR_SMEM, g->stream>>>(g->d_SX, g->d_ST, n, g->d_P, g->d_G, g->d_loss);
+        k_mlp_grad_tc<<<grid, TC_M, TG_SMEM, g->stream>>>(g->d_SX, g->d_ST, n, g->d_P, g->d_G, g->d_loss,
+                                                         g->d_train_status);
         CKL();
         if (e == 0 || e == epochs) {
             float l = 0.f;
@@ -2266,6 +2269,10 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
         CKL();
     }
     g->packed = false;
+    uint32_t tst = 0;
+    CK(cudaMemcpyAsync(&tst, g->d_train_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (tst) return fail(g, MN_ERR_TIMEOUT, "training: MMA completion not seen within the wait bound");
     if (loss_first) *loss_first = l0;
     if (loss_last) *loss_last = l1;
     return MN_OK;
@@ -2634,8 +2641,10 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
     if (!params || (n && (!x || !y))) return fail(nullptr, MN_ERR_INVALID_ARG, "NULL argument");
     if (n > (1ull << 28)) return fail(nullptr, MN_ERR_INVALID_ARG, "too many rows");
     CK(cudaSetDevice(device));
-    DevBuf P, X, Y, W1, W2;
+    DevBuf P, X, Y, W1, W2, St;
     CK(cudaMalloc(&P.p, sizeof(float) * P_COUNT));
+    CK(cudaMalloc(&St.p, sizeof(uint32_t)));
+    CK(cudaMemset(St.p, 0, sizeof(uint32_t)));
     CK(cudaMalloc(&X.p, 2 * NF * std::max<uint64_t>(n, 1)));
     CK(cudaMalloc(&Y.p, sizeof(float) * std::max<uint64_t>(n, 1)));
     CK(cudaMalloc(&W1.p, 2 * NF * NH));
@@ -2645,10 +2654,16 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
     k_mlp_pack<<<cdiv(NH * NH, 256), 256>>>((float *)P.p, (__nv_bfloat16 *)W1.p, (__nv_bfloat16 *)W2.p);
     CK(cudaGetLastError());
     if (n) {
-        k_mlp_forward<<<cdiv(n, 16 * MLP_WARPS), MLP_WARPS * 32>>>(
+        int nsm = 0;
+        CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
+        CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        k_mlp_forward_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)nsm), TC_M, TC_SMEM>>>(
             (const __nv_bfloat16 *)X.p, nullptr, 1, (uint32_t)n, (const __nv_bfloat16 *)W1.p,
-            (const __nv_bfloat16 *)W2.p, (const float *)P.p, (float *)Y.p);
+            (const __nv_bfloat16 *)W2.p, (const float *)P.p, (float *)Y.p, (uint32_t *)St.p);
         CK(cudaGetLastError());
+        uint32_t st = 0;
+        CK(cudaMemcpy(&st, St.p, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (st) return fail(nullptr, MN_ERR_TIMEOUT, "tensor-core forward: MMA completion not seen");
         CK(cudaMemcpy(y, Y.p, sizeof(float) * n, cudaMemcpyDeviceToHost));
     }
     CK(cudaDeviceSynchronize());
@@ -2662,8 +2677,10 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
     if (!params || !grad || !loss || (n && (!x || !t))) return fail(nullptr, MN_ERR_INVALID_ARG, "NULL argument");
     if (n > (1ull << 28)) return fail(nullptr, MN_ERR_INVALID_ARG, "too many rows");
     CK(cudaSetDevice(device));
-    CK(cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TR_SMEM));
-    DevBuf P, X, T, G, L;
+    CK(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM));
+    DevBuf P, X, T, G, L, St;
+    CK(cudaMalloc(&St.p, sizeof(uint32_t)));
+    CK(cudaMemset(St.p, 0, sizeof(uint32_t)));
     CK(cudaMalloc(&P.p, sizeof(float) * P_COUNT));
     CK(cudaMalloc(&G.p, sizeof(float) * P_COUNT));
     CK(cudaMalloc(&L.p, sizeof(float)));
@@ -2678,9 +2695,15 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
     CK(cudaMemset(L.p, 0, sizeof(float)));
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
-    k_mlp_grad<<<nsm, TR_THREADS, TR_SMEM>>>((const __nv_bfloat16 *)X.p, (const float *)T.p,
-                                             (uint32_t)n, (const float *)P.p, (float *)G.p, (float *)L.p);
-    CK(cudaGetLastError());
+    if (n) {
+        k_mlp_grad_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)nsm), TC_M, TG_SMEM>>>(
+            (const __nv_bfloat16 *)X.p, (const float *)T.p, (uint32_t)n, (const float *)P.p, (float *)G.p,
+            (float *)L.p, (uint32_t *)St.p);
+        CK(cudaGetLastError());
+        uint32_t st = 0;
+        CK(cudaMemcpy(&st, St.p, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        if (st) return fail(nullptr, MN_ERR_TIMEOUT, "tensor-core gradient: MMA completion not seen");
+    }
     CK(cudaMemcpy(grad, G.p, sizeof(float) * P_COUNT, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(loss, L.p, sizeof(float), cudaMemcpyDeviceToHost));
     return MN_OK;

@@ -7,9 +7,10 @@
 // connected order of the same query -- only how much work it takes.
 //
 // Network: 16 features -> 128 -> 128 -> 1, ReLU, weights and activations in
-// BF16 with FP32 accumulation (inference: mma.sync m16n8k16 on the tensor
-// cores), FP32 master weights, mean squared error on log2(1 + work), Adam
-// (Kingma & Ba, 2015).  Training data are logged by the enumerator itself:
+// BF16 with FP32 accumulation, FP32 master weights, mean squared error on
+// log2(1 + work), Adam (Kingma & Ba, 2015).  Inference (k_mlp_forward_tc) and
+// the gradient (k_mlp_grad_tc) run on the 5th-generation tensor cores:
+// tcgen05.mma from shared-memory operand tiles into TMEM accumulators.  Training data are logged by the enumerator itself:
 // per seed the SM cycles spent on it (summed over the seed's own unit and
 // every subtree split off from it).
 #pragma once
@@ -95,17 +96,6 @@ __global__ void k_features(FeatParams p)
 
 // ------------------------------------------------------------------ inference
 
-__device__ __forceinline__ void mma_bf16(float &d0, float &d1, float &d2, float &d3, uint32_t a0,
-                                         uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(d0), "+f"(d1), "+f"(d2), "+f"(d3)
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -126,176 +116,538 @@ __global__ void k_mlp_pack(const float *P, __nv_bfloat16 *w1t, __nv_bfloat16 *w2
     }
 }
 
-constexpr int MLP_WARPS = 4;   // 16 rows per warp
+// ------------------------------------------------------------------ inference on tcgen05
+
+// 5th-generation tensor cores: the operands sit in shared memory as K-major
+// tiles of 8-row x 16-byte core matrices (no swizzling), the FP32
+// accumulators in tensor memory (TMEM, one lane per row), one thread issues
+// the MMAs and a commit to an mbarrier tells every thread when they are done.
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling:
+// start address, `lbo` bytes between core matrices adjacent along K, `sbo`
+// bytes between adjacent 8-row groups; bits 46-48 hold the descriptor
+// version (0b001), base offset, address mode and swizzle fields are 0.
+__device__ __forceinline__ unsigned long long umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9, 10-12 = 1), both K-major, N / 8 at bits 17-22, M / 16 at
+// bits 24-28.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(uint32_t m, uint32_t n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols)    // one whole warp
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(dst)), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()                            // one whole warp
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) // one whole warp
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D (TMEM) = A B^T (+ D when accumulate), A: M x K, B: N x K, K = 16
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, unsigned long long a_desc,
+                                          unsigned long long b_desc, uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+                 : "memory");
+}
+
+// arrive on *bar once every MMA this thread issued before has completed
+__device__ __forceinline__ void umma_commit(unsigned long long *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes
+// 32w .. 32w + 31), waited for within the same statement
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) in a K-major core-matrix tile whose rows
+// hold K elements of 2 bytes: core matrices along K are 128 bytes apart
+// (LBO), 8-row groups K / 8 * 128 bytes apart (SBO).
+__host__ __device__ constexpr uint32_t cm_off(uint32_t row, uint32_t k, uint32_t K)
+{
+    return (row >> 3) * (K / 8) * 128u + (k >> 3) * 128u + (row & 7u) * 16u + (k & 7u) * 2u;
+}
+
+constexpr uint32_t TC_M = 128;                         // rows per tile = TMEM lanes
+constexpr uint32_t TC_B1 = 0;                          // W1^T as B: N = 128 x K = 16
+constexpr uint32_t TC_B2 = TC_B1 + NH * NF * 2;        // W2^T as B: N = 128 x K = 128
+constexpr uint32_t TC_A1 = TC_B2 + NH * NH * 2;        // X tile: M = 128 x K = 16
+constexpr uint32_t TC_A2 = TC_A1 + TC_M * NF * 2;      // bf16(relu(layer 1)): M = 128 x K = 128
+constexpr uint32_t TC_VEC = TC_A2 + TC_M * NH * 2;     // b1, b2, w3 (FP32)
+constexpr uint32_t TC_BAR = TC_VEC + 3 * NH * 4;       // mbarrier, TMEM base address
+constexpr uint32_t TC_SMEM = TC_BAR + 16;
+constexpr uint32_t TC_TMEM_COLS = 2 * NH;              // layer 1 in columns [0, 128), layer 2 in [128, 256)
+constexpr uint32_t TC_WAIT_POLLS = 1u << 24;
 
 // y[r] = w3 . relu(W2^T bf16(relu(W1^T x_r + b1)) + b2) + b3 for rows r < n
-// (n read from *n_dev times `per`, or n_host when n_dev is NULL).
-__global__ void __launch_bounds__(MLP_WARPS * 32) k_mlp_forward(
+// (n read from *n_dev times `per`, or n_host when n_dev is NULL); 128 rows
+// per tile, tiles strided over the grid (at most one block per SM: each
+// holds 256 TMEM columns).  *status gets ST_TIMEOUT if an MMA completion was
+// not seen within the wait bound (every thread still runs every tile, so the
+// block's barriers stay matched).
+__global__ void __launch_bounds__(TC_M, 1) k_mlp_forward_tc(
     const __nv_bfloat16 *__restrict__ X, const uint32_t *n_dev, uint32_t per, uint32_t n_host,
     const __nv_bfloat16 *__restrict__ w1t, const __nv_bfloat16 *__restrict__ w2t,
-    const float *__restrict__ P, float *__restrict__ y)
+    const float *__restrict__ P, float *__restrict__ y, uint32_t *status)
 {
-    __shared__ __align__(16) __nv_bfloat16 sw1[NH * NF];
-    __shared__ __align__(16) __nv_bfloat16 sw2[NH * NH];
-    __shared__ float sb1[NH], sb2[NH], sw3[NH];
-    for (int i = threadIdx.x; i < NH * NF; i += blockDim.x) sw1[i] = w1t[i];
-    for (int i = threadIdx.x; i < NH * NH; i += blockDim.x) sw2[i] = w2t[i];
-    for (int i = threadIdx.x; i < NH; i += blockDim.x) {
-        sb1[i] = P[P_B1 + i]; sb2[i] = P[P_B2 + i]; sw3[i] = P[P_W3 + i];
-    }
-    __syncthreads();
+    extern __shared__ __align__(1024) uint8_t tcs[];
+    float *vb1 = reinterpret_cast<float *>(tcs + TC_VEC), *vb2 = vb1 + NH, *vw3 = vb2 + NH;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tcs + TC_BAR);
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(tcs + TC_BAR + 8);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
     const uint32_t n = n_dev ? *n_dev * per : n_host;
+    if (blockIdx.x * TC_M >= n) return;                // the whole block leaves together
+    // weights as B operands: w1t[h][f], w2t[o][h] are N x K row-major
+    for (uint32_t c = tid; c < NH * NF / 8; c += TC_M) {
+        const uint32_t r = c / (NF / 8), kc = c % (NF / 8);
+        *reinterpret_cast<uint4 *>(tcs + TC_B1 + cm_off(r, kc * 8, NF)) =
+            reinterpret_cast<const uint4 *>(w1t)[c];
+    }
+    for (uint32_t c = tid; c < NH * NH / 8; c += TC_M) {
+        const uint32_t r = c / (NH / 8), kc = c % (NH / 8);
+        *reinterpret_cast<uint4 *>(tcs + TC_B2 + cm_off(r, kc * 8, NH)) =
+            reinterpret_cast<const uint4 *>(w2t)[c];
+    }
+    for (uint32_t i = tid; i < NH; i += TC_M) {
+        vb1[i] = P[P_B1 + i];
+        vb2[i] = P[P_B2 + i];
+        vw3[i] = P[P_W3 + i];
+    }
     const float b3 = P[P_B3];
-    const int lane = threadIdx.x & 31, gq = lane >> 2, t4 = lane & 3;
-    const uint32_t *x32 = reinterpret_cast<const uint32_t *>(X);
-    const uint32_t *s1 = reinterpret_cast<const uint32_t *>(sw1);
-    const uint32_t *s2 = reinterpret_cast<const uint32_t *>(sw2);
-    for (uint32_t rb = (blockIdx.x * MLP_WARPS + (threadIdx.x >> 5)) * 16; rb < n;
-         rb += gridDim.x * MLP_WARPS * 16) {
-        const uint32_t r0 = rb + gq, r1 = rb + gq + 8;
-        // A fragment of X (16 rows x 16 features)
-        const uint32_t a0 = r0 < n ? x32[r0 * (NF / 2) + t4] : 0u;
-        const uint32_t a1 = r1 < n ? x32[r1 * (NF / 2) + t4] : 0u;
-        const uint32_t a2 = r0 < n ? x32[r0 * (NF / 2) + t4 + 4] : 0u;
-        const uint32_t a3 = r1 < n ? x32[r1 * (NF / 2) + t4 + 4] : 0u;
-        // layer 1 -> A fragments of layer 2 (k-block m = n-tiles 2m, 2m+1)
-        uint32_t h[NH / 16][4];
-#pragma unroll
-        for (int nt = 0; nt < NH / 8; nt++) {
-            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-            const int col = nt * 8 + gq;
-            mma_bf16(c0, c1, c2, c3, a0, a1, a2, a3, s1[col * (NF / 2) + t4], s1[col * (NF / 2) + t4 + 4]);
-            const int oc = nt * 8 + 2 * t4;
-            c0 = fmaxf(c0 + sb1[oc], 0.f); c1 = fmaxf(c1 + sb1[oc + 1], 0.f);
-            c2 = fmaxf(c2 + sb1[oc], 0.f); c3 = fmaxf(c3 + sb1[oc + 1], 0.f);
-            const int m = nt >> 1, half = nt & 1;
-            h[m][half * 2 + 0] = pack_bf16(c0, c1);
-            h[m][half * 2 + 1] = pack_bf16(c2, c3);
-        }
-        // layer 2 and the output dot product
-        float y0 = 0.f, y1 = 0.f;
-#pragma unroll 4
-        for (int nt = 0; nt < NH / 8; nt++) {
-            float c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-            const int col = nt * 8 + gq;
-#pragma unroll
-            for (int m = 0; m < NH / 16; m++)
-                mma_bf16(c0, c1, c2, c3, h[m][0], h[m][1], h[m][2], h[m][3],
-                         s2[col * (NH / 2) + m * 8 + t4], s2[col * (NH / 2) + m * 8 + t4 + 4]);
-            const int oc = nt * 8 + 2 * t4;
-            c0 = fmaxf(c0 + sb2[oc], 0.f); c1 = fmaxf(c1 + sb2[oc + 1], 0.f);
-            c2 = fmaxf(c2 + sb2[oc], 0.f); c3 = fmaxf(c3 + sb2[oc + 1], 0.f);
-            y0 += c0 * sw3[oc] + c1 * sw3[oc + 1];
-            y1 += c2 * sw3[oc] + c3 * sw3[oc + 1];
-        }
-        y0 += __shfl_xor_sync(FULL, y0, 1); y0 += __shfl_xor_sync(FULL, y0, 2);
-        y1 += __shfl_xor_sync(FULL, y1, 1); y1 += __shfl_xor_sync(FULL, y1, 2);
-        if (t4 == 0) {
-            if (r0 < n) y[r0] = y0 + b3;
-            if (r1 < n) y[r1] = y1 + b3;
-        }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
     }
-}
-
-// ------------------------------------------------------------------ training
-
-constexpr int TR_ROWS = 16, TR_THREADS = NH;
-constexpr size_t TR_SMEM = sizeof(float) * ((size_t)P_COUNT + TR_ROWS * (NF + 4 * NH + 2));
-
-__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-// Gradient of the mean squared error over rows [0, n) with the same BF16
-// rounding as inference (weights and the layer-1 activations), accumulated
-// per block in shared memory and added to g[] (FP32); the loss sum goes to
-// *loss.  Thread h owns hidden unit h.
-__global__ void __launch_bounds__(TR_THREADS) k_mlp_grad(
-    const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T, uint32_t n,
-    const float *__restrict__ P, float *__restrict__ G, float *__restrict__ loss)
-{
-    extern __shared__ float sm[];
-    float *dG = sm;                                  // P_COUNT
-    float *x = dG + P_COUNT;                         // [TR_ROWS][NF]
-    float *h1 = x + TR_ROWS * NF;                    // [TR_ROWS][NH] bf16-rounded relu
-    float *h2 = h1 + TR_ROWS * NH;                   // [TR_ROWS][NH] relu
-    float *d2 = h2 + TR_ROWS * NH;                   // dZ2
-    float *d1 = d2 + TR_ROWS * NH;                   // dZ1
-    float *dy = d1 + TR_ROWS * NH;                   // [TR_ROWS]
-    float *yy = dy + TR_ROWS;                        // [TR_ROWS]
-    const int h = threadIdx.x;
-    for (int i = h; i < P_COUNT; i += blockDim.x) dG[i] = 0.f;
-    float lsum = 0.f;
-    const float inv_n = 1.0f / (float)max(n, 1u);
+    if (warp == 0) {
+        tmem_alloc(tbase, TC_TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
     __syncthreads();
-    for (uint32_t r0 = blockIdx.x * TR_ROWS; r0 < n; r0 += gridDim.x * TR_ROWS) {
-        const int rows = (int)min((uint32_t)TR_ROWS, n - r0);
-        for (int i = h; i < TR_ROWS * NF; i += blockDim.x)
-            x[i] = i / NF < rows ? __bfloat162float(X[(size_t)(r0 + i / NF) * NF + i % NF]) : 0.f;
-        __syncthreads();
-        for (int r = 0; r < rows; r++) {             // layer 1 (unit h)
-            float z = P[P_B1 + h];
-            for (int f = 0; f < NF; f++) z += x[r * NF + f] * bf16r(P[P_W1 + f * NH + h]);
-            h1[r * NH + h] = z > 0.f ? bf16r(z) : 0.f;
-        }
-        __syncthreads();
-        for (int r = 0; r < rows; r++) {             // layer 2 (unit h)
-            float z = P[P_B2 + h];
-            for (int k = 0; k < NH; k++) z += h1[r * NH + k] * bf16r(P[P_W2 + k * NH + h]);
-            h2[r * NH + h] = z > 0.f ? z : 0.f;
-        }
-        __syncthreads();
-        if (h < TR_ROWS) {                           // output and dL/dy
-            float v = P[P_B3];
-            if (h < rows) {
-                for (int k = 0; k < NH; k++) v += h2[h * NH + k] * P[P_W3 + k];
-                const float e = v - T[r0 + h];
-                dy[h] = 2.f * e * inv_n;
-                lsum += e * e;
-            } else {
-                dy[h] = 0.f;
+    tc_fence_after();
+    const uint32_t tm = *tbase;
+    const uint32_t lane_addr = tm + ((warp * 32u) << 16);   // this warp's TMEM lanes
+    const uint32_t sbase = smem_u32(tcs);
+    constexpr uint32_t IDESC = umma_idesc_bf16(TC_M, NH);
+    uint32_t phase = 0;
+    bool stuck = false;
+    auto wait_mma = [&]() {
+        for (uint32_t it = 0; !mbar_try_wait(bar, phase); it++)
+            if (it >= TC_WAIT_POLLS) {
+                stuck = true;
+                break;
             }
-            yy[h] = v;
+        phase ^= 1u;
+        tc_fence_after();
+    };
+    for (uint32_t rb = blockIdx.x * TC_M; rb < n; rb += gridDim.x * TC_M) {   // same trip count in every thread
+        // X tile (rows past n are zero)
+        for (uint32_t c = tid; c < TC_M * NF / 8; c += TC_M) {
+            const uint32_t r = c / (NF / 8), kc = c % (NF / 8);
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (rb + r < n) v = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * (NF / 8) + kc];
+            *reinterpret_cast<uint4 *>(tcs + TC_A1 + cm_off(r, kc * 8, NF)) = v;
         }
+        fence_proxy_async_smem();
+        tc_fence_before();
         __syncthreads();
-        {
-            const float w3 = P[P_W3 + h];
-            float gw3 = 0.f, gb2 = 0.f;
-            for (int r = 0; r < rows; r++) {
-                gw3 += dy[r] * h2[r * NH + h];
-                const float dz = h2[r * NH + h] > 0.f ? dy[r] * w3 : 0.f;
-                d2[r * NH + h] = dz;
-                gb2 += dz;
-            }
-            dG[P_W3 + h] += gw3;
-            dG[P_B2 + h] += gb2;
-            if (h == 0) for (int r = 0; r < rows; r++) dG[P_B3] += dy[r];
+        tc_fence_after();
+        if (tid == 0) {                                  // layer 1: one K = 16 step
+            umma_bf16(tm, umma_desc(sbase + TC_A1, 128, NF / 8 * 128), umma_desc(sbase + TC_B1, 128, NF / 8 * 128),
+                      IDESC, 0);
+            umma_commit(bar);
         }
-        __syncthreads();
-        for (int k = 0; k < NH; k++) {               // dW2[k][h]
-            float s = 0.f;
-            for (int r = 0; r < rows; r++) s += h1[r * NH + k] * d2[r * NH + h];
-            dG[P_W2 + k * NH + h] += s;
-        }
-        for (int r = 0; r < rows; r++) {             // dZ1[r][h] through W2 row h
-            float s = 0.f;
-            for (int o = 0; o < NH; o++) s += bf16r(P[P_W2 + h * NH + o]) * d2[r * NH + o];
-            d1[r * NH + h] = h1[r * NH + h] > 0.f ? s : 0.f;
-        }
-        __syncthreads();
-        {
-            float gb1 = 0.f;
-            for (int r = 0; r < rows; r++) gb1 += d1[r * NH + h];
-            dG[P_B1 + h] += gb1;
-            for (int f = 0; f < NF; f++) {
-                float s = 0.f;
-                for (int r = 0; r < rows; r++) s += x[r * NF + f] * d1[r * NH + h];
-                dG[P_W1 + f * NH + h] += s;
+        wait_mma();
+        // layer-1 epilogue: row tid, bias, ReLU, BF16 -> A operand of layer 2
+#pragma unroll
+        for (uint32_t cc = 0; cc < NH / 32; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + cc * 32, v);
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                uint4 pk;
+                uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+                for (uint32_t e = 0; e < 4; e++) {
+                    const uint32_t h = cc * 32 + q * 8 + 2 * e;
+                    pw[e] = pack_bf16(fmaxf(v[q * 8 + 2 * e] + vb1[h], 0.f),
+                                      fmaxf(v[q * 8 + 2 * e + 1] + vb1[h + 1], 0.f));
+                }
+                *reinterpret_cast<uint4 *>(tcs + TC_A2 + cm_off(tid, cc * 32 + q * 8, NH)) = pk;
             }
         }
+        fence_proxy_async_smem();
+        tc_fence_before();
         __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {                                  // layer 2: K = 128 in 8 steps
+#pragma unroll
+            for (uint32_t s = 0; s < NH / 16; s++)
+                umma_bf16(tm + NH, umma_desc(sbase + TC_A2 + s * 256, 128, NH / 8 * 128),
+                          umma_desc(sbase + TC_B2 + s * 256, 128, NH / 8 * 128), IDESC, s);
+            umma_commit(bar);
+        }
+        wait_mma();
+        // layer-2 epilogue: bias, ReLU, dot with w3
+        float acc = b3;
+#pragma unroll
+        for (uint32_t cc = 0; cc < NH / 32; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + NH + cc * 32, v);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; j++) acc += fmaxf(v[j] + vb2[cc * 32 + j], 0.f) * vw3[cc * 32 + j];
+        }
+        if (rb + tid < n) y[rb + tid] = acc;
+        tc_fence_before();
+        __syncthreads();                                 // the tiles and TMEM are free again
+        tc_fence_after();
     }
-    for (int i = h; i < P_COUNT; i += blockDim.x) atomicAdd(&G[i], dG[i]);
-    if (h < TR_ROWS) atomicAdd(loss, lsum * inv_n);
+    if (stuck) atomicOr(status, ST_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, TC_TMEM_COLS);
 }
+
+// ------------------------------------------------------------------ training on tcgen05
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; i++) v[i] = __uint_as_float(r[i]);
+}
+
+// Column sums of a warp's 32 x 32 block: lane L holds row L's values v[0..31];
+// afterwards v[0] of lane j is the sum over the 32 rows of column j (each
+// step halves the columns a lane keeps and adds its partner's share of them).
+__device__ __forceinline__ float warp_column_sums(float (&v)[32], uint32_t lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & (uint32_t)s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; i++) {
+            const float send = upper ? v[i] : v[i + s];
+            const float keep = upper ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(FULL, send, s);
+        }
+    }
+    return v[0];
+}
+
+// shared-memory layout of the training kernel (bytes); operand tiles are
+// K-major core-matrix tiles as in k_mlp_forward_tc
+constexpr uint32_t TG_B1 = 0;                          // W1^T as B: N = 128 (h) x K = 16 (f)
+constexpr uint32_t TG_B2 = TG_B1 + NH * NF * 2;        // W2^T as B: N = 128 (o) x K = 128 (h)
+constexpr uint32_t TG_BW = TG_B2 + NH * NH * 2;        // W2 as B:   N = 128 (h) x K = 128 (o)
+constexpr uint32_t TG_A1 = TG_BW + NH * NH * 2;        // X tile:    M = 128 (r) x K = 16 (f)
+constexpr uint32_t TG_BX = TG_A1 + TC_M * NF * 2;      // X^T as B:  N = 16 (f) x K = 128 (r)
+constexpr uint32_t TG_A2 = TG_BX + NF * TC_M * 2;      // h1 [r][h], then dZ2 [r][o]
+constexpr uint32_t TG_A3 = TG_A2 + TC_M * NH * 2;      // h1^T [h][r], then dZ1^T [h][r]
+constexpr uint32_t TG_BD = TG_A3 + NH * TC_M * 2;      // dZ2^T as B: N = 128 (o) x K = 128 (r)
+constexpr uint32_t TG_VEC = TG_BD + NH * TC_M * 2;     // b1, b2, w3 (FP32)
+constexpr uint32_t TG_BAR = TG_VEC + 3 * NH * 4;       // mbarrier, TMEM base address
+constexpr uint32_t TG_SMEM = TG_BAR + 16;
+// TMEM columns: z1 then dH1 [0, 128), z2 [128, 256), dW2 [256, 384), dW1^T [384, 400)
+constexpr uint32_t TG_TMEM_COLS = 512;
+static_assert(TG_SMEM <= 227u * 1024u, "training tiles exceed shared memory");
+
+// Gradient of the mean squared error over rows [0, n) (same BF16 roundings
+// as inference: weights and layer-1 activations; straight-through), 128 rows
+// per tile on the tensor cores: forward z1 = X W1, z2 = h1 W2; backward
+// dW2 = h1^T dZ2, dH1 = dZ2 W2^T, dW1 = X^T dZ1 with dZ2 and dZ1 rounded to
+// BF16 as MMA operands (FP32 accumulation in TMEM across the block's tiles);
+// the bias and w3 gradients and the loss are FP32 column sums.  Adds to G[]
+// and *loss; *status gets ST_TIMEOUT if an MMA completion was not seen
+// within the wait bound.  At most one block per SM (512 TMEM columns).
+__global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
+    const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T, uint32_t n,
+    const float *__restrict__ P, float *__restrict__ G, float *__restrict__ loss, uint32_t *status)
+{
+    extern __shared__ __align__(1024) uint8_t tgs[];
+    float *vb1 = reinterpret_cast<float *>(tgs + TG_VEC), *vb2 = vb1 + NH, *vw3 = vb2 + NH;
+    unsigned long long *bar = reinterpret_cast<unsigned long long *>(tgs + TG_BAR);
+    uint32_t *tbase = reinterpret_cast<uint32_t *>(tgs + TG_BAR + 8);
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (blockIdx.x * TC_M >= n) return;                // the whole block leaves together
+    auto st_bf16 = [&](uint32_t off, float v) {
+        *reinterpret_cast<__nv_bfloat16 *>(tgs + off) = __float2bfloat16_rn(v);
+    };
+    // weights, rounded to BF16, as B operands
+    for (uint32_t i = tid; i < NF * NH; i += TC_M) {         // (h, f) = W1[f][h]
+        const uint32_t h = i / NF, f = i % NF;
+        st_bf16(TG_B1 + cm_off(h, f, NF), P[P_W1 + f * NH + h]);
+    }
+    for (uint32_t i = tid; i < NH * NH; i += TC_M) {         // W2[a][b]
+        const uint32_t a = i / NH, b = i % NH;
+        const float w = P[P_W2 + i];
+        st_bf16(TG_B2 + cm_off(b, a, NH), w);                  // (o, h) = W2[h][o]
+        st_bf16(TG_BW + cm_off(a, b, NH), w);                  // (h, o) = W2[h][o]
+    }
+    for (uint32_t i = tid; i < NH; i += TC_M) {
+        vb1[i] = P[P_B1 + i];
+        vb2[i] = P[P_B2 + i];
+        vw3[i] = P[P_W3 + i];
+    }
+    const float b3 = P[P_B3];
+    const float inv_n = 1.0f / (float)n;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    if (warp == 0) {
+        tmem_alloc(tbase, TG_TMEM_COLS);
+        tmem_relinquish();
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tm = *tbase;
+    const uint32_t lane_addr = tm + ((warp * 32u) << 16);
+    const uint32_t sb = smem_u32(tgs);
+    constexpr uint32_t ID_128 = umma_idesc_bf16(TC_M, NH), ID_16 = umma_idesc_bf16(TC_M, NF);
+    constexpr uint32_t SBO16 = NF / 8 * 128, SBO128 = NH / 8 * 128;
+    uint32_t phase = 0;
+    bool stuck = false;
+    auto wait_mma = [&]() {
+        for (uint32_t it = 0; !mbar_try_wait(bar, phase); it++)
+            if (it >= TC_WAIT_POLLS) {
+                stuck = true;
+                break;
+            }
+        phase ^= 1u;
+        tc_fence_after();
+    };
+    auto sync_for_mma = [&]() {                          // generic smem writes -> MMA operands
+        fence_proxy_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+    };
+    float acc_b1[4] = {0.f, 0.f, 0.f, 0.f}, acc_b2[4] = {0.f, 0.f, 0.f, 0.f}, acc_w3[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc_loss = 0.f, acc_b3 = 0.f;
+    uint32_t first = 1;
+    for (uint32_t rb = blockIdx.x * TC_M; rb < n; rb += gridDim.x * TC_M) {   // same trip count in every thread
+        const uint32_t r = tid;                          // this thread's row of the tile
+        const bool valid = rb + r < n;
+        // X tile as A (rows) and as B (transposed)
+        {
+            uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+            if (valid) {
+                v0 = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * 2];
+                v1 = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * 2 + 1];
+            }
+            *reinterpret_cast<uint4 *>(tgs + TG_A1 + cm_off(r, 0, NF)) = v0;
+            *reinterpret_cast<uint4 *>(tgs + TG_A1 + cm_off(r, 8, NF)) = v1;
+            const __nv_bfloat16 *e0 = reinterpret_cast<const __nv_bfloat16 *>(&v0);
+            const __nv_bfloat16 *e1 = reinterpret_cast<const __nv_bfloat16 *>(&v1);
+#pragma unroll
+            for (uint32_t f = 0; f < 8; f++) {
+                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BX + cm_off(f, r, TC_M)) = e0[f];
+                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BX + cm_off(f + 8, r, TC_M)) = e1[f];
+            }
+        }
+        const float tgt = valid ? T[rb + r] : 0.f;
+        sync_for_mma();
+        if (tid == 0) {                                  // z1 = X W1
+            umma_bf16(tm, umma_desc(sb + TG_A1, 128, SBO16), umma_desc(sb + TG_B1, 128, SBO16), ID_128, 0);
+            umma_commit(bar);
+        }
+        wait_mma();
+        // h1 = bf16(relu(z1 + b1)) -> A2 [r][h] and A3 [h][r]; keep its sign mask
+        uint32_t m1[4];
+#pragma unroll
+        for (uint32_t cc = 0; cc < 4; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + cc * 32, v);
+            m1[cc] = 0;
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                uint4 pk;
+                uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+                for (uint32_t e = 0; e < 4; e++) {
+                    const uint32_t j = q * 8 + 2 * e, h = cc * 32 + j;
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(fmaxf(v[j] + vb1[h], 0.f),
+                                                                    fmaxf(v[j + 1] + vb1[h + 1], 0.f));
+                    pw[e] = *reinterpret_cast<const uint32_t *>(&hb);
+                    if (__bfloat162float(hb.x) > 0.f) m1[cc] |= 1u << j;
+                    if (__bfloat162float(hb.y) > 0.f) m1[cc] |= 1u << (j + 1);
+                    *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(h, r, TC_M)) = hb.x;
+                    *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(h + 1, r, TC_M)) = hb.y;
+                }
+                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, cc * 32 + q * 8, NH)) = pk;
+            }
+        }
+        sync_for_mma();
+        if (tid == 0) {                                  // z2 = h1 W2
+#pragma unroll
+            for (uint32_t s = 0; s < NH / 16; s++)
+                umma_bf16(tm + NH, umma_desc(sb + TG_A2 + s * 256, 128, SBO128),
+                          umma_desc(sb + TG_B2 + s * 256, 128, SBO128), ID_128, s);
+            umma_commit(bar);
+        }
+        wait_mma();
+        // output, error and dy (rows past n contribute nothing)
+        float yv = b3;
+#pragma unroll
+        for (uint32_t cc = 0; cc < 4; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + NH + cc * 32, v);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; j++) yv += fmaxf(v[j] + vb2[cc * 32 + j], 0.f) * vw3[cc * 32 + j];
+        }
+        const float err = valid ? yv - tgt : 0.f;
+        const float dy = 2.f * err * inv_n;
+        acc_loss += err * err;
+        acc_b3 += dy;
+        // dZ2 = dy w3 [z2 + b2 > 0] -> A2 [r][o] (BF16) and BD [o][r]; w3 and b2 column sums
+#pragma unroll
+        for (uint32_t cc = 0; cc < 4; cc++) {
+            float v[32], gw[32];
+            tmem_ld32(lane_addr + NH + cc * 32, v);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; j++) {
+                const uint32_t o = cc * 32 + j;
+                const float z = v[j] + vb2[o];
+                gw[j] = z > 0.f ? dy * z : 0.f;
+                v[j] = z > 0.f ? dy * vw3[o] : 0.f;
+            }
+#pragma unroll
+            for (uint32_t q = 0; q < 4; q++) {
+                uint4 pk;
+                uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
+#pragma unroll
+                for (uint32_t e = 0; e < 4; e++) {
+                    const uint32_t j = q * 8 + 2 * e, o = cc * 32 + j;
+                    const __nv_bfloat162 db = __floats2bfloat162_rn(v[j], v[j + 1]);
+                    pw[e] = *reinterpret_cast<const uint32_t *>(&db);
+                    *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BD + cm_off(o, r, TC_M)) = db.x;
+                    *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BD + cm_off(o + 1, r, TC_M)) = db.y;
+                }
+                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, cc * 32 + q * 8, NH)) = pk;
+            }
+            acc_w3[cc] += warp_column_sums(gw, lane);
+            acc_b2[cc] += warp_column_sums(v, lane);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (uint32_t s = 0; s < TC_M / 16; s++)     // dW2 += h1^T dZ2 (K = rows)
+                umma_bf16(tm + 2 * NH, umma_desc(sb + TG_A3 + s * 256, 128, SBO128),
+                          umma_desc(sb + TG_BD + s * 256, 128, SBO128), ID_128, (s | (first ^ 1u)) != 0);
+#pragma unroll
+            for (uint32_t s = 0; s < NH / 16; s++)       // dH1 = dZ2 W2^T (K = o)
+                umma_bf16(tm, umma_desc(sb + TG_A2 + s * 256, 128, SBO128),
+                          umma_desc(sb + TG_BW + s * 256, 128, SBO128), ID_128, s);
+            umma_commit(bar);
+        }
+        wait_mma();
+        // dZ1 = dH1 [h1 > 0] -> A3 [h][r] (BF16); b1 column sums
+#pragma unroll
+        for (uint32_t cc = 0; cc < 4; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + cc * 32, v);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; j++) {
+                v[j] = (m1[cc] >> j) & 1u ? v[j] : 0.f;
+                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(cc * 32 + j, r, TC_M)) =
+                    __float2bfloat16_rn(v[j]);
+            }
+            acc_b1[cc] += warp_column_sums(v, lane);
+        }
+        sync_for_mma();
+        if (tid == 0) {                                  // dW1^T += dZ1^T X (K = rows)
+#pragma unroll
+            for (uint32_t s = 0; s < TC_M / 16; s++)
+                umma_bf16(tm + 3 * NH, umma_desc(sb + TG_A3 + s * 256, 128, SBO128),
+                          umma_desc(sb + TG_BX + s * 256, 128, SBO128), ID_16, (s | (first ^ 1u)) != 0);
+            umma_commit(bar);
+        }
+        wait_mma();
+        first = 0;
+        tc_fence_before();
+        __syncthreads();                                 // A1, BX, A2, A3, BD are free again
+        tc_fence_after();
+    }
+    // dW2[h][o] is TMEM lane h, column 256 + o; dW1[f][h] lane h, column 384 + f
+    {
+        const uint32_t h = tid;
+#pragma unroll
+        for (uint32_t cc = 0; cc < 4; cc++) {
+            float v[32];
+            tmem_ld32(lane_addr + 2 * NH + cc * 32, v);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; j++) atomicAdd(&G[P_W2 + h * NH + cc * 32 + j], v[j]);
+        }
+        float w[16];
+        tmem_ld16(lane_addr + 3 * NH, w);
+#pragma unroll
+        for (uint32_t f = 0; f < NF; f++) atomicAdd(&G[P_W1 + f * NH + h], w[f]);
+    }
+#pragma unroll
+    for (uint32_t cc = 0; cc < 4; cc++) {                // lane j of each warp: column 32 cc + j
+        atomicAdd(&G[P_B1 + cc * 32 + lane], acc_b1[cc]);
+        atomicAdd(&G[P_B2 + cc * 32 + lane], acc_b2[cc]);
+        atomicAdd(&G[P_W3 + cc * 32 + lane], acc_w3[cc]);
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        acc_loss += __shfl_xor_sync(FULL, acc_loss, d);
+        acc_b3 += __shfl_xor_sync(FULL, acc_b3, d);
+    }
+    if (lane == 0) {
+        atomicAdd(loss, acc_loss * inv_n);
+        atomicAdd(&G[P_B3], acc_b3);
+    }
+    if (stuck) atomicOr(status, ST_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tm, TG_TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ optimiser
 
 // One Adam step (Kingma & Ba 2015) on the FP32 master parameters.
 __global__ void k_adam(float *P, const float *G, float *M1, float *M2, int n, float lr, float b1,
