@@ -219,9 +219,11 @@ mn_status mn_set_order_policy(mn_graph *g, uint32_t policy);
 
 /* Train the work model on the samples logged under MN_ORDER_EXPLORE: full
  * batch Adam (lr, beta1 0.9, beta2 0.999, eps 1e-8) on the mean squared error
- * of log2(1 + cycles) (the SM cycles the enumerator spent per seed), `epochs` steps; the loss before the first and after the
- * last step go to *loss_first / *loss_last (either may be NULL).
- * MN_ERR_STATE if nothing has been logged. */
+ * of log2(1 + cycles) (the SM cycles the enumerator spent per seed), `epochs`
+ * steps, each gradient on the tensor cores (see mn_mlp_gradient); the loss
+ * before the first and after the last step go to *loss_first / *loss_last
+ * (either may be NULL).  MN_ERR_STATE if nothing has been logged,
+ * MN_ERR_TIMEOUT if an MMA completion was not seen within the wait bound. */
 mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *loss_first,
                                float *loss_last);
 
@@ -230,10 +232,13 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
 mn_status mn_order_model_params(mn_graph *g, float *get, const float *set);
 
 /* Test hooks of the model's kernels, host pointers, on `device`: the
- * tensor-core forward pass over n rows of 16 BF16 features (x holds raw BF16
- * bit patterns) into y[n], and the gradient of the mean squared error against
- * targets t[n] into grad[MN_MLP_PARAMS] with the loss in *loss.  Both use
- * BF16 weights and BF16 layer-1 activations with FP32 accumulation. */
+ * tensor-core (tcgen05) forward pass over n rows of 16 BF16 features (x holds
+ * raw BF16 bit patterns) into y[n], and the tensor-core gradient of the mean
+ * squared error against targets t[n] into grad[MN_MLP_PARAMS] with the loss
+ * in *loss.  Both use BF16 weights and BF16 layer-1 activations with FP32
+ * accumulation; the gradient also rounds dZ2 and dZ1 to BF16 as MMA
+ * operands.  MN_ERR_TIMEOUT if an MMA completion was not seen within the
+ * kernels' wait bound. */
 mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x, uint64_t n,
                          float *y);
 mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x, const float *t,
