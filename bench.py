@@ -129,6 +129,26 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
+def measured_bf16_peak(sustained=False):
+    """Dense BF16 tensor throughput in TFLOP/s (cuBLAS, MEASURED_PEAKS.json):
+    the burst figure for a kernel timed alone, the sustained one for a kernel
+    inside a long loop."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        k = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+        if k in d:
+            return float(d[k]), "measured"
+    return (1400.0 if sustained else 1800.0), "fallback"
+
+
+# tensor-core flops per row of the work model (16 -> 128 -> 128 -> 1): the
+# forward's two MMAs, and the gradient's forward plus dW2, dH1 and dW1
+MLP_FWD_FLOPS = 2 * (16 * 128 + 128 * 128)
+MLP_GRAD_FLOPS = 2 * (2 * 16 * 128 + 3 * 128 * 128)
+NCAND = 4                          # candidate matching orders scored per seed
+
+
 # ------------------------------------------------------------------ CPU oracle sample
 
 def oracle_sample(stream, queries, W, B, batch_index, sample, seed=7):
@@ -424,7 +444,7 @@ def main():
         line["batched_uneven"] = {k: extra[k] for k in (
             "value", "unit", "ms_per_step", "config", "plain", "learned_vs_plain", "latency_ms",
             "embeddings_per_step", "stage_ms_per_step", "work_per_step", "roofline", "tuning", "train",
-            "clocks", "filtered", "presplit_gain")}
+            "clocks", "filtered", "presplit_gain", "model_roofline")}
         line["gpu_launches"] += extra["gpu_launches"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         W, B = main_wl["window"], main_wl["batch"]
@@ -556,8 +576,10 @@ def run_workload(args, ctx, wl, with_e2e):
         if policy == "learned":
             t0 = time.perf_counter()
             l0, l1 = g.train_order_model(epochs=args.train_epochs, lr=2e-3)
+            ts = g.stats()
             res["train"] = {"loss_first": l0, "loss_last": l1, "epochs": args.train_epochs,
-                            "seconds": time.perf_counter() - t0}
+                            "seconds": time.perf_counter() - t0, "device_ms": ts["ms_train"],
+                            "rows": ts["train_rows"]}
             g.set_order_policy("learned")
             if not args.tuning:                                  # online autotuning on live batches
                 g.autotune(1)
@@ -663,7 +685,8 @@ def run_workload(args, ctx, wl, with_e2e):
     # ---- roofline of the dominant stage, from the live event timings
     peak, peak_kind = measured_peaks()
     stage_ms = {"enumerate": st["ms_enumerate"], "adjacency": st["ms_adjacency"],
-                "ingest": st["ms_ingest"], "seeds": st["ms_seeds"], "expire": st["ms_expire"]}
+                "ingest": st["ms_ingest"], "seeds": st["ms_seeds"], "expire": st["ms_expire"],
+                "model": st["ms_model"]}
     # Algorithmic bytes of the enumerator (the method's traffic, counted from
     # the device work counters): per tested adjacency entry 8 B (neighbour,
     # seq) + 4 B DEBI word + 8 B timestamp when the query is temporal; per
@@ -709,10 +732,29 @@ def run_workload(args, ctx, wl, with_e2e):
     # read and written once per batch
     adj_alg = 16 * B
     adj_layout = 4 * 2 * (W + B) * 12
-    adj = {"kernel": "adjacency update (sort+compact+merge+offsets)",
+    adj = {"kernel": "adjacency update (delta sort + one-pass merge + offsets)",
            "ms_per_batch": st["ms_adjacency"] / K,
            "achieved_layout": adj_layout / (st["ms_adjacency"] / K / 1e3) / 1e9 if st["ms_adjacency"] else None,
            "unit": "GB/s", "algorithmic_bytes_per_batch": adj_alg, "layout_bytes_per_batch": adj_layout}
+
+    # the work model's tensor-core kernels: the forward in every timed batch
+    # (seeds x NCAND rows), the gradient kernel over the training passes
+    bf16_burst, bf16_kind = measured_bf16_peak()
+    model_roof = None
+    if st.get("ms_model"):
+        fl = st["seeds"] * NCAND * MLP_FWD_FLOPS / max(1, st["model_launches"])
+        ms = st["ms_model"] / max(1, st["model_launches"])
+        model_roof = {"kernel": "k_mlp_forward_tc", "bound": "tensor", "unit": "TFLOP/s",
+                      "achieved": fl / (ms / 1e3) / 1e12, "peak": bf16_burst, "ms_per_launch": ms,
+                      "flops_per_launch": fl, "peak_source": f"{bf16_kind} dense BF16 (cuBLAS burst)"}
+        model_roof["frac"] = model_roof["achieved"] / bf16_burst
+    tr = learned.get("train") or {}
+    if tr.get("device_ms"):
+        fl = tr["rows"] * MLP_GRAD_FLOPS
+        tr["roofline"] = {"kernel": "k_mlp_grad_tc (+ k_adam)", "bound": "tensor", "unit": "TFLOP/s",
+                          "achieved": fl / (tr["device_ms"] / 1e3) / 1e12, "peak": bf16_burst,
+                          "peak_source": f"{bf16_kind} dense BF16 (cuBLAS burst)"}
+        tr["roofline"]["frac"] = tr["roofline"]["achieved"] / bf16_burst
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": WU,
@@ -768,6 +810,7 @@ def run_workload(args, ctx, wl, with_e2e):
         "gpu_launches": st["kernel_launches"],
         "roofline": roof,
         "adjacency_roofline": adj,
+        "model_roofline": model_roof,
         "clocks": clocks,
         "e2e": e2e,
     }

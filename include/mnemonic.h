@@ -536,6 +536,10 @@ typedef struct {
     uint64_t graph_instantiations; /* graph instantiations (the rest were updated in place) */
     uint64_t spill_bytes;          /* bytes copied to the host spill (mn_set_spill) */
     uint64_t entries_staged;       /* adjacency entries read through staged windows */
+    double   ms_model;             /* tensor-core forward of the work model (order choice) */
+    uint64_t model_launches;       /* its launches */
+    double   ms_train;             /* mn_train_order_model on the device (gradients + Adam) */
+    uint64_t train_rows;           /* rows through the gradient kernel (samples x passes) */
 } mn_stats;
 
 /* Turn per-stage event timing on (1) or off (0, the default). */

@@ -48,7 +48,7 @@ struct Ctrl {
     unsigned long long time_cut;        // edges a time window expires after this batch
 };
 
-enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_FILTER, S_COUNT };
+enum Stage { S_INGEST = 0, S_ADJ, S_SEEDS, S_ENUM, S_EXPIRE, S_FILTER, S_MODEL, S_COUNT };
 
 struct QueryHost {
     uint32_t nv = 0, ne = 0, iso = 0, temporal = 0;
@@ -332,7 +332,8 @@ void collect_timing(mn_graph *g)
         float ms = 0.f;
         cudaEventElapsedTime(&ms, p.second.first, p.second.second);
         double *dst[S_COUNT] = {&g->stats.ms_ingest, &g->stats.ms_adjacency, &g->stats.ms_seeds,
-                                &g->stats.ms_enumerate, &g->stats.ms_expire, &g->stats.ms_filter};
+                                &g->stats.ms_enumerate, &g->stats.ms_expire, &g->stats.ms_filter,
+                                &g->stats.ms_model};
         *dst[p.first] += ms;
         g->ev_pool.push_back(p.second.first);
         g->ev_pool.push_back(p.second.second);
@@ -674,10 +675,13 @@ mn_status choose_orders(mn_graph *g, int phase)
         k_features<<<grid, 256, 0, g->stream>>>(feat_params(g, phase, true));
         CKL();
         CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+        stage_begin(g);
         k_mlp_forward_tc<<<g->nsm, TC_M, TC_SMEM, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND, 0,
                                                                g->d_w1t, g->d_w2t, g->d_P, g->d_y,
                                                                &g->d_ctrl->status);
         CKL();
+        stage_end(g, S_MODEL);
+        g->stats.model_launches++;
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
                                             1.0f, g->presplit_log2);
         CKL();
@@ -1162,9 +1166,10 @@ mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
         const uint64_t edges = s == 0 ? n_new : n_expired;
         if (!edges) continue;
         for (size_t q = 0; q < g->queries.size() && q < g->rec_rate[s].size(); q++) {
-            // half again the decayed maximum: batch-to-batch swings of one
-            // query's output stay inside the list
-            const double est = 1.5 * g->rec_rate[s][q] * (double)edges;
+            // three times the decayed maximum: a batch that brings a hub
+            // into play multiplies one query's output, and a second launch
+            // costs more than the memory (lists are grown within the budget)
+            const double est = 3.0 * g->rec_rate[s][q] * (double)edges;
             if (est <= (double)g->queries[q].out_cap[s]) continue;
             bool grown = false;
             TRY(ensure_out_cap(g, q, s, (uint64_t)est, &grown, &over));
@@ -2247,6 +2252,8 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
     CK(cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM));
     const uint32_t grid = (uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)g->nsm);
     CK(cudaMemsetAsync(g->d_train_status, 0, sizeof(uint32_t), g->stream));
+    cudaEvent_t t0 = take_event(g), t1 = take_event(g);
+    CK(cudaEventRecord(t0, g->stream));
     float l0 = 0.f, l1 = 0.f;
     for (uint32_t e = 0; e <= epochs; e++) {
         CK(cudaMemsetAsync(g->d_G, 0, sizeof(float) * P_COUNT, g->stream));
@@ -2269,9 +2276,16 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
         CKL();
     }
     g->packed = false;
+    CK(cudaEventRecord(t1, g->stream));
     uint32_t tst = 0;
     CK(cudaMemcpyAsync(&tst, g->d_train_status, sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    float tms = 0.f;
+    CK(cudaEventElapsedTime(&tms, t0, t1));
+    g->ev_pool.push_back(t0);
+    g->ev_pool.push_back(t1);
+    g->stats.ms_train += tms;
+    g->stats.train_rows += (uint64_t)n * (epochs + 1);
     if (tst) return fail(g, MN_ERR_TIMEOUT, "training: MMA completion not seen within the wait bound");
     if (loss_first) *loss_first = l0;
     if (loss_last) *loss_last = l1;

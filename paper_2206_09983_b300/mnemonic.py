@@ -89,7 +89,9 @@ class Stats(C.Structure):
                 ("rerun_launches", C.c_uint64), ("dualsim_passes", C.c_uint64),
                 ("ms_filter", C.c_double), ("seeds_filtered", C.c_uint64), ("filter_changes", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
-                ("spill_bytes", C.c_uint64), ("entries_staged", C.c_uint64)]
+                ("spill_bytes", C.c_uint64), ("entries_staged", C.c_uint64),
+                ("ms_model", C.c_double), ("model_launches", C.c_uint64),
+                ("ms_train", C.c_double), ("train_rows", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
