@@ -563,11 +563,17 @@ __global__ void __launch_bounds__(CBLK) k_merge_live(Adj4 A, Adj4 B, Adj4 O, uin
     // delta entries anchored in this tile: [jlo, jhi)
     if (threadIdx.x == 0) jr[0] = lower_in(an, 0, nB, i0);
     if (threadIdx.x == 1) jr[1] = last_tile ? nB : lower_in(an, 0, nB, i1);
-    uint32_t sv[CITEMS], r[CITEMS];
+    uint32_t sv[CITEMS], kv[CITEMS], nv[CITEMS], r[CITEMS];
+#pragma unroll
+    for (int u = 0; u < CITEMS; u++) {          // all three arrays in flight at once
+        const uint32_t i = i0 + u * CBLK + threadIdx.x;
+        sv[u] = i < i1 ? S[i] : 0;
+        kv[u] = i < i1 ? K[i] : 0;
+        nv[u] = i < i1 ? N[i] : 0;
+    }
 #pragma unroll
     for (int u = 0; u < CITEMS; u++) {
         const uint32_t i = i0 + u * CBLK + threadIdx.x;
-        sv[u] = i < i1 ? S[i] : 0;
         r[u] = (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) ? 1u : 0u;
     }
     uint32_t total;
@@ -588,8 +594,8 @@ __global__ void __launch_bounds__(CBLK) k_merge_live(Adj4 A, Adj4 B, Adj4 O, uin
         if (i < i1 && (uint32_t)(sv[u] - lo32) < live_span) {
             const uint32_t jp = in_smem ? jlo + upper_in(sa, 0, jhi - jlo, i) : upper_in(an, jlo, jhi, i);
             const uint32_t o = live0 + r[u] + jp;
-            OK[o] = K[i];
-            ON[o] = N[i];
+            OK[o] = kv[u];
+            ON[o] = nv[u];
             OS[o] = sv[u];
         }
     }

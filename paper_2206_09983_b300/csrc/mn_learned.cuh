@@ -215,11 +215,12 @@ constexpr uint32_t TC_WAIT_POLLS = 1u << 24;
 
 // y[r] = w3 . relu(W2^T bf16(relu(W1^T x_r + b1)) + b2) + b3 for rows r < n
 // (n read from *n_dev times `per`, or n_host when n_dev is NULL); 128 rows
-// per tile, tiles strided over the grid (at most one block per SM: each
-// holds 256 TMEM columns).  *status gets ST_TIMEOUT if an MMA completion was
+// per tile, tiles strided over the grid (launched with two blocks per SM:
+// each holds 256 of the SM's 512 TMEM columns, so one block's epilogue runs
+// while the other's MMAs do).  *status gets ST_TIMEOUT if an MMA completion was
 // not seen within the wait bound (every thread still runs every tile, so the
 // block's barriers stay matched).
-__global__ void __launch_bounds__(TC_M, 1) k_mlp_forward_tc(
+__global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
     const __nv_bfloat16 *__restrict__ X, const uint32_t *n_dev, uint32_t per, uint32_t n_host,
     const __nv_bfloat16 *__restrict__ w1t, const __nv_bfloat16 *__restrict__ w2t,
     const float *__restrict__ P, float *__restrict__ y, uint32_t *status)
