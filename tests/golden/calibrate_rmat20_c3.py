@@ -95,11 +95,11 @@ def search(i, max_trials=400):
     for trial in range(max_trials):
         el, vl = draw_labels(rng, w, len(edges), nv, temp)
         q = workloads.c3_query(nv, edges, el, vl)
-        est, exact, verdict = None, None, "sparse"
+        est, exact, outcome = None, None, "sparse"
         for sample, budget in ((1024, 2 * 10**7), (8192, 2 * 10**8), (B, 2 * 10**9)):
             est, cnt, complete = _count(q, W, B, sample, rng, budget)
             if est is None or est > 8 * HI_T:
-                verdict = "dense"
+                outcome = "dense"
                 break
             if est == 0:
                 # as dense as labels go, or just below a draw that was too
@@ -108,12 +108,12 @@ def search(i, max_trials=400):
                     est, cnt, complete = _count(q, W, B, B, rng, 5 * 10**8)
                     if complete:
                         exact = cnt
-                        verdict = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
+                        outcome = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
                 break
             if sample == B:
                 exact = cnt
-                verdict = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
-        if verdict == "ok":
+                outcome = "sparse" if cnt < LO_T else ("dense" if cnt > HI_T else "ok")
+        if outcome == "ok":
             return dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
                         first_batch_new=exact, trials=trial + 1, accepted=True,
                         seconds=time.time() - t0)
@@ -121,8 +121,8 @@ def search(i, max_trials=400):
             best = dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
                         first_batch_new=exact, trials=trial + 1, accepted=False)
         # move the label density toward the target range
-        temp = min(1.0, temp + 0.04) if verdict == "sparse" else max(-1.0, temp - 0.04)
-        last = verdict
+        temp = min(1.0, temp + 0.04) if outcome == "sparse" else max(-1.0, temp - 0.04)
+        last = outcome
     if best is None:                     # nothing countable: keep the last draw, uncounted
         best = dict(index=i, nv=nv, kind=kind, edges=edges, elabels=el, vlabels=vl,
                     first_batch_new=-1, trials=max_trials, accepted=False)
