@@ -444,7 +444,7 @@ def main():
         line["batched_uneven"] = {k: extra[k] for k in (
             "value", "unit", "ms_per_step", "config", "plain", "learned_vs_plain", "latency_ms",
             "embeddings_per_step", "stage_ms_per_step", "work_per_step", "roofline", "tuning", "train",
-            "clocks", "filtered", "presplit_gain", "model_roofline")}
+            "clocks", "filtered", "presplit_gain", "model_roofline", "filter_trial")}
         line["gpu_launches"] += extra["gpu_launches"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         W, B = main_wl["window"], main_wl["batch"]
@@ -588,6 +588,7 @@ def run_workload(args, ctx, wl, with_e2e):
                     g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
                     pos += B
                 res["autotune"] = g.autotune_results()
+                res["filter_trial"] = g.autotune_filter_result()
         else:
             for _ in range(skip):                                # same batches as the learned arm
                 g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
@@ -686,7 +687,7 @@ def run_workload(args, ctx, wl, with_e2e):
     peak, peak_kind = measured_peaks()
     stage_ms = {"enumerate": st["ms_enumerate"], "adjacency": st["ms_adjacency"],
                 "ingest": st["ms_ingest"], "seeds": st["ms_seeds"], "expire": st["ms_expire"],
-                "model": st["ms_model"]}
+                "model": st["ms_model"], "filter": st["ms_filter"]}
     # Algorithmic bytes of the enumerator (the method's traffic, counted from
     # the device work counters): per tested adjacency entry 8 B (neighbour,
     # seq) + 4 B DEBI word + 8 B timestamp when the query is temporal; per
@@ -788,6 +789,9 @@ def run_workload(args, ctx, wl, with_e2e):
             "work_per_step": {k: filtered["st"][k] / K for k in ("entries_scanned", "binds")}},
         "train": learned.get("train"),
         "tuning": {"plain": plain.get("tuning_used"), "learned": learned.get("tuning_used")},
+        # the autotuner's trial of the DEBI filtering on the learned arm (kept
+        # for the timed batches when it was faster per inserted edge)
+        "filter_trial": learned.get("filter_trial"),
         # the autotuner's live measurements (one batch per candidate, learned
         # order): the best configuration with and without learned pre-splitting
         "presplit_gain": presplit_gain(learned.get("autotune")),

@@ -346,10 +346,19 @@ mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries);
  * x split threshold {40, 64, 128} x split depth {3, any} x pre-split
  * threshold {off, 2^20, 2^22 cycles}, all without slice staging, plus split
  * threshold 40 at any depth with staging of ranges of at least {256, 1024}
- * entries (mn_set_slice_staging).  mn_autotune_state reports whether
- * tuning is still running and how many configurations are left. */
+ * entries (mn_set_slice_staging).  Then the DEBI filtering (mn_set_filtering)
+ * is tried the same way on live inserting batches: 3 with it off, then 3 with
+ * it on (its full pass to turn on is not timed), each timed from the filter
+ * pass to the end of the enumeration, and the filtering is kept when it is
+ * at least 3% faster per inserted edge (it removes seeds and candidates but
+ * costs a pass per batch, so which wins depends on the queries).  mn_autotune_state reports whether tuning is
+ * still running and how many of its batches are left; mn_autotune_filter_result
+ * gives the trial's times (ms per 1,000 inserted edges) and choice
+ * (MN_ERR_STATE before a trial has finished). */
 mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config);
-mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left);
+mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batches_left);
+mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off, double *ms_per_kedge_on,
+                                    int32_t *filtering_kept);
 
 /* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off;
  * slice_min = 0: no shared-memory staging, mn_set_slice_staging). */

@@ -94,7 +94,7 @@ struct Phase {
 struct PendingBatch {
     bool active = false;
     uint64_t id = 0, n = 0, x = 0, hi_new = 0;
-    bool count_only = false, tune_now = false;
+    bool count_only = false, tune_now = false, trial_now = false;
     int nph = 0;
     Phase ph[2] = {};
 };
@@ -183,6 +183,12 @@ struct mn_graph {
     std::vector<double> tune_ms, tune_work;
     uint32_t tune_per = 1, tune_idx = 0, tune_in = 0;
     cudaEvent_t tune_e0 = nullptr, tune_e1 = nullptr;
+    // the autotuner's filtering trial: batches with the DEBI filtering off
+    // (ftrial 1), then on (2); the faster per inserted edge is kept
+    int ftrial = 0;
+    uint32_t ft_left = 0, ft_per = 3;
+    double ft_ms[2] = {0.0, 0.0}, ft_edges[2] = {0.0, 0.0};
+    int ft_choice = -1;                 // -1: no trial has finished
     mn_stats stats{};
     bool timing = false;
     // learned matching order
@@ -1256,6 +1262,24 @@ void build_tune_candidates(mn_graph *g)
     for (uint32_t sl : {256u, 1024u}) g->tune_cfgs.push_back({b, 40u, (uint32_t)MN_MAX_QE, INFINITY, sl});
 }
 
+// Turn the DEBI filtering on: per-query sets built by one full pass over the
+// current graph (nothing may be pending).
+mn_status filter_enable(mn_graph *g)
+{
+    if (g->filter) return MN_OK;
+    TRY(filter_globals(g));
+    for (size_t q = 0; q < g->queries.size(); q++) TRY(filter_alloc(g, q));
+    g->filter = true;
+    // build every query's sets on the current graph; nothing is pending then
+    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
+    TRY(filter_pass(g, g->cur, g->merged_lo, g->hi, true));
+    CK(cudaMemsetAsync(g->d_dmap, 0, sizeof(uint32_t) * g->W32, g->stream));
+    CK(cudaMemsetAsync(g->d_ndirty, 0, sizeof(uint32_t), g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    g->filter_dirty = false;
+    return MN_OK;
+}
+
 }  // namespace
 
 // Complete the queued batch g->pending: wait for its enumeration, grow and
@@ -1266,7 +1290,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     const PendingBatch pd = g->pending;
     g->pending.active = false;
     const uint64_t n = pd.n, x = pd.x, hi_new = pd.hi_new;
-    const bool count_only = pd.count_only, tune_now = pd.tune_now;
+    const bool count_only = pd.count_only, tune_now = pd.tune_now, trial_now = pd.trial_now;
     const int nph = pd.nph;
     const Phase *ph = pd.ph;
     bool over_budget = false;
@@ -1289,6 +1313,32 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
                 g->presplit_log2 = c.presplit_log2;
                 g->slice_min = c.slice_min;
                 g->tuning = false;
+                // then the filtering trial: first with the filtering off
+                g->ftrial = 1;
+                g->ft_left = g->ft_per;
+                g->ft_ms[0] = g->ft_ms[1] = g->ft_edges[0] = g->ft_edges[1] = 0.0;
+                g->filter = false;
+            }
+        }
+    }
+    int ft_switch = 0;                       // after the commit: 1 turn the filtering on, -1 off
+    if (trial_now && est == MN_OK) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
+        g->ft_ms[g->ftrial - 1] += ms;
+        g->ft_edges[g->ftrial - 1] += (double)n;
+        if (--g->ft_left == 0) {
+            if (g->ftrial == 1) {
+                g->ftrial = 2;
+                g->ft_left = g->ft_per;
+                ft_switch = 1;
+            } else {
+                // kept only when clearly faster: the dirty-vertex marking at
+                // insertion and expiry is outside the timed span
+                const bool on = g->ft_ms[1] / g->ft_edges[1] < 0.97 * (g->ft_ms[0] / g->ft_edges[0]);
+                g->ft_choice = on ? 1 : 0;
+                g->ftrial = 0;
+                if (!on) ft_switch = -1;
             }
         }
     }
@@ -1322,6 +1372,8 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     g->batch_id++;
     g->stats.batches++;
     if (!count_only && est == MN_OK) note_rates(g, n, x);
+    if (ft_switch > 0) TRY(filter_enable(g));
+    if (ft_switch < 0) g->filter = false;
     fill_result(g, out, seq_lo, hi_new, ex_lo, ex_lo + x);
     if (est == MN_ERR_TIMEOUT) return fail(g, MN_ERR_TIMEOUT, timeout_msg);
     if (over_budget) return fail(g, MN_ERR_OUTPUT_OVERFLOW, "result lists truncated at mem_budget_bytes");
@@ -1599,7 +1651,8 @@ mn_status mn_register_query(mn_graph *g, const mn_query_desc *d, uint32_t *query
 // CUDA graph (nothing here may then allocate or wait: the callers size every
 // buffer first).
 static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_t flags, uint64_t hi_new,
-                             uint64_t *x_io, Phase *ph, int *nph_out, bool count_only, bool tune_now)
+                             uint64_t *x_io, Phase *ph, int *nph_out, bool count_only, bool tune_now,
+                             bool trial_now = false)
 {
     uint64_t x = *x_io;
     CK(cudaMemsetAsync(g->d_ctrl, 0, sizeof(Ctrl), g->stream));
@@ -1648,6 +1701,8 @@ static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint
             x = g->h_ctrl->time_cut;
         }
     }
+    // the filtering trial times the filter pass with the enumeration
+    if (trial_now) CK(cudaEventRecord(g->tune_e0, g->stream));
     // DEBI filtering on G1 (the new adjacency, the expiring edges still visible)
     if (n) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
     if (tune_now) CK(cudaEventRecord(g->tune_e0, g->stream));
@@ -1673,7 +1728,7 @@ static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint
     if (nph && !count_only) TRY(presize_outputs(g, n, x));
     if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
     for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
-    if (tune_now) CK(cudaEventRecord(g->tune_e1, g->stream));
+    if (tune_now || trial_now) CK(cudaEventRecord(g->tune_e1, g->stream));
     *x_io = x;
     *nph_out = nph;
     return MN_OK;
@@ -1707,6 +1762,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
     // autotuning: run this batch's enumeration under the next candidate
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
+    const bool trial_now = !tune_now && g->ftrial && !g->queries.empty() && n;
     if (tune_now) {
         const auto &c = g->tune_cfgs[g->tune_idx];
         g->enum_grid = g->nsm * (int)c.bps;
@@ -1717,7 +1773,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     }
     Phase ph[2];
     int nph = 0;
-    if (graph_eligible(g, edges, n, flags, tune_now)) {
+    if (graph_eligible(g, edges, n, flags, tune_now || trial_now)) {
         // size everything the chain would grow, then record it
         if (!g->queries.empty()) {
             uint64_t total_ne = 0;
@@ -1764,7 +1820,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         CK(cudaGraphLaunch(g->gexec, g->stream));
         g->stats.graph_launches++;
     } else {
-        TRY(queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, tune_now));
+        TRY(queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, tune_now, trial_now));
     }
     PendingBatch &pd = g->pending;
     pd.active = true;
@@ -1774,6 +1830,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     pd.hi_new = hi_new;
     pd.count_only = count_only;
     pd.tune_now = tune_now;
+    pd.trial_now = trial_now;
     pd.nph = nph;
     for (int k = 0; k < nph; k++) pd.ph[k] = ph[k];
     if (flags & MN_ASYNC) {
@@ -2146,19 +2203,9 @@ mn_status mn_set_filtering(mn_graph *g, int32_t enable)
         g->filter = false;
         return MN_OK;
     }
-    if (g->filter) return MN_OK;
-    TRY(filter_globals(g));
-    for (size_t q = 0; q < g->queries.size(); q++) TRY(filter_alloc(g, q));
-    g->filter = true;
-    // build every query's sets on the current graph; nothing is pending then
-    CK(cudaMemsetAsync(&g->d_ctrl->status, 0, sizeof(uint32_t), g->stream));
-    TRY(filter_pass(g, g->cur, g->merged_lo, g->hi, true));
-    CK(cudaMemsetAsync(g->d_dmap, 0, sizeof(uint32_t) * g->W32, g->stream));
-    CK(cudaMemsetAsync(g->d_ndirty, 0, sizeof(uint32_t), g->stream));
-    CK(cudaStreamSynchronize(g->stream));
-    g->filter_dirty = false;
-    return MN_OK;
+    return filter_enable(g);
 }
+
 
 mn_status mn_read_filter(mn_graph *g, uint32_t query_id, uint32_t *td, uint32_t *bu, int32_t *root,
                          int32_t *parent, int32_t *tree_edge)
@@ -2537,11 +2584,31 @@ mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries)
     return MN_OK;
 }
 
-mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *configs_left)
+mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batches_left)
 {
     if (!g) return MN_ERR_INVALID_ARG;
-    if (active) *active = g->tuning ? 1 : 0;
-    if (configs_left) *configs_left = g->tuning ? (uint32_t)(g->tune_cfgs.size() - g->tune_idx) : 0u;
+    if (active) *active = (g->tuning || g->ftrial) ? 1 : 0;
+    if (batches_left) {
+        uint64_t left = 0;
+        if (g->tuning)
+            left = (uint64_t)(g->tune_cfgs.size() - g->tune_idx) * g->tune_per - g->tune_in + 2ull * g->ft_per;
+        else if (g->ftrial == 1)
+            left = g->ft_left + g->ft_per;
+        else if (g->ftrial == 2)
+            left = g->ft_left;
+        *batches_left = (uint32_t)left;
+    }
+    return MN_OK;
+}
+
+mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off, double *ms_per_kedge_on,
+                                    int32_t *filtering_kept)
+{
+    if (!g) return MN_ERR_INVALID_ARG;
+    if (g->ft_choice < 0) return MN_ERR_STATE;
+    if (ms_per_kedge_off) *ms_per_kedge_off = 1e3 * g->ft_ms[0] / std::max(g->ft_edges[0], 1.0);
+    if (ms_per_kedge_on) *ms_per_kedge_on = 1e3 * g->ft_ms[1] / std::max(g->ft_edges[1], 1.0);
+    if (filtering_kept) *filtering_kept = g->ft_choice;
     return MN_OK;
 }
 

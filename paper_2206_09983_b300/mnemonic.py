@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmnemonic.so")
 
 MN_OK = 0
+MN_ERR_STATE = -9
 STATUS_NAMES = {
     -1: "MN_ERR_INVALID_ARG", -2: "MN_ERR_INVALID_VERTEX", -3: "MN_ERR_TS_ORDER",
     -4: "MN_ERR_OOM", -5: "MN_ERR_ADMISSION", -6: "MN_ERR_OUTPUT_OVERFLOW",
@@ -45,7 +46,7 @@ EXPORTS = [
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
     "mn_set_graph_capture", "mn_set_spill", "mn_read_spill", "mn_set_slice_staging",
-    "mn_get_slice_staging", "mn_last_error",
+    "mn_get_slice_staging", "mn_autotune_filter_result", "mn_last_error",
 ]
 MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
@@ -172,6 +173,8 @@ def load(path: str | None = None):
         "mn_read_filter": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_int32), P, P]),
         "mn_get_presplit": (S, [P, C.POINTER(C.c_float)]),
         "mn_set_slice_staging": (S, [P, C.c_uint32]),
+        "mn_autotune_filter_result": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int32)]),
         "mn_get_slice_staging": (S, [P, C.POINTER(C.c_uint32)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_autotune_results": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
@@ -556,6 +559,16 @@ class Graph:
         self._check(self._lib.mn_autotune_results(self._h, n.value, arr, C.byref(n)))
         return [(r.config.blocks_per_sm, r.config.split_min, r.config.split_depth, r.config.presplit_log2,
                  r.config.slice_min, r.enumerate_ms, r.work) for r in arr[:n.value]]
+
+    def autotune_filter_result(self):
+        """The autotuner's filtering trial: ms per 1,000 inserted edges with the
+        filtering off and on, and whether it was kept; None before a trial."""
+        off, on, kept = C.c_double(), C.c_double(), C.c_int32()
+        st = self._lib.mn_autotune_filter_result(self._h, C.byref(off), C.byref(on), C.byref(kept))
+        if st == MN_ERR_STATE:
+            return None
+        self._check(st)
+        return {"ms_per_kedge_off": off.value, "ms_per_kedge_on": on.value, "filtering_kept": bool(kept.value)}
 
     def autotune_state(self):
         a, left = C.c_int32(), C.c_uint32()

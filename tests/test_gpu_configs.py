@@ -126,8 +126,10 @@ def test_learned_presplit_is_exact_and_splits():
 
 
 def test_online_autotuner_batches_are_exact():
-    """Each batch of the tuning walk runs under another candidate; every one
-    of them (and the batches after the choice) equals the oracle."""
+    """Each batch of the tuning walk runs under another candidate, then the
+    filtering trial runs batches with the DEBI filtering off and on; every
+    one of them (and the batches after the choice) equals the oracle, and the
+    trial keeps the filtering only when it is at least 3% faster."""
     s, qs = split_stream(), split_queries()
     with fresh(s, qs) as g:
         g.set_order_policy("explore")
@@ -137,17 +139,23 @@ def test_online_autotuner_batches_are_exact():
         g.train_order_model(epochs=100, lr=2e-3)
         g.set_order_policy("learned")
         n = len(g.autotune_candidates())
+        assert g.autotune_filter_result() is None
         g.autotune(1)
         active, left = g.autotune_state()
-        assert active and left == n
+        assert active and left == n + 6              # the candidates, then 3 + 3 filtering-trial batches
         g.reset_stats()
         k = 3
-        while k < 3 + n + 2:
+        while k < 3 + left + 2:
             r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
             check(g, s, qs, k, r, "autotune")
+            assert g.autotune_state()[1] == max(0, left - (k - 2))
             k += 1
         assert not g.autotune_state()[0]
         assert g.stats()["tasks_split"] > 0
+        ft = g.autotune_filter_result()
+        assert ft is not None and ft["ms_per_kedge_off"] > 0 and ft["ms_per_kedge_on"] > 0
+        assert ft["filtering_kept"] == (ft["ms_per_kedge_on"] < 0.97 * ft["ms_per_kedge_off"])
+        assert g.stats()["seeds_filtered"] > 0         # the trial's filtered batches pruned seeds
 
 
 def test_multi_label_vertices_subset_masks():
