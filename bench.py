@@ -237,7 +237,7 @@ def run_serve(args, local):
     W, MB = w["window"], w["max_batch"]
     levels = [0.5, 0.8, 0.95]
     per_level = args.serve_edges
-    n_total = W + 3 * (1 << 16) + (1 + len(levels)) * per_level
+    n_total = W + (3 + 40) * (1 << 16) + (1 + len(levels)) * per_level    # warm-up, tuning, levels
     assert n_total <= w["num_edges"], "serve run longer than the stream"
     t0 = time.perf_counter()
     stream = workloads.flow_prefix(n_total)
@@ -256,9 +256,19 @@ def run_serve(args, local):
     for _ in range(3):                                             # warm-up
         g.insert(packed[pos:pos + (1 << 16)])
         pos += 1 << 16
+    tune = None
     if args.serve_order == "learned":
         g.train_order_model(epochs=args.train_epochs, lr=2e-3)
         g.set_order_policy("learned")
+        # the learned + batched form: online autotuning of the launch and of
+        # the filtering on live 65,536-edge batches before serving
+        g.autotune(1)
+        nt = 0
+        while g.autotune_state()[0] and nt < 40:
+            g.insert(packed[pos:pos + (1 << 16)])
+            pos += 1 << 16
+            nt += 1
+        tune = {"batches": nt, "tuning": g.get_tuning(), "filter_trial": g.autotune_filter_result()}
     rng = np.random.default_rng(0x5E4E)
     rec_bytes = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
 
@@ -296,7 +306,7 @@ def run_serve(args, local):
         dev = {"batches": len(ten.batches), "mean_edges": float(np.mean([b[0] for b in ten.batches])),
                "insert_ms": {"mean": float(ins.mean()), "p50": float(np.percentile(ins, 50)),
                              "p99": float(np.percentile(ins, 99))},
-               "stage_ms_per_batch": {k: st["ms_" + k] / nb for k in ("ingest", "adjacency", "seeds",
+               "stage_ms_per_batch": {k: st["ms_" + k] / nb for k in ("ingest", "adjacency", "seeds", "filter",
                                                                       "enumerate", "expire")},
                "rerun_launches": st["rerun_launches"]}
         return {"offered_edges_per_s": rate, "value": n_edges / (t_end - t_start), "requests": len(reqs),
@@ -309,9 +319,11 @@ def run_serve(args, local):
     out = {"mode": "serve", "metric": METRIC, "unit": UNIT,
            "config": {"workload": w["name"], "hosts": w["hosts"], "window": W, "max_batch": MB,
                       "queries": len(qs), "arrivals": "Poisson, batch sizes log-uniform in [1024, 262144]",
-                      "path": (("learned matching order" if args.serve_order == "learned" else
+                      "path": (("learned matching order, autotuned launch and filtering"
+                                if args.serve_order == "learned" else
                                 "paper's matching order") + ", continuous batching (queued requests merged)"),
-                      "stream_generation_s": gen_s}}
+                      "stream_generation_s": gen_s},
+           "tuning": tune}
     mx, _, _ = one_level(None, per_level)
     out["max_sustained"] = mx
     out["levels"] = []
