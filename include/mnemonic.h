@@ -186,7 +186,8 @@ mn_status mn_delete_batch(mn_graph *g, const uint64_t *seqs, uint64_t n, uint32_
  * sorted fetch of a batch sorts it in place, with scratch of 8 B plus one
  * record per record, allocated for the sort and freed; later fetches of the
  * batch, sorted or not, return sorted records), ascending by the vertex ids
- * f(u_0), ..., f(u_{nv-1}) and then the edge seqs. */
+ * f(u_0), ..., f(u_{nv-1}) and then the edge seqs; MN_ERR_INVALID_ARG for a
+ * list above 2^32 records, MN_ERR_OOM if the scratch cannot be allocated. */
 mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id, int32_t sign,
                               uint64_t offset, uint64_t max_records, void *dst,
                               uint32_t dst_flags, uint64_t *n_written);

@@ -1941,6 +1941,8 @@ mn_status mn_fetch_embeddings(mn_graph *g, uint64_t batch_id, uint32_t query_id,
     const uint64_t cnt = std::min<uint64_t>(max_records, avail - offset);
     if (!dst) return fail(g, MN_ERR_INVALID_ARG, "dst is NULL");
     CK(cudaSetDevice(g->device));
+    if ((dst_flags & MN_FETCH_SORTED) && avail > 0xffffffffull)
+        return fail(g, MN_ERR_INVALID_ARG, "sorted fetch of a list above 2^32 records");
     if ((dst_flags & MN_FETCH_SORTED) && Q.sorted_batch[s] != batch_id && avail > 1) {
         // sort the whole list once for this batch, in place: runs of
         // MERGE_ITEMS sorted per thread, index merge passes, then one gather
