@@ -682,7 +682,7 @@ mn_status choose_orders(mn_graph *g, int phase)
         CKL();
         CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
         stage_begin(g);
-        k_mlp_forward_tc<<<2 * g->nsm, TC_M, TC_SMEM, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND, 0,
+        k_mlp_forward_tc<<<2 * g->nsm, TC_FWD_THREADS, TC_SMEM, g->stream>>>(g->d_X, &g->d_ctrl->nseeds[phase], NCAND, 0,
                                                                g->d_w1t, g->d_w2t, g->d_P, g->d_y,
                                                                &g->d_ctrl->status);
         CKL();
@@ -2740,7 +2740,7 @@ mn_status mn_mlp_forward(int32_t device, const float *params, const uint16_t *x,
         int nsm = 0;
         CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
         CK(cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-        k_mlp_forward_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), 2ull * nsm), TC_M, TC_SMEM>>>(
+        k_mlp_forward_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), 2ull * nsm), TC_FWD_THREADS, TC_SMEM>>>(
             (const __nv_bfloat16 *)X.p, nullptr, 1, (uint32_t)n, (const __nv_bfloat16 *)W1.p,
             (const __nv_bfloat16 *)W2.p, (const float *)P.p, (float *)Y.p, (uint32_t *)St.p);
         CK(cudaGetLastError());

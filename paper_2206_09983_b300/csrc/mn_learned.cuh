@@ -8,11 +8,12 @@
 //
 // Network: 16 features -> 128 -> 128 -> 1, ReLU, weights and activations in
 // BF16 with FP32 accumulation, FP32 master weights, mean squared error on
-// log2(1 + work), Adam (Kingma & Ba, 2015).  Inference (k_mlp_forward_tc) and
-// the gradient (k_mlp_grad_tc) run on the 5th-generation tensor cores:
-// tcgen05.mma from shared-memory operand tiles into TMEM accumulators.  Training data are logged by the enumerator itself:
-// per seed the SM cycles spent on it (summed over the seed's own unit and
-// every subtree split off from it).
+// log2(1 + work), Adam (Kingma & Ba, 2015).  Inference (k_mlp_forward_tc)
+// and the gradient (k_mlp_grad_tc) run on the 5th-generation tensor cores:
+// tcgen05.mma from shared-memory operand tiles into TMEM accumulators.
+// Training data are logged by the enumerator itself: per seed the SM cycles
+// spent on it (summed over the seed's own unit and every subtree split off
+// from it).
 #pragma once
 #include <cuda_bf16.h>
 #include "mn_device.cuh"
@@ -208,19 +209,25 @@ constexpr uint32_t TC_B2 = TC_B1 + NH * NF * 2;        // W2^T as B: N = 128 x K
 constexpr uint32_t TC_A1 = TC_B2 + NH * NH * 2;        // X tile: M = 128 x K = 16
 constexpr uint32_t TC_A2 = TC_A1 + TC_M * NF * 2;      // bf16(relu(layer 1)): M = 128 x K = 128
 constexpr uint32_t TC_VEC = TC_A2 + TC_M * NH * 2;     // b1, b2, w3 (FP32)
-constexpr uint32_t TC_BAR = TC_VEC + 3 * NH * 4;       // mbarrier, TMEM base address
+constexpr uint32_t TC_SUM = TC_VEC + 3 * NH * 4;       // the second column half's output sums
+constexpr uint32_t TC_BAR = TC_SUM + TC_M * 4;         // mbarrier, TMEM base address
 constexpr uint32_t TC_SMEM = TC_BAR + 16;
 constexpr uint32_t TC_TMEM_COLS = 2 * NH;              // layer 1 in columns [0, 128), layer 2 in [128, 256)
 constexpr uint32_t TC_WAIT_POLLS = 1u << 24;
+
+constexpr uint32_t TC_FWD_THREADS = 2 * TC_M;     // two warpgroups: column halves of each row
 
 // y[r] = w3 . relu(W2^T bf16(relu(W1^T x_r + b1)) + b2) + b3 for rows r < n
 // (n read from *n_dev times `per`, or n_host when n_dev is NULL); 128 rows
 // per tile, tiles strided over the grid (launched with two blocks per SM:
 // each holds 256 of the SM's 512 TMEM columns, so one block's epilogue runs
-// while the other's MMAs do).  *status gets ST_TIMEOUT if an MMA completion was
-// not seen within the wait bound (every thread still runs every tile, so the
-// block's barriers stay matched).
-__global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
+// while the other's MMAs do).  Two warpgroups share the epilogues: warp w
+// reads TMEM lanes 32 (w mod 4) .. + 31 (its rows), warpgroup 0 the columns
+// 0-63 of each accumulator and warpgroup 1 the columns 64-127; the output
+// dot product adds the two halves through shared memory.  *status gets
+// ST_TIMEOUT if an MMA completion was not seen within the wait bound (every
+// thread still runs every tile, so the block's barriers stay matched).
+__global__ void __launch_bounds__(TC_FWD_THREADS, 2) k_mlp_forward_tc(
     const __nv_bfloat16 *__restrict__ X, const uint32_t *n_dev, uint32_t per, uint32_t n_host,
     const __nv_bfloat16 *__restrict__ w1t, const __nv_bfloat16 *__restrict__ w2t,
     const float *__restrict__ P, float *__restrict__ y, uint32_t *status)
@@ -229,21 +236,23 @@ __global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
     float *vb1 = reinterpret_cast<float *>(tcs + TC_VEC), *vb2 = vb1 + NH, *vw3 = vb2 + NH;
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(tcs + TC_BAR);
     uint32_t *tbase = reinterpret_cast<uint32_t *>(tcs + TC_BAR + 8);
+    float *half_sum = reinterpret_cast<float *>(tcs + TC_SUM);
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t row = tid & (TC_M - 1), wg = tid / TC_M;   // this thread's tile row and column half
     const uint32_t n = n_dev ? *n_dev * per : n_host;
     if (blockIdx.x * TC_M >= n) return;                // the whole block leaves together
     // weights as B operands: w1t[h][f], w2t[o][h] are N x K row-major
-    for (uint32_t c = tid; c < NH * NF / 8; c += TC_M) {
+    for (uint32_t c = tid; c < NH * NF / 8; c += TC_FWD_THREADS) {
         const uint32_t r = c / (NF / 8), kc = c % (NF / 8);
         *reinterpret_cast<uint4 *>(tcs + TC_B1 + cm_off(r, kc * 8, NF)) =
             reinterpret_cast<const uint4 *>(w1t)[c];
     }
-    for (uint32_t c = tid; c < NH * NH / 8; c += TC_M) {
+    for (uint32_t c = tid; c < NH * NH / 8; c += TC_FWD_THREADS) {
         const uint32_t r = c / (NH / 8), kc = c % (NH / 8);
         *reinterpret_cast<uint4 *>(tcs + TC_B2 + cm_off(r, kc * 8, NH)) =
             reinterpret_cast<const uint4 *>(w2t)[c];
     }
-    for (uint32_t i = tid; i < NH; i += TC_M) {
+    for (uint32_t i = tid; i < NH; i += TC_FWD_THREADS) {
         vb1[i] = P[P_B1 + i];
         vb2[i] = P[P_B2 + i];
         vw3[i] = P[P_W3 + i];
@@ -262,7 +271,8 @@ __global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = *tbase;
-    const uint32_t lane_addr = tm + ((warp * 32u) << 16);   // this warp's TMEM lanes
+    const uint32_t lane_addr = tm + (((warp & 3u) * 32u) << 16);   // this warp's TMEM lanes
+    const uint32_t c0 = wg * (NH / 2);                 // this warpgroup's first column
     const uint32_t sbase = smem_u32(tcs);
     constexpr uint32_t IDESC = umma_idesc_bf16(TC_M, NH);
     uint32_t phase = 0;
@@ -278,7 +288,7 @@ __global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
     };
     for (uint32_t rb = blockIdx.x * TC_M; rb < n; rb += gridDim.x * TC_M) {   // same trip count in every thread
         // X tile (rows past n are zero)
-        for (uint32_t c = tid; c < TC_M * NF / 8; c += TC_M) {
+        for (uint32_t c = tid; c < TC_M * NF / 8; c += TC_FWD_THREADS) {
             const uint32_t r = c / (NF / 8), kc = c % (NF / 8);
             uint4 v = make_uint4(0, 0, 0, 0);
             if (rb + r < n) v = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * (NF / 8) + kc];
@@ -294,22 +304,23 @@ __global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
             umma_commit(bar);
         }
         wait_mma();
-        // layer-1 epilogue: row tid, bias, ReLU, BF16 -> A operand of layer 2
+        // layer-1 epilogue: bias, ReLU, BF16 -> A operand of layer 2
 #pragma unroll
-        for (uint32_t cc = 0; cc < NH / 32; cc++) {
+        for (uint32_t cc = 0; cc < NH / 64; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + cc * 32, v);
+            tmem_ld32(lane_addr + col, v);
 #pragma unroll
             for (uint32_t q = 0; q < 4; q++) {
                 uint4 pk;
                 uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
                 for (uint32_t e = 0; e < 4; e++) {
-                    const uint32_t h = cc * 32 + q * 8 + 2 * e;
+                    const uint32_t h = col + q * 8 + 2 * e;
                     pw[e] = pack_bf16(fmaxf(v[q * 8 + 2 * e] + vb1[h], 0.f),
                                       fmaxf(v[q * 8 + 2 * e + 1] + vb1[h + 1], 0.f));
                 }
-                *reinterpret_cast<uint4 *>(tcs + TC_A2 + cm_off(tid, cc * 32 + q * 8, NH)) = pk;
+                *reinterpret_cast<uint4 *>(tcs + TC_A2 + cm_off(row, col + q * 8, NH)) = pk;
             }
         }
         fence_proxy_async_smem();
@@ -324,19 +335,21 @@ __global__ void __launch_bounds__(TC_M, 2) k_mlp_forward_tc(
             umma_commit(bar);
         }
         wait_mma();
-        // layer-2 epilogue: bias, ReLU, dot with w3
-        float acc = b3;
+        // layer-2 epilogue: bias, ReLU, dot with w3 over this half's columns
+        float acc = 0.f;
 #pragma unroll
-        for (uint32_t cc = 0; cc < NH / 32; cc++) {
+        for (uint32_t cc = 0; cc < NH / 64; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + NH + cc * 32, v);
+            tmem_ld32(lane_addr + NH + col, v);
 #pragma unroll
-            for (uint32_t j = 0; j < 32; j++) acc += fmaxf(v[j] + vb2[cc * 32 + j], 0.f) * vw3[cc * 32 + j];
+            for (uint32_t j = 0; j < 32; j++) acc += fmaxf(v[j] + vb2[col + j], 0.f) * vw3[col + j];
         }
-        if (rb + tid < n) y[rb + tid] = acc;
+        if (wg == 1) half_sum[row] = acc;
         tc_fence_before();
         __syncthreads();                                 // the tiles and TMEM are free again
         tc_fence_after();
+        if (wg == 0 && rb + row < n) y[rb + row] = b3 + acc + half_sum[row];
     }
     if (stuck) atomicOr(status, ST_TIMEOUT);
     tc_fence_before();
