@@ -2307,7 +2307,7 @@ mn_status mn_train_order_model(mn_graph *g, uint32_t epochs, float lr, float *lo
     for (uint32_t e = 0; e <= epochs; e++) {
         CK(cudaMemsetAsync(g->d_G, 0, sizeof(float) * P_COUNT, g->stream));
         CK(cudaMemsetAsync(g->d_loss, 0, sizeof(float), g->stream));
-        k_mlp_grad_tc<<<grid, TC_M, TG_SMEM, g->stream>>>(g->d_SX, g->d_ST, n, g->d_P, g->d_G, g->d_loss,
+        k_mlp_grad_tc<<<grid, TG_THREADS, TG_SMEM, g->stream>>>(g->d_SX, g->d_ST, n, g->d_P, g->d_G, g->d_loss,
                                                          g->d_train_status);
         CKL();
         if (e == 0 || e == epochs) {
@@ -2779,7 +2779,7 @@ mn_status mn_mlp_gradient(int32_t device, const float *params, const uint16_t *x
     int nsm = 0;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device));
     if (n) {
-        k_mlp_grad_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)nsm), TC_M, TG_SMEM>>>(
+        k_mlp_grad_tc<<<(uint32_t)std::min<uint64_t>(cdiv(n, TC_M), (uint64_t)nsm), TG_THREADS, TG_SMEM>>>(
             (const __nv_bfloat16 *)X.p, (const float *)T.p, (uint32_t)n, (const float *)P.p, (float *)G.p,
             (float *)L.p, (uint32_t *)St.p);
         CK(cudaGetLastError());

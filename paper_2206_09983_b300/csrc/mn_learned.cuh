@@ -400,45 +400,54 @@ constexpr uint32_t TG_A2 = TG_BX + NF * TC_M * 2;      // h1 [r][h], then dZ2 [r
 constexpr uint32_t TG_A3 = TG_A2 + TC_M * NH * 2;      // h1^T [h][r], then dZ1^T [h][r]
 constexpr uint32_t TG_BD = TG_A3 + NH * TC_M * 2;      // dZ2^T as B: N = 128 (o) x K = 128 (r)
 constexpr uint32_t TG_VEC = TG_BD + NH * TC_M * 2;     // b1, b2, w3 (FP32)
-constexpr uint32_t TG_BAR = TG_VEC + 3 * NH * 4;       // mbarrier, TMEM base address
+constexpr uint32_t TG_XCH = TG_VEC + 3 * NH * 4;       // per row: second half's output sum, dy
+constexpr uint32_t TG_BAR = TG_XCH + 2 * TC_M * 4;     // mbarrier, TMEM base address
 constexpr uint32_t TG_SMEM = TG_BAR + 16;
 // TMEM columns: z1 then dH1 [0, 128), z2 [128, 256), dW2 [256, 384), dW1^T [384, 400)
 constexpr uint32_t TG_TMEM_COLS = 512;
 static_assert(TG_SMEM <= 227u * 1024u, "training tiles exceed shared memory");
+
+constexpr uint32_t TG_THREADS = 2 * TC_M;         // two warpgroups: column halves of each row
 
 // Gradient of the mean squared error over rows [0, n) (same BF16 roundings
 // as inference: weights and layer-1 activations; straight-through), 128 rows
 // per tile on the tensor cores: forward z1 = X W1, z2 = h1 W2; backward
 // dW2 = h1^T dZ2, dH1 = dZ2 W2^T, dW1 = X^T dZ1 with dZ2 and dZ1 rounded to
 // BF16 as MMA operands (FP32 accumulation in TMEM across the block's tiles);
-// the bias and w3 gradients and the loss are FP32 column sums.  Adds to G[]
-// and *loss; *status gets ST_TIMEOUT if an MMA completion was not seen
-// within the wait bound.  At most one block per SM (512 TMEM columns).
-__global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
+// the bias and w3 gradients and the loss are FP32 column sums.  Two
+// warpgroups share every epilogue: warp w reads the TMEM lanes of warp
+// w mod 4 (its rows), warpgroup 0 the columns 0-63 and warpgroup 1 the
+// columns 64-127 of each accumulator.  Adds to G[] and *loss; *status gets
+// ST_TIMEOUT if an MMA completion was not seen within the wait bound.  At
+// most one block per SM (512 TMEM columns).
+__global__ void __launch_bounds__(TG_THREADS, 1) k_mlp_grad_tc(
     const __nv_bfloat16 *__restrict__ X, const float *__restrict__ T, uint32_t n,
     const float *__restrict__ P, float *__restrict__ G, float *__restrict__ loss, uint32_t *status)
 {
     extern __shared__ __align__(1024) uint8_t tgs[];
     float *vb1 = reinterpret_cast<float *>(tgs + TG_VEC), *vb2 = vb1 + NH, *vw3 = vb2 + NH;
+    float *xch = reinterpret_cast<float *>(tgs + TG_XCH);       // per row: the other half's sum, then dy
     unsigned long long *bar = reinterpret_cast<unsigned long long *>(tgs + TG_BAR);
     uint32_t *tbase = reinterpret_cast<uint32_t *>(tgs + TG_BAR + 8);
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t r = tid & (TC_M - 1), wg = tid / TC_M;       // this thread's tile row and column half
+    const uint32_t c0 = wg * (NH / 2);
     if (blockIdx.x * TC_M >= n) return;                // the whole block leaves together
     auto st_bf16 = [&](uint32_t off, float v) {
         *reinterpret_cast<__nv_bfloat16 *>(tgs + off) = __float2bfloat16_rn(v);
     };
     // weights, rounded to BF16, as B operands
-    for (uint32_t i = tid; i < NF * NH; i += TC_M) {         // (h, f) = W1[f][h]
+    for (uint32_t i = tid; i < NF * NH; i += TG_THREADS) {   // (h, f) = W1[f][h]
         const uint32_t h = i / NF, f = i % NF;
         st_bf16(TG_B1 + cm_off(h, f, NF), P[P_W1 + f * NH + h]);
     }
-    for (uint32_t i = tid; i < NH * NH; i += TC_M) {         // W2[a][b]
+    for (uint32_t i = tid; i < NH * NH; i += TG_THREADS) {   // W2[a][b]
         const uint32_t a = i / NH, b = i % NH;
         const float w = P[P_W2 + i];
         st_bf16(TG_B2 + cm_off(b, a, NH), w);                  // (o, h) = W2[h][o]
         st_bf16(TG_BW + cm_off(a, b, NH), w);                  // (h, o) = W2[h][o]
     }
-    for (uint32_t i = tid; i < NH; i += TC_M) {
+    for (uint32_t i = tid; i < NH; i += TG_THREADS) {
         vb1[i] = P[P_B1 + i];
         vb2[i] = P[P_B2 + i];
         vw3[i] = P[P_W3 + i];
@@ -458,7 +467,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
     __syncthreads();
     tc_fence_after();
     const uint32_t tm = *tbase;
-    const uint32_t lane_addr = tm + ((warp * 32u) << 16);
+    const uint32_t lane_addr = tm + (((warp & 3u) * 32u) << 16);
     const uint32_t sb = smem_u32(tgs);
     constexpr uint32_t ID_128 = umma_idesc_bf16(TC_M, NH), ID_16 = umma_idesc_bf16(TC_M, NF);
     constexpr uint32_t SBO16 = NF / 8 * 128, SBO128 = NH / 8 * 128;
@@ -479,28 +488,21 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
         __syncthreads();
         tc_fence_after();
     };
-    float acc_b1[4] = {0.f, 0.f, 0.f, 0.f}, acc_b2[4] = {0.f, 0.f, 0.f, 0.f}, acc_w3[4] = {0.f, 0.f, 0.f, 0.f};
+    // column sums, lane j of a warp: columns c0 + 32 cc + j of its rows
+    float acc_b1[2] = {0.f, 0.f}, acc_b2[2] = {0.f, 0.f}, acc_w3[2] = {0.f, 0.f};
     float acc_loss = 0.f, acc_b3 = 0.f;
     uint32_t first = 1;
     for (uint32_t rb = blockIdx.x * TC_M; rb < n; rb += gridDim.x * TC_M) {   // same trip count in every thread
-        const uint32_t r = tid;                          // this thread's row of the tile
         const bool valid = rb + r < n;
-        // X tile as A (rows) and as B (transposed)
+        // X tile as A (rows) and as B (transposed): warpgroup wg moves features 8 wg .. 8 wg + 7
         {
-            uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
-            if (valid) {
-                v0 = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * 2];
-                v1 = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * 2 + 1];
-            }
-            *reinterpret_cast<uint4 *>(tgs + TG_A1 + cm_off(r, 0, NF)) = v0;
-            *reinterpret_cast<uint4 *>(tgs + TG_A1 + cm_off(r, 8, NF)) = v1;
-            const __nv_bfloat16 *e0 = reinterpret_cast<const __nv_bfloat16 *>(&v0);
-            const __nv_bfloat16 *e1 = reinterpret_cast<const __nv_bfloat16 *>(&v1);
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (valid) v = reinterpret_cast<const uint4 *>(X)[(size_t)(rb + r) * 2 + wg];
+            *reinterpret_cast<uint4 *>(tgs + TG_A1 + cm_off(r, wg * 8, NF)) = v;
+            const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
 #pragma unroll
-            for (uint32_t f = 0; f < 8; f++) {
-                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BX + cm_off(f, r, TC_M)) = e0[f];
-                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BX + cm_off(f + 8, r, TC_M)) = e1[f];
-            }
+            for (uint32_t f = 0; f < 8; f++)
+                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BX + cm_off(wg * 8 + f, r, TC_M)) = e[f];
         }
         const float tgt = valid ? T[rb + r] : 0.f;
         sync_for_mma();
@@ -510,11 +512,12 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
         }
         wait_mma();
         // h1 = bf16(relu(z1 + b1)) -> A2 [r][h] and A3 [h][r]; keep its sign mask
-        uint32_t m1[4];
+        uint32_t m1[2];
 #pragma unroll
-        for (uint32_t cc = 0; cc < 4; cc++) {
+        for (uint32_t cc = 0; cc < 2; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + cc * 32, v);
+            tmem_ld32(lane_addr + col, v);
             m1[cc] = 0;
 #pragma unroll
             for (uint32_t q = 0; q < 4; q++) {
@@ -522,7 +525,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
                 uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
                 for (uint32_t e = 0; e < 4; e++) {
-                    const uint32_t j = q * 8 + 2 * e, h = cc * 32 + j;
+                    const uint32_t j = q * 8 + 2 * e, h = col + j;
                     const __nv_bfloat162 hb = __floats2bfloat162_rn(fmaxf(v[j] + vb1[h], 0.f),
                                                                     fmaxf(v[j + 1] + vb1[h + 1], 0.f));
                     pw[e] = *reinterpret_cast<const uint32_t *>(&hb);
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
                     *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(h, r, TC_M)) = hb.x;
                     *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(h + 1, r, TC_M)) = hb.y;
                 }
-                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, cc * 32 + q * 8, NH)) = pk;
+                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, col + q * 8, NH)) = pk;
             }
         }
         sync_for_mma();
@@ -543,27 +546,37 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
             umma_commit(bar);
         }
         wait_mma();
-        // output, error and dy (rows past n contribute nothing)
-        float yv = b3;
+        // output: this half's share of w3 . relu(z2 + b2), the halves added
+        // through shared memory; error and dy (rows past n contribute nothing)
+        float yv = 0.f;
 #pragma unroll
-        for (uint32_t cc = 0; cc < 4; cc++) {
+        for (uint32_t cc = 0; cc < 2; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + NH + cc * 32, v);
+            tmem_ld32(lane_addr + NH + col, v);
 #pragma unroll
-            for (uint32_t j = 0; j < 32; j++) yv += fmaxf(v[j] + vb2[cc * 32 + j], 0.f) * vw3[cc * 32 + j];
+            for (uint32_t j = 0; j < 32; j++) yv += fmaxf(v[j] + vb2[col + j], 0.f) * vw3[col + j];
         }
-        const float err = valid ? yv - tgt : 0.f;
-        const float dy = 2.f * err * inv_n;
-        acc_loss += err * err;
-        acc_b3 += dy;
+        if (wg == 1) xch[r] = yv;
+        __syncthreads();
+        if (wg == 0) {
+            const float err = valid ? b3 + yv + xch[r] - tgt : 0.f;
+            const float d = 2.f * err * inv_n;
+            acc_loss += err * err;
+            acc_b3 += d;
+            xch[TC_M + r] = d;
+        }
+        __syncthreads();
+        const float dy = xch[TC_M + r];
         // dZ2 = dy w3 [z2 + b2 > 0] -> A2 [r][o] (BF16) and BD [o][r]; w3 and b2 column sums
 #pragma unroll
-        for (uint32_t cc = 0; cc < 4; cc++) {
+        for (uint32_t cc = 0; cc < 2; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32], gw[32];
-            tmem_ld32(lane_addr + NH + cc * 32, v);
+            tmem_ld32(lane_addr + NH + col, v);
 #pragma unroll
             for (uint32_t j = 0; j < 32; j++) {
-                const uint32_t o = cc * 32 + j;
+                const uint32_t o = col + j;
                 const float z = v[j] + vb2[o];
                 gw[j] = z > 0.f ? dy * z : 0.f;
                 v[j] = z > 0.f ? dy * vw3[o] : 0.f;
@@ -574,13 +587,13 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
                 uint32_t *pw = reinterpret_cast<uint32_t *>(&pk);
 #pragma unroll
                 for (uint32_t e = 0; e < 4; e++) {
-                    const uint32_t j = q * 8 + 2 * e, o = cc * 32 + j;
+                    const uint32_t j = q * 8 + 2 * e, o = col + j;
                     const __nv_bfloat162 db = __floats2bfloat162_rn(v[j], v[j + 1]);
                     pw[e] = *reinterpret_cast<const uint32_t *>(&db);
                     *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BD + cm_off(o, r, TC_M)) = db.x;
                     *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_BD + cm_off(o + 1, r, TC_M)) = db.y;
                 }
-                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, cc * 32 + q * 8, NH)) = pk;
+                *reinterpret_cast<uint4 *>(tgs + TG_A2 + cm_off(r, col + q * 8, NH)) = pk;
             }
             acc_w3[cc] += warp_column_sums(gw, lane);
             acc_b2[cc] += warp_column_sums(v, lane);
@@ -600,13 +613,14 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
         wait_mma();
         // dZ1 = dH1 [h1 > 0] -> A3 [h][r] (BF16); b1 column sums
 #pragma unroll
-        for (uint32_t cc = 0; cc < 4; cc++) {
+        for (uint32_t cc = 0; cc < 2; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + cc * 32, v);
+            tmem_ld32(lane_addr + col, v);
 #pragma unroll
             for (uint32_t j = 0; j < 32; j++) {
                 v[j] = (m1[cc] >> j) & 1u ? v[j] : 0.f;
-                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(cc * 32 + j, r, TC_M)) =
+                *reinterpret_cast<__nv_bfloat16 *>(tgs + TG_A3 + cm_off(col + j, r, TC_M)) =
                     __float2bfloat16_rn(v[j]);
             }
             acc_b1[cc] += warp_column_sums(v, lane);
@@ -627,33 +641,38 @@ __global__ void __launch_bounds__(TC_M, 1) k_mlp_grad_tc(
     }
     // dW2[h][o] is TMEM lane h, column 256 + o; dW1[f][h] lane h, column 384 + f
     {
-        const uint32_t h = tid;
+        const uint32_t h = r;
 #pragma unroll
-        for (uint32_t cc = 0; cc < 4; cc++) {
+        for (uint32_t cc = 0; cc < 2; cc++) {
+            const uint32_t col = c0 + cc * 32;
             float v[32];
-            tmem_ld32(lane_addr + 2 * NH + cc * 32, v);
+            tmem_ld32(lane_addr + 2 * NH + col, v);
 #pragma unroll
-            for (uint32_t j = 0; j < 32; j++) atomicAdd(&G[P_W2 + h * NH + cc * 32 + j], v[j]);
+            for (uint32_t j = 0; j < 32; j++) atomicAdd(&G[P_W2 + h * NH + col + j], v[j]);
         }
-        float w[16];
-        tmem_ld16(lane_addr + 3 * NH, w);
+        if (wg == 0) {
+            float w[16];
+            tmem_ld16(lane_addr + 3 * NH, w);
 #pragma unroll
-        for (uint32_t f = 0; f < NF; f++) atomicAdd(&G[P_W1 + f * NH + h], w[f]);
+            for (uint32_t f = 0; f < NF; f++) atomicAdd(&G[P_W1 + f * NH + h], w[f]);
+        }
     }
 #pragma unroll
-    for (uint32_t cc = 0; cc < 4; cc++) {                // lane j of each warp: column 32 cc + j
-        atomicAdd(&G[P_B1 + cc * 32 + lane], acc_b1[cc]);
-        atomicAdd(&G[P_B2 + cc * 32 + lane], acc_b2[cc]);
-        atomicAdd(&G[P_W3 + cc * 32 + lane], acc_w3[cc]);
+    for (uint32_t cc = 0; cc < 2; cc++) {                // lane j: column c0 + 32 cc + j
+        atomicAdd(&G[P_B1 + c0 + cc * 32 + lane], acc_b1[cc]);
+        atomicAdd(&G[P_B2 + c0 + cc * 32 + lane], acc_b2[cc]);
+        atomicAdd(&G[P_W3 + c0 + cc * 32 + lane], acc_w3[cc]);
     }
+    if (wg == 0) {
 #pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) {
-        acc_loss += __shfl_xor_sync(FULL, acc_loss, d);
-        acc_b3 += __shfl_xor_sync(FULL, acc_b3, d);
-    }
-    if (lane == 0) {
-        atomicAdd(loss, acc_loss * inv_n);
-        atomicAdd(&G[P_B3], acc_b3);
+        for (int d = 16; d >= 1; d >>= 1) {
+            acc_loss += __shfl_xor_sync(FULL, acc_loss, d);
+            acc_b3 += __shfl_xor_sync(FULL, acc_b3, d);
+        }
+        if (lane == 0) {
+            atomicAdd(loss, acc_loss * inv_n);
+            atomicAdd(&G[P_B3], acc_b3);
+        }
     }
     if (stuck) atomicOr(status, ST_TIMEOUT);
     tc_fence_before();
