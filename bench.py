@@ -201,8 +201,11 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": w["name"], "vertices": 1 << w["scale"], "window": W, "batch": B,
-                   "queries": workloads.QUERY_NAMES},
+        "config": {"workload": w["name"], "vertices": 1 << w["scale"], "edges": w["num_edges"],
+                   "window": W, "batch": B, "queries": list(workloads.QUERY_NAMES),
+                   "semantics": "isomorphism, increasing timestamps",
+                   "parallelism": f"host CPU, {threads} OpenMP threads",
+                   "path": "CPU oracle: seed DFS over sampled inserted edges of every timed batch"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{sample} random inserted edges per batch (|dS+| of all 4 queries, "
                                    f"seeds over {threads} OpenMP threads, adjacency rebuild included), "
