@@ -307,3 +307,33 @@ def test_sorted_fetch_is_the_oracle_order_without_host_sorting():
                 v3, s3 = g.fetch(qi, sign)            # the list stays sorted for this batch
                 assert (np.concatenate([v3.astype(np.uint64), s3], axis=1) == want).all()
         assert max(len(oracle.delta(s, 0, 8000, 5000, 8000, q)) for q in qs) > 100000
+
+
+def test_maximum_query_size():
+    """Queries at the maximum size -- a directed 16-cycle (16 vertices, 16
+    edges) under isomorphism and a 15-edge path (16 vertices) under
+    homomorphism, one vertex label per query vertex -- over a sliding window:
+    every batch's dS+ and dS- equal the oracle's."""
+    s = gen.uniform_stream(200, 20000, 16, 4, seed=0x4D4E00D0)
+    labels = [i % 4 for i in range(16)]
+    vm = [1 << i for i in range(16)]
+    qs = [gen.q_cycle(16, labels=labels, vmask=vm, iso=True),
+          gen.q_path(15, labels=labels[:15], vmask=vm, iso=False)]
+    assert all(q["nv"] == M.MN_MAX_QV for q in qs) and len(qs[0]["edges"]) == M.MN_MAX_QE
+    W, B = 14000, 3000
+    found = 0
+    with make_graph(s, window=W, max_batch=W) as g:
+        g.insert(M.edges_from_stream(s, 0, W), count_only=True)
+        for q in qs:
+            g.register_query(q)
+        for lo_b in (W, W + B):
+            r = g.insert(M.edges_from_stream(s, lo_b, lo_b + B))
+            lo = lo_b - W                        # G1 = [lo, lo_b + B); [lo, lo + B) expires
+            for qi, q in enumerate(qs):
+                pos = oracle.delta(s, lo, lo_b + B, lo_b, lo_b + B, q)
+                neg = oracle.delta(s, lo, lo_b + B, lo, lo + B, q)
+                assert r.count_pos[qi] == len(pos) and r.count_neg[qi] == len(neg), (lo_b, qi)
+                assert_rows_equal(g.fetch_rows(qi, +1), pos, f"max-size q{qi} dS+ at {lo_b}")
+                assert_rows_equal(g.fetch_rows(qi, -1), neg, f"max-size q{qi} dS- at {lo_b}")
+                found += len(pos) + len(neg)
+    assert found > 1000
