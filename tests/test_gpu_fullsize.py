@@ -2,8 +2,12 @@
 window 2^22 edges, batches of 65,536), for both benchmark workloads -- the
 four calibrated queries (rmat20_window) and the 36 batched uneven queries
 (rmat20_uneven: 32 random trees and chorded cycles plus the four) -- in the
-same launch configuration as bench.py (device-resident batches, count-only
-preload, queries registered on the full window).
+launch configurations bench.py times (device-resident batches, count-only
+preload, queries registered on the full window): the plain path (paper
+order, default launch), and the learned arm (orders picked by the work
+model trained on three explore batches, the launch parameters and
+pre-splitting the autotuner keeps on these workloads, and on the uneven
+workload the DEBI filtering it keeps there).
 
 The oracle cannot list a whole batch quickly, so per batch and query:
 * sampled exactness: for a seeded sample of the batch's edges, the GPU records
@@ -26,17 +30,26 @@ pytestmark = pytest.mark.gpu
 _STREAM = {}
 
 
-@pytest.fixture(scope="module", params=["rmat20_window", "rmat20_uneven"])
+# the autotuner's choices on these workloads (blocks per SM at the limit,
+# split threshold, split depth; pre-split threshold; filtering)
+LEARNED = {"rmat20_window": ((0, 40, 3), 22.0, False), "rmat20_uneven": ((0, 128, 16), 22.0, True)}
+
+
+@pytest.fixture(scope="module", params=[("rmat20_window", "plain"), ("rmat20_uneven", "plain"),
+                                        ("rmat20_window", "learned"), ("rmat20_uneven", "learned")],
+                ids=lambda p: f"{p[0]}-{p[1]}")
 def run(request):
     import torch
     from paper_2206_09983_b300 import build
     build.build()
-    wl = workloads.WORKLOADS[request.param]
+    name, mode = request.param
+    wl = workloads.WORKLOADS[name]
     W, B = wl["window"], wl["batch"]
     if "s" not in _STREAM:
         _STREAM["s"] = workloads.rmat20_stream()
     s = _STREAM["s"]
-    packed = M.edges_from_stream(s, 0, W + 2 * B)
+    skip = 3 if mode == "learned" else 0
+    packed = M.edges_from_stream(s, 0, W + (skip + 2) * B)
     d = torch.from_numpy(packed.view(np.uint8)).cuda()
     qs = wl["queries"]()
     g = M.Graph(s["num_vertices"], s["num_edge_labels"], vmask=s["vmask"], window=W, max_batch=B,
@@ -45,12 +58,22 @@ def run(request):
     for lo in range(0, W, B):
         g.insert(None, device_ptr=d.data_ptr() + 24 * lo, n=B, count_only=True)
     qids = [g.register_query(q) for q in qs]
+    if mode == "learned":
+        g.set_order_policy("explore")
+        for k in range(skip):
+            g.insert(None, device_ptr=d.data_ptr() + 24 * (W + k * B), n=B)
+        g.train_order_model(epochs=300, lr=2e-3)
+        g.set_order_policy("learned")
+        tuning, presplit, filtering = LEARNED[name]
+        g.set_tuning(*tuning)
+        g.set_presplit(presplit)
+        g.set_filtering(filtering)
     out = []
-    for k in range(2):
+    for k in range(skip, skip + 2):
         hi = W + k * B
         r = g.insert(None, device_ptr=d.data_ptr() + 24 * hi, n=B)
         rows = {(qi, sg): g.fetch_rows(qi, sg) for qi in qids for sg in (+1, -1)}
-        out.append((k * B, hi, hi + B, r, rows))
+        out.append((hi - W, hi, hi + B, r, rows))
     g.close()
     return s, qs, out
 
