@@ -201,6 +201,9 @@ struct mn_graph {
     __nv_bfloat16 *d_X = nullptr;        // features, seed_cap x NCAND rows
     float *d_y = nullptr;
     unsigned long long *d_seed_work = nullptr;
+    unsigned long long *d_picked = nullptr;  // picked seed words before the heaviest-first scatter
+    uint8_t *d_bucket = nullptr;             // their cost buckets
+    uint32_t *d_pick_hist = nullptr;         // PICK_BUCKETS sizes, then PICK_BUCKETS cursors
     uint64_t learn_rows = 0;             // capacity of d_X / d_y / d_seed_work (rows)
     __nv_bfloat16 *d_SX = nullptr;       // training ring
     float *d_ST = nullptr;
@@ -626,11 +629,17 @@ mn_status ensure_learn_rows(mn_graph *g, uint64_t seeds)
     dfree(g, g->d_X, old * NF * sizeof(__nv_bfloat16));
     dfree(g, g->d_y, old * sizeof(float));
     dfree(g, g->d_seed_work, 2 * (old / NCAND) * sizeof(unsigned long long));
+    dfree(g, g->d_picked, (old / NCAND) * sizeof(unsigned long long));
+    dfree(g, g->d_bucket, old / NCAND);
     g->d_X = nullptr; g->d_y = nullptr; g->d_seed_work = nullptr; g->learn_rows = 0;
+    g->d_picked = nullptr; g->d_bucket = nullptr;
     const uint64_t cap = next_pow2(rows);
     TRY(dalloc(g, &g->d_X, cap * NF, false));
     TRY(dalloc(g, &g->d_y, cap, false));
     TRY(dalloc(g, &g->d_seed_work, 2 * (cap / NCAND), false));     // one half per phase
+    TRY(dalloc(g, &g->d_picked, cap / NCAND, false));
+    TRY(dalloc(g, &g->d_bucket, cap / NCAND, false));
+    if (!g->d_pick_hist) TRY(dalloc(g, &g->d_pick_hist, 2 * PICK_BUCKETS, false));
     g->learn_rows = cap;
     return MN_OK;
 }
@@ -688,8 +697,14 @@ mn_status choose_orders(mn_graph *g, int phase)
         CKL();
         stage_end(g, S_MODEL);
         g->stats.model_launches++;
+        CK(cudaMemsetAsync(g->d_pick_hist, 0, 2 * PICK_BUCKETS * sizeof(uint32_t), g->stream));
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
-                                            1.0f, g->presplit_log2);
+                                            1.0f, g->presplit_log2, g->d_picked, g->d_bucket,
+                                            g->d_pick_hist);
+        CKL();
+        k_seed_order<<<grid, 256, 0, g->stream>>>(g->d_picked, g->d_bucket, &g->d_ctrl->nseeds[phase], cap,
+                                                  g->d_pick_hist, g->d_pick_hist + PICK_BUCKETS,
+                                                  g->d_seeds[phase]);
         CKL();
     }
     if (g->policy == MN_ORDER_EXPLORE)

@@ -698,14 +698,32 @@ __global__ void k_adam(float *P, const float *G, float *M1, float *M2, int n, fl
 
 // ------------------------------------------------------------------ order choice
 
+// Seeds are enumerated heaviest predicted first (longest processing time
+// first): the launch's tail then holds light seeds, not a late hub whose
+// subtree the idle warps must wait to be split off.  The order is by buckets
+// of half a log2 unit of predicted cost; bucket 0 holds the heaviest.
+constexpr uint32_t PICK_BUCKETS = 64;
+
+__device__ __forceinline__ uint32_t cost_bucket(float log2_cycles)
+{
+    const float h = fminf(fmaxf(2.f * log2_cycles, 0.f), (float)(PICK_BUCKETS - 1));
+    return PICK_BUCKETS - 1 - (uint32_t)h;
+}
+
 // Per seed: the candidate order with the smallest predicted cost, but the
 // paper's order (candidate 0) unless the best prediction beats it by at least
 // `margin` (log2 units): the paper's order is the fallback.  A seed whose
 // predicted cost under the chosen order is at least `split_log2` is flagged
-// for pre-splitting (SEED_PRESPLIT; split_log2 = +inf: never).
-__global__ void k_pick(unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
-                       const float *y, float margin, float split_log2)
+// for pre-splitting (SEED_PRESPLIT; split_log2 = +inf: never).  The picked
+// seed words go to `picked`, their cost buckets to `bucket`, and `hist`
+// (PICK_BUCKETS counters, zeroed by the caller) counts each bucket.
+__global__ void k_pick(const unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
+                       const float *y, float margin, float split_log2, unsigned long long *picked,
+                       uint8_t *bucket, uint32_t *hist)
 {
+    __shared__ uint32_t sh[PICK_BUCKETS];
+    for (uint32_t i = threadIdx.x; i < PICK_BUCKETS; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     const uint32_t n = min(*nseeds, seed_cap);
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         uint32_t best = 0;
@@ -718,7 +736,51 @@ __global__ void k_pick(unsigned long long *seeds, const uint32_t *nseeds, uint32
         if (bv > y0 - margin) { best = 0; bv = y0; }
         unsigned long long w = (seeds[s] & ~(0xffull << 24)) | ((unsigned long long)best << 24);
         if (bv >= split_log2) w |= SEED_PRESPLIT;
-        seeds[s] = w;
+        picked[s] = w;
+        const uint32_t b = cost_bucket(bv);
+        bucket[s] = (uint8_t)b;
+        atomicAdd(&sh[b], 1u);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < PICK_BUCKETS; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Scatter the picked seeds into `seeds` by bucket, bucket 0 first (a counting
+// sort; the order inside a bucket is arbitrary).  `cursor`: PICK_BUCKETS
+// counters zeroed by the caller.  The positions taken in bucket b total
+// hist[b], so every write lands in [0, n).  blockDim.x >= 32.
+__global__ void k_seed_order(const unsigned long long *picked, const uint8_t *bucket, const uint32_t *nseeds,
+                             uint32_t seed_cap, const uint32_t *hist, uint32_t *cursor,
+                             unsigned long long *seeds)
+{
+    __shared__ uint32_t base[PICK_BUCKETS], cnt[PICK_BUCKETS], res[PICK_BUCKETS];
+    static_assert(PICK_BUCKETS == 64, "two buckets per lane of one warp");
+    if (threadIdx.x < 32) {                 // exclusive prefix of the bucket sizes
+        const uint32_t b0 = 2 * threadIdx.x, v0 = hist[b0], v1 = hist[b0 + 1];
+        uint32_t inc = v0 + v1;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(FULL, inc, o);
+            if ((int)threadIdx.x >= o) inc += u;
+        }
+        base[b0] = inc - v0 - v1;
+        base[b0 + 1] = inc - v1;
+    }
+    const uint32_t n = min(*nseeds, seed_cap);
+    const uint32_t step = gridDim.x * blockDim.x;
+    for (uint32_t t0 = blockIdx.x * blockDim.x; t0 < n; t0 += step) {     // uniform over the block
+        for (uint32_t i = threadIdx.x; i < PICK_BUCKETS; i += blockDim.x) cnt[i] = 0;
+        __syncthreads();
+        const uint32_t s = t0 + threadIdx.x;
+        const bool in = s < n;
+        const uint32_t b = in ? bucket[s] : 0u;
+        const uint32_t r = in ? atomicAdd(&cnt[b], 1u) : 0u;
+        __syncthreads();
+        for (uint32_t i = threadIdx.x; i < PICK_BUCKETS; i += blockDim.x)
+            res[i] = cnt[i] ? atomicAdd(&cursor[i], cnt[i]) : 0u;
+        __syncthreads();
+        if (in) seeds[base[b] + res[b] + r] = picked[s];
+        __syncthreads();
     }
 }
 
