@@ -240,7 +240,7 @@ def run_serve(args, local):
     W, MB = w["window"], w["max_batch"]
     levels = [0.5, 0.8, 0.95]
     per_level = args.serve_edges
-    n_total = W + (3 + 40) * (1 << 16) + (1 + len(levels)) * per_level    # warm-up, tuning, levels
+    n_total = W + (3 + 60) * (1 << 16) + (1 + len(levels)) * per_level    # warm-up, tuning, levels
     assert n_total <= w["num_edges"], "serve run longer than the stream"
     t0 = time.perf_counter()
     stream = workloads.flow_prefix(n_total)
@@ -267,11 +267,12 @@ def run_serve(args, local):
         # the filtering on live 65,536-edge batches before serving
         g.autotune(1)
         nt = 0
-        while g.autotune_state()[0] and nt < 40:
+        while g.autotune_state()[0] and nt < 60:
             g.insert(packed[pos:pos + (1 << 16)])
             pos += 1 << 16
             nt += 1
-        tune = {"batches": nt, "tuning": g.get_tuning(), "filter_trial": g.autotune_filter_result()}
+        tune = {"batches": nt, "tuning": g.get_tuning(), "filter_trial": g.autotune_filter_result(),
+                "margin_trial": g.autotune_margin_result()}
     rng = np.random.default_rng(0x5E4E)
     rec_bytes = [(4 * q["nv"] + 7) // 8 * 8 + 8 * len(q["edges"]) for q in qs]
 
@@ -459,7 +460,7 @@ def main():
         line["batched_uneven"] = {k: extra[k] for k in (
             "value", "unit", "ms_per_step", "config", "plain", "learned_vs_plain", "latency_ms",
             "embeddings_per_step", "stage_ms_per_step", "work_per_step", "roofline", "tuning", "train",
-            "clocks", "filtered", "presplit_gain", "model_roofline", "filter_trial")}
+            "clocks", "filtered", "presplit_gain", "model_roofline", "filter_trial", "margin_trial")}
         line["gpu_launches"] += extra["gpu_launches"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         W, B = main_wl["window"], main_wl["batch"]
@@ -604,6 +605,7 @@ def run_workload(args, ctx, wl, with_e2e):
                     pos += B
                 res["autotune"] = g.autotune_results()
                 res["filter_trial"] = g.autotune_filter_result()
+                res["margin_trial"] = g.autotune_margin_result()
         else:
             for _ in range(skip):                                # same batches as the learned arm
                 g.insert(None, device_ptr=base_ptr + 24 * pos, n=B)
@@ -807,6 +809,9 @@ def run_workload(args, ctx, wl, with_e2e):
         # the autotuner's trial of the DEBI filtering on the learned arm (kept
         # for the timed batches when it was faster per inserted edge)
         "filter_trial": learned.get("filter_trial"),
+        # the autotuner's trial of the learned order's margin (log2 units by
+        # which a pick must beat the paper's order), run first
+        "margin_trial": learned.get("margin_trial"),
         # the autotuner's live measurements (one batch per candidate, learned
         # order): the best configuration with and without learned pre-splitting
         "presplit_gain": presplit_gain(learned.get("autotune")),

@@ -209,7 +209,8 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
 #define MN_ORDER_PAPER   0   /* always candidate 0 (default) */
 #define MN_ORDER_EXPLORE 1   /* a pseudo-random candidate per seed; per-seed SM cycles are logged for training */
 #define MN_ORDER_LEARNED 2   /* the candidate with the smallest predicted cost, if it beats the
-                                paper's order by at least 2x; otherwise the paper's order */
+                                paper's order by at least the margin (mn_set_order_margin;
+                                default 2x); otherwise the paper's order */
 
 #define MN_MLP_FEATURES 16
 /* FP32 parameter block of the work model, in this order: W1[16][128],
@@ -338,7 +339,8 @@ mn_status mn_get_presplit(const mn_graph *g, float *log2_cycles);
 mn_status mn_set_slice_staging(mn_graph *g, uint32_t min_entries);
 mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries);
 
-/* Online autotuning of the launch parameters above: each of the next
+/* Online autotuning of the launch parameters above (under MN_ORDER_LEARNED
+ * after the margin trial of mn_set_order_margin, below): each of the next
  * insert batches that enumerates runs under one candidate configuration,
  * `batches_per_config` batches each; then the configuration with the least
  * enumeration time per unit of work (adjacency entries tested + candidates
@@ -360,6 +362,28 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config);
 mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batches_left);
 mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off, double *ms_per_kedge_on,
                                     int32_t *filtering_kept);
+
+/* The learned order's margin, in log2 units of predicted cost (SM cycles):
+ * under MN_ORDER_LEARNED a seed leaves the paper's order (Sec. III
+ * preprocessing, the fallback) only for a candidate whose predicted cost is
+ * at least 2^margin times smaller.  Default 1 (2x); 0 trusts the model
+ * outright; a large margin keeps the paper's order.  MN_ERR_INVALID_ARG for
+ * a negative, infinite or NaN margin.  Results are unaffected; only the
+ * work changes.  How far the model's ranking can be trusted depends on the
+ * queries, so when mn_autotune starts under MN_ORDER_LEARNED it first runs a
+ * margin trial on live inserting batches: margins {0, 0.5, 1, 2, 3} in turn,
+ * two rounds (10 batches), each timed like a filtering-trial batch, and the
+ * margin with the least time per inserted edge is kept; the launch candidates
+ * and the filtering trial follow.  (Switching the policy away from learned
+ * before the trial ends skips it.)  mn_autotune_margin_result copies the
+ * candidate margins and their ms per 1,000 inserted edges to
+ * margins[0..*n) and ms_per_kedge[0..*n) (either may be NULL; *n gets the
+ * count, 5; MN_ERR_INVALID_ARG if cap is below it) and the kept margin to
+ * *kept (may be NULL); MN_ERR_STATE before a margin trial has finished. */
+mn_status mn_set_order_margin(mn_graph *g, float log2_margin);
+mn_status mn_get_order_margin(const mn_graph *g, float *log2_margin);
+mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
+                                    uint32_t *n, float *kept);
 
 /* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off;
  * slice_min = 0: no shared-memory staging, mn_set_slice_staging). */

@@ -91,10 +91,15 @@ struct Phase {
 };
 
 // A batch queued by mn_insert_batch with MN_ASYNC: what its completion needs.
+// the autotuner's candidate margins of the learned order (log2 units)
+constexpr uint32_t MT_N = 5, MT_ROUNDS = 2;
+constexpr float MT_CANDS[MT_N] = {0.f, 0.5f, 1.f, 2.f, 3.f};
+
 struct PendingBatch {
     bool active = false;
     uint64_t id = 0, n = 0, x = 0, hi_new = 0;
-    bool count_only = false, tune_now = false, trial_now = false;
+    bool count_only = false, tune_now = false, trial_now = false, margin_now = false;
+    uint32_t mt_k = 0;                  // margin_now: the candidate margin this batch ran under
     int nph = 0;
     Phase ph[2] = {};
 };
@@ -189,6 +194,15 @@ struct mn_graph {
     uint32_t ft_left = 0, ft_per = 3;
     double ft_ms[2] = {0.0, 0.0}, ft_edges[2] = {0.0, 0.0};
     int ft_choice = -1;                 // -1: no trial has finished
+    // the learned order's margin (log2 units of predicted cost by which the
+    // best candidate must beat the paper's order) and the autotuner's margin
+    // trial, run first under MN_ORDER_LEARNED: MT_ROUNDS rounds over the
+    // MT_N candidate margins, one live inserting batch each
+    float pick_margin = 1.0f;
+    int mtrial = 0;
+    uint32_t mt_idx = 0;
+    double mt_ms[MT_N] = {}, mt_edges[MT_N] = {};
+    int mt_choice = -1;                 // -1: no margin trial has finished
     mn_stats stats{};
     bool timing = false;
     // learned matching order
@@ -699,7 +713,7 @@ mn_status choose_orders(mn_graph *g, int phase)
         g->stats.model_launches++;
         CK(cudaMemsetAsync(g->d_pick_hist, 0, 2 * PICK_BUCKETS * sizeof(uint32_t), g->stream));
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
-                                            1.0f, g->presplit_log2, g->d_picked, g->d_bucket,
+                                            g->pick_margin, g->presplit_log2, g->d_picked, g->d_bucket,
                                             g->d_pick_hist);
         CKL();
         k_seed_order<<<grid, 256, 0, g->stream>>>(g->d_picked, g->d_bucket, &g->d_ctrl->nseeds[phase], cap,
@@ -1306,6 +1320,7 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     g->pending.active = false;
     const uint64_t n = pd.n, x = pd.x, hi_new = pd.hi_new;
     const bool count_only = pd.count_only, tune_now = pd.tune_now, trial_now = pd.trial_now;
+    const bool margin_now = pd.margin_now;
     const int nph = pd.nph;
     const Phase *ph = pd.ph;
     bool over_budget = false;
@@ -1334,6 +1349,21 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
                 g->ft_ms[0] = g->ft_ms[1] = g->ft_edges[0] = g->ft_edges[1] = 0.0;
                 g->filter = false;
             }
+        }
+    }
+    if (margin_now && est == MN_OK) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
+        g->mt_ms[pd.mt_k] += ms;
+        g->mt_edges[pd.mt_k] += (double)n;
+        if (++g->mt_idx >= MT_N * MT_ROUNDS) {     // keep the fastest per inserted edge
+            uint32_t best = 0;
+            for (uint32_t k = 1; k < MT_N; k++)
+                if (g->mt_ms[k] / g->mt_edges[k] < g->mt_ms[best] / g->mt_edges[best]) best = k;
+            g->pick_margin = MT_CANDS[best];
+            g->mt_choice = (int)best;
+            g->mtrial = 0;
+            g->tuning = true;                      // then the launch parameters
         }
     }
     int ft_switch = 0;                       // after the commit: 1 turn the filtering on, -1 off
@@ -1776,6 +1806,13 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     const uint64_t hi_new = g->hi + n;
     uint64_t x = (g->W && hi_new - g->lo > g->W) ? hi_new - g->lo - g->W : 0;
     // autotuning: run this batch's enumeration under the next candidate
+    if (g->mtrial && g->policy != MN_ORDER_LEARNED) {   // the margin acts only on learned orders
+        g->mtrial = 0;
+        g->tuning = true;
+    }
+    const bool margin_now = g->mtrial && !g->queries.empty() && n;
+    const uint32_t mt_k = g->mt_idx % MT_N;
+    if (margin_now) g->pick_margin = MT_CANDS[mt_k];
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
     const bool trial_now = !tune_now && g->ftrial && !g->queries.empty() && n;
     if (tune_now) {
@@ -1788,7 +1825,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     }
     Phase ph[2];
     int nph = 0;
-    if (graph_eligible(g, edges, n, flags, tune_now || trial_now)) {
+    if (graph_eligible(g, edges, n, flags, tune_now || trial_now || margin_now)) {
         // size everything the chain would grow, then record it
         if (!g->queries.empty()) {
             uint64_t total_ne = 0;
@@ -1835,7 +1872,8 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         CK(cudaGraphLaunch(g->gexec, g->stream));
         g->stats.graph_launches++;
     } else {
-        TRY(queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, tune_now, trial_now));
+        TRY(queue_batch(g, edges, n, flags, hi_new, &x, ph, &nph, count_only, tune_now,
+                        trial_now || margin_now));
     }
     PendingBatch &pd = g->pending;
     pd.active = true;
@@ -1846,6 +1884,8 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     pd.count_only = count_only;
     pd.tune_now = tune_now;
     pd.trial_now = trial_now;
+    pd.margin_now = margin_now;
+    pd.mt_k = mt_k;
     pd.nph = nph;
     for (int k = 0; k < nph; k++) pd.ph[k] = ph[k];
     if (flags & MN_ASYNC) {
@@ -2538,7 +2578,12 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     g->tune_per = std::max<uint32_t>(batches_per_config, 1);
     g->tune_idx = 0;
     g->tune_in = 0;
-    g->tuning = true;
+    // under learned orders the margin trial comes first, then the launch
+    g->mtrial = g->policy == MN_ORDER_LEARNED ? 1 : 0;
+    g->mt_idx = 0;
+    for (uint32_t k = 0; k < MT_N; k++) g->mt_ms[k] = g->mt_edges[k] = 0.0;
+    g->mt_choice = -1;
+    g->tuning = !g->mtrial;
     return MN_OK;
 }
 
@@ -2604,10 +2649,13 @@ mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries)
 mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batches_left)
 {
     if (!g) return MN_ERR_INVALID_ARG;
-    if (active) *active = (g->tuning || g->ftrial) ? 1 : 0;
+    if (active) *active = (g->mtrial || g->tuning || g->ftrial) ? 1 : 0;
     if (batches_left) {
         uint64_t left = 0;
-        if (g->tuning)
+        if (g->mtrial)
+            left = (uint64_t)(MT_N * MT_ROUNDS - g->mt_idx) + (uint64_t)g->tune_cfgs.size() * g->tune_per +
+                   2ull * g->ft_per;
+        else if (g->tuning)
             left = (uint64_t)(g->tune_cfgs.size() - g->tune_idx) * g->tune_per - g->tune_in + 2ull * g->ft_per;
         else if (g->ftrial == 1)
             left = g->ft_left + g->ft_per;
@@ -2626,6 +2674,37 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
     if (ms_per_kedge_off) *ms_per_kedge_off = 1e3 * g->ft_ms[0] / std::max(g->ft_edges[0], 1.0);
     if (ms_per_kedge_on) *ms_per_kedge_on = 1e3 * g->ft_ms[1] / std::max(g->ft_edges[1], 1.0);
     if (filtering_kept) *filtering_kept = g->ft_choice;
+    return MN_OK;
+}
+
+mn_status mn_set_order_margin(mn_graph *g, float log2_margin)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    if (!(log2_margin >= 0.f) || std::isinf(log2_margin))
+        return fail(g, MN_ERR_INVALID_ARG, "margin must be finite and >= 0");
+    g->pick_margin = log2_margin;
+    return MN_OK;
+}
+
+mn_status mn_get_order_margin(const mn_graph *g, float *log2_margin)
+{
+    if (!g || !log2_margin) return MN_ERR_INVALID_ARG;
+    *log2_margin = g->pick_margin;
+    return MN_OK;
+}
+
+mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
+                                    uint32_t *n, float *kept)
+{
+    if (!g || !n) return MN_ERR_INVALID_ARG;
+    *n = MT_N;
+    if (g->mt_choice < 0) return MN_ERR_STATE;
+    if ((margins || ms_per_kedge) && cap < MT_N) return MN_ERR_INVALID_ARG;
+    for (uint32_t k = 0; k < MT_N; k++) {
+        if (margins) margins[k] = MT_CANDS[k];
+        if (ms_per_kedge) ms_per_kedge[k] = g->mt_edges[k] > 0 ? 1e3 * g->mt_ms[k] / g->mt_edges[k] : 0.0;
+    }
+    if (kept) *kept = MT_CANDS[g->mt_choice];
     return MN_OK;
 }
 

@@ -46,7 +46,8 @@ EXPORTS = [
     "mn_dual_simulation", "mn_set_wait_limit", "mn_set_presplit", "mn_get_presplit",
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
     "mn_set_graph_capture", "mn_set_spill", "mn_read_spill", "mn_set_slice_staging",
-    "mn_get_slice_staging", "mn_autotune_filter_result", "mn_last_error",
+    "mn_get_slice_staging", "mn_autotune_filter_result", "mn_last_error", "mn_set_order_margin",
+    "mn_get_order_margin", "mn_autotune_margin_result",
 ]
 MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
@@ -176,6 +177,9 @@ def load(path: str | None = None):
         "mn_autotune_filter_result": (S, [P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_int32)]),
         "mn_get_slice_staging": (S, [P, C.POINTER(C.c_uint32)]),
+        "mn_set_order_margin": (S, [P, C.c_float]),
+        "mn_get_order_margin": (S, [P, C.POINTER(C.c_float)]),
+        "mn_autotune_margin_result": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_autotune_results": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_set_timing": (S, [P, C.c_int32]),
@@ -570,6 +574,29 @@ class Graph:
         self._check(st)
         return {"ms_per_kedge_off": off.value, "ms_per_kedge_on": on.value, "filtering_kept": bool(kept.value)}
 
+    def autotune_margin_result(self):
+        """The autotuner's margin trial of the learned order: the candidate
+        margins (log2 units), their ms per 1,000 inserted edges, and the margin
+        kept; None before a trial."""
+        n, kept = C.c_uint32(), C.c_float()
+        m = (C.c_float * 16)()
+        ms = (C.c_double * 16)()
+        st = self._lib.mn_autotune_margin_result(self._h, 16, m, ms, C.byref(n), C.byref(kept))
+        if st == MN_ERR_STATE:
+            return None
+        self._check(st)
+        return {"margins": list(m[:n.value]), "ms_per_kedge": list(ms[:n.value]), "kept": kept.value}
+
+    def set_order_margin(self, log2_margin: float):
+        """Margin (log2 units of predicted cost) by which a learned pick must
+        beat the paper's order (mn_set_order_margin)."""
+        self._check(self._lib.mn_set_order_margin(self._h, log2_margin))
+
+    def get_order_margin(self) -> float:
+        v = C.c_float()
+        self._check(self._lib.mn_get_order_margin(self._h, C.byref(v)))
+        return v.value
+
     def autotune_state(self):
         a, left = C.c_int32(), C.c_uint32()
         self._check(self._lib.mn_autotune_state(self._h, C.byref(a), C.byref(left)))
@@ -582,6 +609,7 @@ class Graph:
                       "smem_carveout"), [x.value for x in v]))
         d["presplit_log2"] = self.get_presplit()
         d["slice_min"] = self.get_slice_staging()
+        d["order_margin"] = self.get_order_margin()
         return d
 
     def reset_stats(self):

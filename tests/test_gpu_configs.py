@@ -32,10 +32,10 @@ def built():
 W, B = 8000, 2000
 
 
-def split_stream():
+def split_stream(batches=40):
     """R-MAT, 4,096 vertices, 4 edge labels: hub label slices of ~100-200
     entries (long enough to split) and 10^4-10^5 embeddings per batch."""
-    return gen.rmat_stream(12, W + 40 * B, 0.57, 0.19, 0.19, 4, 1.2, 2, 100, seed=0x4D4E0078)
+    return gen.rmat_stream(12, W + batches * B, 0.57, 0.19, 0.19, 4, 1.2, 2, 100, seed=0x4D4E0078)
 
 
 def split_queries():
@@ -48,12 +48,14 @@ _ORACLE = {}
 
 
 def expected(s, qs, k):
-    """Oracle dS+ / dS- of batch k (G1 = [k B, W + (k + 1) B))."""
-    if k not in _ORACLE:
+    """Oracle dS+ / dS- of batch k (G1 = [k B, W + (k + 1) B)); streams of
+    different lengths are different streams."""
+    key = (len(s["src"]), k)
+    if key not in _ORACLE:
         lo, hi = k * B, W + k * B
-        _ORACLE[k] = [(oracle.delta(s, lo, hi + B, hi, hi + B, q), oracle.delta(s, lo, hi + B, lo, lo + B, q))
+        _ORACLE[key] = [(oracle.delta(s, lo, hi + B, hi, hi + B, q), oracle.delta(s, lo, hi + B, lo, lo + B, q))
                       for q in qs]
-    return _ORACLE[k]
+    return _ORACLE[key]
 
 
 def check(g, s, qs, k, r, what):
@@ -126,11 +128,13 @@ def test_learned_presplit_is_exact_and_splits():
 
 
 def test_online_autotuner_batches_are_exact():
-    """Each batch of the tuning walk runs under another candidate, then the
-    filtering trial runs batches with the DEBI filtering off and on; every
-    one of them (and the batches after the choice) equals the oracle, and the
-    trial keeps the filtering only when it is at least 3% faster."""
-    s, qs = split_stream(), split_queries()
+    """Under learned orders the margin trial runs first (two rounds over the
+    five candidate margins), then each batch of the tuning walk runs under
+    another launch candidate, then the filtering trial runs batches with the
+    DEBI filtering off and on; every one of them (and the batches after the
+    choices) equals the oracle, the margin kept is the fastest per inserted
+    edge, and the filtering is kept only when it is at least 3% faster."""
+    s, qs = split_stream(56), split_queries()
     with fresh(s, qs) as g:
         g.set_order_policy("explore")
         for k in range(3):
@@ -139,10 +143,11 @@ def test_online_autotuner_batches_are_exact():
         g.train_order_model(epochs=100, lr=2e-3)
         g.set_order_policy("learned")
         n = len(g.autotune_candidates())
-        assert g.autotune_filter_result() is None
+        assert g.autotune_filter_result() is None and g.autotune_margin_result() is None
         g.autotune(1)
         active, left = g.autotune_state()
-        assert active and left == n + 6              # the candidates, then 3 + 3 filtering-trial batches
+        # 2 x 5 margin-trial batches, the candidates, then 3 + 3 filtering-trial batches
+        assert active and left == 10 + n + 6
         g.reset_stats()
         k = 3
         while k < 3 + left + 2:
@@ -155,7 +160,39 @@ def test_online_autotuner_batches_are_exact():
         ft = g.autotune_filter_result()
         assert ft is not None and ft["ms_per_kedge_off"] > 0 and ft["ms_per_kedge_on"] > 0
         assert ft["filtering_kept"] == (ft["ms_per_kedge_on"] < 0.97 * ft["ms_per_kedge_off"])
+        mt = g.autotune_margin_result()
+        assert mt is not None and mt["margins"] == [0.0, 0.5, 1.0, 2.0, 3.0]
+        assert all(v > 0 for v in mt["ms_per_kedge"])
+        assert mt["kept"] == mt["margins"][int(np.argmin(mt["ms_per_kedge"]))] == g.get_order_margin()
         assert g.stats()["seeds_filtered"] > 0         # the trial's filtered batches pruned seeds
+
+
+def test_order_margin_is_exact_and_checked():
+    """The learned order at margins 0 (the model trusted outright) and 3:
+    lists equal the oracle's; the margin changes the picks, so the work
+    differs; negative, infinite and NaN margins are refused."""
+    s, qs = split_stream(), split_queries()
+    with fresh(s, qs) as g:
+        assert g.get_order_margin() == 1.0
+        for bad in (-0.5, float("inf"), float("nan")):
+            with pytest.raises(M.MnError):
+                g.set_order_margin(bad)
+        g.set_order_policy("explore")
+        for k in range(3):
+            r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
+            check(g, s, qs, k, r, "explore")
+        g.train_order_model(epochs=100, lr=2e-3)
+        g.set_order_policy("learned")
+        work = []
+        for k, m in ((3, 0.0), (4, 3.0)):
+            g.set_order_margin(m)
+            assert g.get_order_margin() == m
+            g.reset_stats()
+            r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
+            check(g, s, qs, k, r, f"margin {m}")
+            st = g.stats()
+            work.append(st["entries_scanned"] + st["binds"])
+        assert work[0] != work[1]
 
 
 def test_multi_label_vertices_subset_masks():

@@ -5,9 +5,9 @@ four calibrated queries (rmat20_window) and the 36 batched uneven queries
 launch configurations bench.py times (device-resident batches, count-only
 preload, queries registered on the full window): the plain path (paper
 order, default launch), and the learned arm (orders picked by the work
-model trained on three explore batches, the launch parameters and
-pre-splitting the autotuner keeps on these workloads, and on the uneven
-workload the DEBI filtering it keeps there).
+model trained on three explore batches, with the order margin, the launch
+parameters and the pre-splitting the autotuner keeps on these workloads, and
+on the uneven workload the DEBI filtering it keeps there).
 
 The oracle cannot list a whole batch quickly, so per batch and query:
 * sampled exactness: for a seeded sample of the batch's edges, the GPU records
@@ -31,8 +31,9 @@ _STREAM = {}
 
 
 # the autotuner's choices on these workloads (blocks per SM at the limit,
-# split threshold, split depth; pre-split threshold; filtering)
-LEARNED = {"rmat20_window": ((0, 40, 3), 22.0, False), "rmat20_uneven": ((0, 128, 16), 22.0, True)}
+# split threshold, split depth; pre-split threshold, 0 = off; filtering;
+# margin of the learned order)
+LEARNED = {"rmat20_window": ((0, 40, 3), 22.0, False, 2.0), "rmat20_uneven": ((0, 64, 16), 0.0, True, 0.0)}
 
 
 @pytest.fixture(scope="module", params=[("rmat20_window", "plain"), ("rmat20_uneven", "plain"),
@@ -64,10 +65,11 @@ def run(request):
             g.insert(None, device_ptr=d.data_ptr() + 24 * (W + k * B), n=B)
         g.train_order_model(epochs=300, lr=2e-3)
         g.set_order_policy("learned")
-        tuning, presplit, filtering = LEARNED[name]
+        tuning, presplit, filtering, margin = LEARNED[name]
         g.set_tuning(*tuning)
         g.set_presplit(presplit)
         g.set_filtering(filtering)
+        g.set_order_margin(margin)
     out = []
     for k in range(skip, skip + 2):
         hi = W + k * B
