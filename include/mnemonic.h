@@ -209,8 +209,9 @@ mn_status mn_count_static(mn_graph *g, uint32_t query_id, uint64_t *count);
 #define MN_ORDER_PAPER   0   /* always candidate 0 (default) */
 #define MN_ORDER_EXPLORE 1   /* a pseudo-random candidate per seed; per-seed SM cycles are logged for training */
 #define MN_ORDER_LEARNED 2   /* the candidate with the smallest predicted cost, if it beats the
-                                paper's order by at least the margin (mn_set_order_margin;
-                                default 2x); otherwise the paper's order */
+                                paper's order by at least the query's margin
+                                (mn_set_order_margin; default 2x); otherwise the
+                                paper's order */
 
 #define MN_MLP_FEATURES 16
 /* FP32 parameter block of the work model, in this order: W1[16][128],
@@ -366,24 +367,37 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
 /* The learned order's margin, in log2 units of predicted cost (SM cycles):
  * under MN_ORDER_LEARNED a seed leaves the paper's order (Sec. III
  * preprocessing, the fallback) only for a candidate whose predicted cost is
- * at least 2^margin times smaller.  Default 1 (2x); 0 trusts the model
- * outright; a large margin keeps the paper's order.  MN_ERR_INVALID_ARG for
- * a negative, infinite or NaN margin.  Results are unaffected; only the
- * work changes.  How far the model's ranking can be trusted depends on the
- * queries, so when mn_autotune starts under MN_ORDER_LEARNED it first runs a
- * margin trial on live inserting batches: margins {0, 0.5, 1, 2, 3} in turn,
- * two rounds (10 batches), each timed like a filtering-trial batch, and the
- * margin with the least time per inserted edge is kept; the launch candidates
- * and the filtering trial follow.  (Switching the policy away from learned
- * before the trial ends skips it.)  mn_autotune_margin_result copies the
- * candidate margins and their ms per 1,000 inserted edges to
- * margins[0..*n) and ms_per_kedge[0..*n) (either may be NULL; *n gets the
- * count, 5; MN_ERR_INVALID_ARG if cap is below it) and the kept margin to
- * *kept (may be NULL); MN_ERR_STATE before a margin trial has finished. */
+ * at least 2^margin times smaller.  Each query has its own margin; the
+ * default for every query is 1 (2x).  0 trusts the model outright; a large
+ * margin keeps the paper's order.  Results are unaffected; only the work
+ * changes.  mn_set_order_margin sets every query's margin (also of queries
+ * registered later), mn_set_query_margin one registered query's
+ * (MN_ERR_INVALID_ARG for another id); both refuse a negative, infinite or
+ * NaN margin (MN_ERR_INVALID_ARG).  mn_get_order_margin reads a registered
+ * query's margin, or with query_id = MN_DEFAULT_MARGIN the one queries
+ * registered later get.
+ *
+ * How far the model's ranking can be trusted depends on the query, so when
+ * mn_autotune starts under MN_ORDER_LEARNED it first runs a margin trial on
+ * live inserting batches: margins {0, 0.5, 1, 2, 3} in turn for every query,
+ * two rounds (10 batches), each batch timed like a filtering-trial batch and
+ * the SM cycles of each query's work units logged.  Each registered query
+ * then keeps the margin under which its units took the fewest cycles per
+ * inserted edge, and the margin with the least time per inserted edge
+ * becomes the default for later queries; the launch candidates and the
+ * filtering trial follow.  (Switching the policy away from learned before the
+ * trial ends skips it.)  mn_autotune_margin_result gives, for candidate k <
+ * *n (= 5): margins[k], ms_per_kedge[k] (ms per 1,000 inserted edges) and,
+ * for registered query q, query_cycles_per_edge[q * cap + k]; any of the
+ * three may be NULL, and MN_ERR_INVALID_ARG if cap is below *n.  *kept (may
+ * be NULL) gets the default margin chosen.  MN_ERR_STATE before a margin
+ * trial has finished. */
+#define MN_DEFAULT_MARGIN 0xffffffffu
 mn_status mn_set_order_margin(mn_graph *g, float log2_margin);
-mn_status mn_get_order_margin(const mn_graph *g, float *log2_margin);
+mn_status mn_set_query_margin(mn_graph *g, uint32_t query_id, float log2_margin);
+mn_status mn_get_order_margin(const mn_graph *g, uint32_t query_id, float *log2_margin);
 mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
-                                    uint32_t *n, float *kept);
+                                    double *query_cycles_per_edge, uint32_t *n, float *kept);
 
 /* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off;
  * slice_min = 0: no shared-memory staging, mn_set_slice_staging). */

@@ -844,6 +844,7 @@ struct EnumParams {
                                         //  seeds whose endpoints the filtering excludes,
                                         //  entries read from staged windows]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
+    unsigned long long *q_cycles;       // optional: SM cycles spent per query (all its units)
     // optional second seed set, enumerated in the same launch after the first
     // (the other phase of the same batch): its seeds, avoid interval, sign and
     // work log; seeds1 == NULL: one set
@@ -1687,6 +1688,7 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
             w_busy += cyc;
             unsigned long long *sw_log = set ? p.seed_work1 : p.seed_work;
             if (sw_log) atomicAdd(&sw_log[sid], cyc);
+            if (p.q_cycles) atomicAdd(&p.q_cycles[q], cyc);
         }
         if (lane == 0) {
             __threadfence();

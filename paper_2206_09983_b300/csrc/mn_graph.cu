@@ -194,14 +194,23 @@ struct mn_graph {
     uint32_t ft_left = 0, ft_per = 3;
     double ft_ms[2] = {0.0, 0.0}, ft_edges[2] = {0.0, 0.0};
     int ft_choice = -1;                 // -1: no trial has finished
-    // the learned order's margin (log2 units of predicted cost by which the
-    // best candidate must beat the paper's order) and the autotuner's margin
-    // trial, run first under MN_ORDER_LEARNED: MT_ROUNDS rounds over the
-    // MT_N candidate margins, one live inserting batch each
+    // the learned order's margins (log2 units of predicted cost by which the
+    // best candidate must beat the paper's order): per query (q_margin,
+    // mirrored in d_qmargin), pick_margin for queries registered later.  The
+    // autotuner's margin trial, run first under MN_ORDER_LEARNED: MT_ROUNDS
+    // rounds over the MT_N candidate margins, one live inserting batch each,
+    // every query under the batch's candidate (trial_margin >= 0) and the SM
+    // cycles of each query's units logged (qcyc_on, d_qcyc)
     float pick_margin = 1.0f;
+    std::vector<float> q_margin;
+    float *d_qmargin = nullptr;
+    unsigned long long *d_qcyc = nullptr;
+    bool qcyc_on = false;
+    float trial_margin = -1.f;
     int mtrial = 0;
     uint32_t mt_idx = 0;
     double mt_ms[MT_N] = {}, mt_edges[MT_N] = {};
+    std::vector<double> mt_qcyc;        // [candidate][query]: SM cycles
     int mt_choice = -1;                 // -1: no margin trial has finished
     mn_stats stats{};
     bool timing = false;
@@ -301,6 +310,16 @@ void dfree(mn_graph *g, void *p, uint64_t bytes)
         mn_status s_ = (x);           \
         if (s_ != MN_OK) return s_;   \
     } while (0)
+
+// Copy the per-query margins of the learned order to the device (between
+// batches: nothing of the graph's is queued on the stream then).
+mn_status upload_margins(mn_graph *g)
+{
+    CK(cudaMemcpyAsync(g->d_qmargin, g->q_margin.data(), g->max_queries * sizeof(float), cudaMemcpyHostToDevice,
+                       g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    return MN_OK;
+}
 
 mn_status map_status(mn_graph *g, uint32_t st)
 {
@@ -713,7 +732,9 @@ mn_status choose_orders(mn_graph *g, int phase)
         g->stats.model_launches++;
         CK(cudaMemsetAsync(g->d_pick_hist, 0, 2 * PICK_BUCKETS * sizeof(uint32_t), g->stream));
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
-                                            g->pick_margin, g->presplit_log2, g->d_picked, g->d_bucket,
+                                            std::max(g->trial_margin, 0.f),
+                                            g->trial_margin >= 0.f ? nullptr : g->d_qmargin,
+                                            g->presplit_log2, g->d_picked, g->d_bucket,
                                             g->d_pick_hist);
         CKL();
         k_seed_order<<<grid, 256, 0, g->stream>>>(g->d_picked, g->d_bucket, &g->d_ctrl->nseeds[phase], cap,
@@ -996,6 +1017,7 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     // a re-run (qrun given) logs no work: its seeds were logged by the first run
     const bool explore = g->policy == MN_ORDER_EXPLORE && !qrun;
     p.seed_work = explore && a.phase < 2 ? seed_work_of(g, a.phase) : nullptr;
+    p.q_cycles = g->qcyc_on ? g->d_qcyc : nullptr;
     p.qrun[0] = qrun ? qrun[0] : ~0ull;
     p.qrun[1] = qrun ? qrun[1] : ~0ull;
     p.wait_polls = g->wait_polls;
@@ -1351,17 +1373,38 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
             }
         }
     }
+    g->trial_margin = -1.f;
+    g->qcyc_on = false;
     if (margin_now && est == MN_OK) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
+        const size_t nq = g->queries.size();
+        std::vector<unsigned long long> qc(nq);
+        CK(cudaMemcpyAsync(qc.data(), g->d_qcyc, nq * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           g->stream));
+        CK(cudaStreamSynchronize(g->stream));
         g->mt_ms[pd.mt_k] += ms;
         g->mt_edges[pd.mt_k] += (double)n;
-        if (++g->mt_idx >= MT_N * MT_ROUNDS) {     // keep the fastest per inserted edge
+        for (size_t q = 0; q < nq; q++) g->mt_qcyc[pd.mt_k * g->max_queries + q] += (double)qc[q];
+        if (++g->mt_idx >= MT_N * MT_ROUNDS) {
+            // each query keeps the margin under which its units took the
+            // fewest SM cycles per inserted edge; queries registered later
+            // take the margin of the least time per inserted edge
             uint32_t best = 0;
             for (uint32_t k = 1; k < MT_N; k++)
                 if (g->mt_ms[k] / g->mt_edges[k] < g->mt_ms[best] / g->mt_edges[best]) best = k;
             g->pick_margin = MT_CANDS[best];
             g->mt_choice = (int)best;
+            for (size_t q = 0; q < g->max_queries; q++) g->q_margin[q] = g->pick_margin;
+            for (size_t q = 0; q < nq; q++) {
+                uint32_t bq = 0;
+                for (uint32_t k = 1; k < MT_N; k++)
+                    if (g->mt_qcyc[k * g->max_queries + q] / g->mt_edges[k] <
+                        g->mt_qcyc[bq * g->max_queries + q] / g->mt_edges[bq])
+                        bq = k;
+                g->q_margin[q] = MT_CANDS[bq];
+            }
+            TRY(upload_margins(g));
             g->mtrial = 0;
             g->tuning = true;                      // then the launch parameters
         }
@@ -1560,6 +1603,8 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
     A(dalloc(g, &g->d_out_cap, (uint64_t)g->max_queries * 2));
     A(dalloc(g, &g->d_ctrl, 1));
     A(dalloc(g, &g->d_temporal, g->max_queries));
+    A(dalloc(g, &g->d_qmargin, g->max_queries, false));
+    A(dalloc(g, &g->d_qcyc, g->max_queries));
 #undef A
     {
         int nsm = 0, per_sm = 0;
@@ -1575,8 +1620,12 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
     e = cudaMallocHost((void **)&g->h_ctrl, sizeof(Ctrl));
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_OOM); }
     memset(g->h_ctrl, 0, sizeof(Ctrl));
+    g->q_margin.assign(g->max_queries, g->pick_margin);
     e = cudaMemcpyAsync(g->d_vmask, g->vmask_host.data(), sizeof(uint32_t) * g->V,
                         cudaMemcpyHostToDevice, g->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(g->d_qmargin, g->q_margin.data(), sizeof(float) * g->max_queries,
+                            cudaMemcpyHostToDevice, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) { g->err = cudaGetErrorString(e); return bail(MN_ERR_DEVICE); }
     *out = g;
@@ -1812,7 +1861,10 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     }
     const bool margin_now = g->mtrial && !g->queries.empty() && n;
     const uint32_t mt_k = g->mt_idx % MT_N;
-    if (margin_now) g->pick_margin = MT_CANDS[mt_k];
+    g->trial_margin = margin_now ? MT_CANDS[mt_k] : -1.f;
+    g->qcyc_on = margin_now;
+    if (margin_now)
+        CK(cudaMemsetAsync(g->d_qcyc, 0, g->queries.size() * sizeof(unsigned long long), g->stream));
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
     const bool trial_now = !tune_now && g->ftrial && !g->queries.empty() && n;
     if (tune_now) {
@@ -2582,6 +2634,7 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     g->mtrial = g->policy == MN_ORDER_LEARNED ? 1 : 0;
     g->mt_idx = 0;
     for (uint32_t k = 0; k < MT_N; k++) g->mt_ms[k] = g->mt_edges[k] = 0.0;
+    g->mt_qcyc.assign((size_t)MT_N * g->max_queries, 0.0);
     g->mt_choice = -1;
     g->tuning = !g->mtrial;
     return MN_OK;
@@ -2677,32 +2730,53 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
     return MN_OK;
 }
 
+static bool margin_ok(float m) { return m >= 0.f && !std::isinf(m); }   // false for NaN too
+
 mn_status mn_set_order_margin(mn_graph *g, float log2_margin)
 {
     if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
-    if (!(log2_margin >= 0.f) || std::isinf(log2_margin))
-        return fail(g, MN_ERR_INVALID_ARG, "margin must be finite and >= 0");
+    TRY(refuse_if_pending(g));
+    if (!margin_ok(log2_margin)) return fail(g, MN_ERR_INVALID_ARG, "margin must be finite and >= 0");
+    CK(cudaSetDevice(g->device));
     g->pick_margin = log2_margin;
-    return MN_OK;
+    for (auto &m : g->q_margin) m = log2_margin;
+    return upload_margins(g);
 }
 
-mn_status mn_get_order_margin(const mn_graph *g, float *log2_margin)
+mn_status mn_set_query_margin(mn_graph *g, uint32_t query_id, float log2_margin)
+{
+    if (!g) return fail(nullptr, MN_ERR_INVALID_ARG, "graph is NULL");
+    TRY(refuse_if_pending(g));
+    if (query_id >= g->queries.size()) return fail(g, MN_ERR_INVALID_ARG, "no such query");
+    if (!margin_ok(log2_margin)) return fail(g, MN_ERR_INVALID_ARG, "margin must be finite and >= 0");
+    CK(cudaSetDevice(g->device));
+    g->q_margin[query_id] = log2_margin;
+    return upload_margins(g);
+}
+
+mn_status mn_get_order_margin(const mn_graph *g, uint32_t query_id, float *log2_margin)
 {
     if (!g || !log2_margin) return MN_ERR_INVALID_ARG;
-    *log2_margin = g->pick_margin;
+    if (query_id == MN_DEFAULT_MARGIN) { *log2_margin = g->pick_margin; return MN_OK; }
+    if (query_id >= g->queries.size()) return MN_ERR_INVALID_ARG;
+    *log2_margin = g->q_margin[query_id];
     return MN_OK;
 }
 
 mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
-                                    uint32_t *n, float *kept)
+                                    double *query_cycles_per_edge, uint32_t *n, float *kept)
 {
     if (!g || !n) return MN_ERR_INVALID_ARG;
     *n = MT_N;
     if (g->mt_choice < 0) return MN_ERR_STATE;
-    if ((margins || ms_per_kedge) && cap < MT_N) return MN_ERR_INVALID_ARG;
+    if ((margins || ms_per_kedge || query_cycles_per_edge) && cap < MT_N) return MN_ERR_INVALID_ARG;
     for (uint32_t k = 0; k < MT_N; k++) {
         if (margins) margins[k] = MT_CANDS[k];
         if (ms_per_kedge) ms_per_kedge[k] = g->mt_edges[k] > 0 ? 1e3 * g->mt_ms[k] / g->mt_edges[k] : 0.0;
+        if (query_cycles_per_edge)
+            for (size_t q = 0; q < g->queries.size(); q++)
+                query_cycles_per_edge[q * cap + k] =
+                    g->mt_edges[k] > 0 ? g->mt_qcyc[k * g->max_queries + q] / g->mt_edges[k] : 0.0;
     }
     if (kept) *kept = MT_CANDS[g->mt_choice];
     return MN_OK;

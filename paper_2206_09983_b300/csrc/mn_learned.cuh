@@ -712,14 +712,15 @@ __device__ __forceinline__ uint32_t cost_bucket(float log2_cycles)
 
 // Per seed: the candidate order with the smallest predicted cost, but the
 // paper's order (candidate 0) unless the best prediction beats it by at least
-// `margin` (log2 units): the paper's order is the fallback.  A seed whose
+// the margin (log2 units; q_margin[q] for the seed's query q, or `margin` for
+// every query if q_margin is NULL): the paper's order is the fallback.  A seed whose
 // predicted cost under the chosen order is at least `split_log2` is flagged
 // for pre-splitting (SEED_PRESPLIT; split_log2 = +inf: never).  The picked
 // seed words go to `picked`, their cost buckets to `bucket`, and `hist`
 // (PICK_BUCKETS counters, zeroed by the caller) counts each bucket.
 __global__ void k_pick(const unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
-                       const float *y, float margin, float split_log2, unsigned long long *picked,
-                       uint8_t *bucket, uint32_t *hist)
+                       const float *y, float margin, const float *q_margin, float split_log2,
+                       unsigned long long *picked, uint8_t *bucket, uint32_t *hist)
 {
     __shared__ uint32_t sh[PICK_BUCKETS];
     for (uint32_t i = threadIdx.x; i < PICK_BUCKETS; i += blockDim.x) sh[i] = 0;
@@ -733,8 +734,10 @@ __global__ void k_pick(const unsigned long long *seeds, const uint32_t *nseeds, 
             const float v = y[(size_t)s * NCAND + k];
             if (v < bv) { bv = v; best = k; }
         }
-        if (bv > y0 - margin) { best = 0; bv = y0; }
-        unsigned long long w = (seeds[s] & ~(0xffull << 24)) | ((unsigned long long)best << 24);
+        const unsigned long long sd = seeds[s];
+        const float m = q_margin ? q_margin[(sd >> 8) & 0xffffu] : margin;
+        if (bv > y0 - m) { best = 0; bv = y0; }
+        unsigned long long w = (sd & ~(0xffull << 24)) | ((unsigned long long)best << 24);
         if (bv >= split_log2) w |= SEED_PRESPLIT;
         picked[s] = w;
         const uint32_t b = cost_bucket(bv);

@@ -47,7 +47,7 @@ EXPORTS = [
     "mn_autotune_candidates", "mn_autotune_results", "mn_set_filtering", "mn_read_filter",
     "mn_set_graph_capture", "mn_set_spill", "mn_read_spill", "mn_set_slice_staging",
     "mn_get_slice_staging", "mn_autotune_filter_result", "mn_last_error", "mn_set_order_margin",
-    "mn_get_order_margin", "mn_autotune_margin_result",
+    "mn_get_order_margin", "mn_autotune_margin_result", "mn_set_query_margin",
 ]
 MN_WAIT_HOLD = 0x1
 MN_ORDER = {"paper": 0, "explore": 1, "learned": 2}
@@ -178,8 +178,9 @@ def load(path: str | None = None):
                                           C.POINTER(C.c_int32)]),
         "mn_get_slice_staging": (S, [P, C.POINTER(C.c_uint32)]),
         "mn_set_order_margin": (S, [P, C.c_float]),
-        "mn_get_order_margin": (S, [P, C.POINTER(C.c_float)]),
-        "mn_autotune_margin_result": (S, [P, C.c_uint32, P, P, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]),
+        "mn_set_query_margin": (S, [P, C.c_uint32, C.c_float]),
+        "mn_get_order_margin": (S, [P, C.c_uint32, C.POINTER(C.c_float)]),
+        "mn_autotune_margin_result": (S, [P, C.c_uint32, P, P, P, C.POINTER(C.c_uint32), C.POINTER(C.c_float)]),
         "mn_autotune_candidates": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_autotune_results": (S, [P, C.c_uint32, P, C.POINTER(C.c_uint32)]),
         "mn_set_timing": (S, [P, C.c_int32]),
@@ -576,25 +577,34 @@ class Graph:
 
     def autotune_margin_result(self):
         """The autotuner's margin trial of the learned order: the candidate
-        margins (log2 units), their ms per 1,000 inserted edges, and the margin
-        kept; None before a trial."""
+        margins (log2 units), their ms per 1,000 inserted edges, per registered
+        query the SM cycles per inserted edge under each, and the default
+        margin kept; None before a trial."""
+        cap = 16
         n, kept = C.c_uint32(), C.c_float()
-        m = (C.c_float * 16)()
-        ms = (C.c_double * 16)()
-        st = self._lib.mn_autotune_margin_result(self._h, 16, m, ms, C.byref(n), C.byref(kept))
+        m = (C.c_float * cap)()
+        ms = (C.c_double * cap)()
+        qc = np.zeros((max(1, len(self.layouts)), cap), dtype=np.float64)
+        st = self._lib.mn_autotune_margin_result(self._h, cap, m, ms, qc.ctypes.data, C.byref(n), C.byref(kept))
         if st == MN_ERR_STATE:
             return None
         self._check(st)
-        return {"margins": list(m[:n.value]), "ms_per_kedge": list(ms[:n.value]), "kept": kept.value}
+        k = n.value
+        return {"margins": list(m[:k]), "ms_per_kedge": list(ms[:k]),
+                "query_cycles_per_edge": qc[:len(self.layouts), :k].tolist(), "kept": kept.value}
 
     def set_order_margin(self, log2_margin: float):
-        """Margin (log2 units of predicted cost) by which a learned pick must
-        beat the paper's order (mn_set_order_margin)."""
+        """Every query's margin (log2 units of predicted cost) by which a
+        learned pick must beat the paper's order (mn_set_order_margin)."""
         self._check(self._lib.mn_set_order_margin(self._h, log2_margin))
 
-    def get_order_margin(self) -> float:
+    def set_query_margin(self, qid: int, log2_margin: float):
+        self._check(self._lib.mn_set_query_margin(self._h, qid, log2_margin))
+
+    def get_order_margin(self, qid: int = None) -> float:
+        """One query's margin; qid None: the default for queries registered later."""
         v = C.c_float()
-        self._check(self._lib.mn_get_order_margin(self._h, C.byref(v)))
+        self._check(self._lib.mn_get_order_margin(self._h, 0xFFFFFFFF if qid is None else qid, C.byref(v)))
         return v.value
 
     def autotune_state(self):
@@ -610,6 +620,7 @@ class Graph:
         d["presplit_log2"] = self.get_presplit()
         d["slice_min"] = self.get_slice_staging()
         d["order_margin"] = self.get_order_margin()
+        d["query_margins"] = [self.get_order_margin(q) for q in range(len(self.layouts))]
         return d
 
     def reset_stats(self):

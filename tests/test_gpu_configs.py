@@ -164,19 +164,30 @@ def test_online_autotuner_batches_are_exact():
         assert mt is not None and mt["margins"] == [0.0, 0.5, 1.0, 2.0, 3.0]
         assert all(v > 0 for v in mt["ms_per_kedge"])
         assert mt["kept"] == mt["margins"][int(np.argmin(mt["ms_per_kedge"]))] == g.get_order_margin()
+        for qi in range(len(qs)):                      # each query: the fewest SM cycles per edge
+            cyc = mt["query_cycles_per_edge"][qi]
+            assert all(v > 0 for v in cyc)
+            assert g.get_order_margin(qi) == mt["margins"][int(np.argmin(cyc))]
         assert g.stats()["seeds_filtered"] > 0         # the trial's filtered batches pruned seeds
 
 
 def test_order_margin_is_exact_and_checked():
-    """The learned order at margins 0 (the model trusted outright) and 3:
-    lists equal the oracle's; the margin changes the picks, so the work
-    differs; negative, infinite and NaN margins are refused."""
+    """The learned order at margins 0 (the model trusted outright) and 3, and
+    with a different margin per query: lists equal the oracle's; the margin
+    changes the picks, so the work differs; negative, infinite and NaN margins
+    and unknown query ids are refused."""
     s, qs = split_stream(), split_queries()
     with fresh(s, qs) as g:
-        assert g.get_order_margin() == 1.0
+        assert g.get_order_margin() == 1.0 and [g.get_order_margin(q) for q in range(len(qs))] == [1.0] * len(qs)
         for bad in (-0.5, float("inf"), float("nan")):
             with pytest.raises(M.MnError):
                 g.set_order_margin(bad)
+            with pytest.raises(M.MnError):
+                g.set_query_margin(0, bad)
+        with pytest.raises(M.MnError):
+            g.set_query_margin(len(qs), 1.0)
+        with pytest.raises(M.MnError):
+            g.get_order_margin(len(qs))
         g.set_order_policy("explore")
         for k in range(3):
             r = g.insert(M.edges_from_stream(s, W + k * B, W + (k + 1) * B))
@@ -193,6 +204,12 @@ def test_order_margin_is_exact_and_checked():
             st = g.stats()
             work.append(st["entries_scanned"] + st["binds"])
         assert work[0] != work[1]
+        for qi, m in enumerate((0.0, 3.0, 0.5)):
+            g.set_query_margin(qi, m)
+        assert [g.get_order_margin(q) for q in range(len(qs))] == [0.0, 3.0, 0.5]
+        assert g.get_order_margin() == 3.0             # later queries: the last set_order_margin
+        r = g.insert(M.edges_from_stream(s, W + 5 * B, W + 6 * B))
+        check(g, s, qs, 5, r, "margins per query")
 
 
 def test_multi_label_vertices_subset_masks():
