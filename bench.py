@@ -95,7 +95,7 @@ class ClockSampler:
 # launch, the mean of the learned arm's first two timed launches (one per batch) in
 # one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
 # enumerator code it was taken on (enum_source_sha1): null once that changed.
-ENUM_TRAFFIC = {"source_sha1": "c0d8f24927b8660bd5803a058df6918295909c9c", "bytes_per_launch": 1084.3e6}
+ENUM_TRAFFIC = {"source_sha1": "9f06f603ebe0fd83b6d7536fca7e54931b253b10", "bytes_per_launch": 946.3e6}
 
 
 def enum_source_sha1() -> str:
