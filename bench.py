@@ -336,10 +336,11 @@ def run_serve(args, local):
         r["fraction_of_max"] = f
         out["levels"].append(r)
     out["value"] = out["levels"][-1]["value"]
+    out["device_memory"] = g.memory_info()
+    g.close()
     # sampled parity on a fresh replay of device batches (the serve run kept
     # no lists): a second graph replays the same edges as the same batches
     out["parity"] = None if args.no_serve_parity else serve_parity(args, local, stream, packed, qs, W, MB)
-    g.close()
     return out
 
 

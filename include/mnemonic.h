@@ -378,26 +378,33 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
  * registered later get.
  *
  * How far the model's ranking can be trusted depends on the query, so when
- * mn_autotune starts under MN_ORDER_LEARNED it first runs a margin trial on
- * live inserting batches: margins {0, 0.5, 1, 2, 3} in turn for every query,
- * two rounds (10 batches), each batch timed like a filtering-trial batch and
- * the SM cycles of each query's work units logged.  Each registered query
- * then keeps the margin under which its units took the fewest cycles per
- * inserted edge, and the margin with the least time per inserted edge
- * becomes the default for later queries; the launch candidates and the
- * filtering trial follow.  (Switching the policy away from learned before the
- * trial ends skips it.)  mn_autotune_margin_result gives, for candidate k <
- * *n (= 5): margins[k], ms_per_kedge[k] (ms per 1,000 inserted edges) and,
- * for registered query q, query_cycles_per_edge[q * cap + k]; any of the
- * three may be NULL, and MN_ERR_INVALID_ARG if cap is below *n.  *kept (may
- * be NULL) gets the default margin chosen.  MN_ERR_STATE before a margin
- * trial has finished. */
+ * mn_autotune starts under MN_ORDER_LEARNED it first runs a margin trial on 6
+ * live inserting batches.  Only a seed whose model pick beats the paper's
+ * order by a predicted gain in (0, 3) log2 units can be decided differently
+ * by the candidate margins {0, 0.5, 1, 2, 3}; such a seed takes the paper's
+ * order or the pick with equal odds (drawn pseudo-randomly per seed), and
+ * the enumerator logs the SM cycles of its work units per (query, gain
+ * interval between two candidates, arm).  Since a margin picks the model's
+ * order exactly for the intervals at or above it, each candidate's cycles
+ * follow from the two arms' means per interval; each registered query keeps
+ * the margin of the fewest estimated cycles (both arms run on random halves
+ * of the same batches' seeds, so batch-to-batch differences cancel), and the
+ * margin of the fewest cycles over all queries becomes the default for later
+ * queries; the launch candidates and the filtering trial follow.  (Switching
+ * the policy away from learned before the trial ends skips it.)
+ * mn_autotune_margin_result gives, for candidate k < *n (= 5): margins[k],
+ * cycles_per_seed[k] (the estimated SM cycles per trial seed under margin k,
+ * over all queries) and, for registered query q, query_cycles_per_seed[q *
+ * cap + k] (0 for a query none of whose seeds depended on the margin: it
+ * keeps the default); any of the three may be NULL, and MN_ERR_INVALID_ARG if
+ * cap is below *n.  *kept (may be NULL) gets the default margin chosen.
+ * MN_ERR_STATE before a margin trial has finished. */
 #define MN_DEFAULT_MARGIN 0xffffffffu
 mn_status mn_set_order_margin(mn_graph *g, float log2_margin);
 mn_status mn_set_query_margin(mn_graph *g, uint32_t query_id, float log2_margin);
 mn_status mn_get_order_margin(const mn_graph *g, uint32_t query_id, float *log2_margin);
-mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
-                                    double *query_cycles_per_edge, uint32_t *n, float *kept);
+mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *cycles_per_seed,
+                                    double *query_cycles_per_seed, uint32_t *n, float *kept);
 
 /* One candidate of the autotuner (presplit_log2 = 0: pre-splitting off;
  * slice_min = 0: no shared-memory staging, mn_set_slice_staging). */

@@ -810,8 +810,10 @@ constexpr uint32_t RESERVE_POLLS = 1u << 12;
 constexpr uint32_t SPLIT_MIN = 40;         // default: split a depth's range only above this many entries
 // Seed word flag (set by k_pick): the seed's predicted work is above the
 // pre-split threshold.  Seed words: seq32 << 32 | flags and candidate order
-// << 24 | query << 8 | query edge.
+// << 24 | query << 8 | query edge; during the autotuner's margin trial bits
+// 26-29 hold the seed's trial slot (MARGIN_SLOTS - 1: not in the trial).
 constexpr unsigned long long SEED_PRESPLIT = 1ull << 31;
+constexpr uint32_t SEED_MARGIN_SHIFT = 26, MARGIN_SLOTS = 16;
 constexpr int PRESPLIT_PIECES = 16;
 
 struct EnumParams {
@@ -844,7 +846,8 @@ struct EnumParams {
                                         //  seeds whose endpoints the filtering excludes,
                                         //  entries read from staged windows]
     unsigned long long *seed_work;      // optional: SM cycles spent per seed (all its units)
-    unsigned long long *q_cycles;       // optional: SM cycles spent per query (all its units)
+    unsigned long long *q_cycles;       // optional: SM cycles per (query, trial slot of the seed
+                                        // word), [q][MARGIN_SLOTS], all units of the seed
     // optional second seed set, enumerated in the same launch after the first
     // (the other phase of the same batch): its seeds, avoid interval, sign and
     // work log; seeds1 == NULL: one set
@@ -1688,7 +1691,10 @@ __global__ void __launch_bounds__(ENUM_WARPS * 32, ENUM_MIN_BLOCKS) k_enumerate(
             w_busy += cyc;
             unsigned long long *sw_log = set ? p.seed_work1 : p.seed_work;
             if (sw_log) atomicAdd(&sw_log[sid], cyc);
-            if (p.q_cycles) atomicAdd(&p.q_cycles[q], cyc);
+            if (p.q_cycles) {
+                const unsigned long long sdw = (set ? p.seeds1 : p.seeds)[sid];
+                atomicAdd(&p.q_cycles[q * MARGIN_SLOTS + ((uint32_t)(sdw >> SEED_MARGIN_SHIFT) & 15u)], cyc);
+            }
         }
         if (lane == 0) {
             __threadfence();

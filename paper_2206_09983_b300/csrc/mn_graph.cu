@@ -92,14 +92,14 @@ struct Phase {
 
 // A batch queued by mn_insert_batch with MN_ASYNC: what its completion needs.
 // the autotuner's candidate margins of the learned order (log2 units)
-constexpr uint32_t MT_N = 5, MT_ROUNDS = 2;
+constexpr uint32_t MT_N = 5, MT_BATCHES = 6;
 constexpr float MT_CANDS[MT_N] = {0.f, 0.5f, 1.f, 2.f, 3.f};
+static_assert(MT_N <= MARGIN_SLOTS / 2, "two trial slots per margin interval");
 
 struct PendingBatch {
     bool active = false;
     uint64_t id = 0, n = 0, x = 0, hi_new = 0;
     bool count_only = false, tune_now = false, trial_now = false, margin_now = false;
-    uint32_t mt_k = 0;                  // margin_now: the candidate margin this batch ran under
     int nph = 0;
     Phase ph[2] = {};
 };
@@ -197,20 +197,20 @@ struct mn_graph {
     // the learned order's margins (log2 units of predicted cost by which the
     // best candidate must beat the paper's order): per query (q_margin,
     // mirrored in d_qmargin), pick_margin for queries registered later.  The
-    // autotuner's margin trial, run first under MN_ORDER_LEARNED: MT_ROUNDS
-    // rounds over the MT_N candidate margins, one live inserting batch each,
-    // every query under the batch's candidate (trial_margin >= 0) and the SM
-    // cycles of each query's units logged (qcyc_on, d_qcyc)
+    // autotuner's margin trial, run first under MN_ORDER_LEARNED on MT_BATCHES
+    // live inserting batches (qcyc_on): each seed whose choice depends on the
+    // margin takes the paper's order or the model's pick at random (k_pick),
+    // and the SM cycles of its units and the seeds are logged per (query,
+    // interval of predicted gain, arm) (d_qcyc, d_qseeds)
     float pick_margin = 1.0f;
     std::vector<float> q_margin;
     float *d_qmargin = nullptr;
-    unsigned long long *d_qcyc = nullptr;
+    unsigned long long *d_qcyc = nullptr;   // [q][MARGIN_SLOTS]
+    uint32_t *d_qseeds = nullptr;           // [q][MARGIN_SLOTS]
     bool qcyc_on = false;
-    float trial_margin = -1.f;
     int mtrial = 0;
     uint32_t mt_idx = 0;
-    double mt_ms[MT_N] = {}, mt_edges[MT_N] = {};
-    std::vector<double> mt_qcyc;        // [candidate][query]: SM cycles
+    std::vector<double> mt_qcyc, mt_qseeds;   // [query][MARGIN_SLOTS]: SM cycles, seeds
     int mt_choice = -1;                 // -1: no margin trial has finished
     mn_stats stats{};
     bool timing = false;
@@ -706,6 +706,44 @@ unsigned long long *seed_work_of(mn_graph *g, int phase)
     return g->d_seed_work + (phase == 1 ? g->learn_rows / NCAND : 0);
 }
 
+// Estimated SM cycles of each registered query's trial seeds under each
+// candidate margin j, [q][MT_N]: the seeds of gain interval i take the
+// model's pick under margin j iff i >= j, so cost(j) = sum over i < j of
+// S_i x (mean cycles of its paper-order arm) + sum over i >= j of S_i x
+// (mean cycles of its pick arm), S_i the interval's seeds (an empty arm
+// takes the other arm's mean).
+std::vector<double> margin_costs(const mn_graph *g)
+{
+    const size_t nq = g->queries.size();
+    std::vector<double> cost(nq * MT_N, 0.0);
+    for (size_t q = 0; q < nq; q++) {
+        const double *C = &g->mt_qcyc[q * MARGIN_SLOTS], *S = &g->mt_qseeds[q * MARGIN_SLOTS];
+        for (uint32_t i = 0; i + 1 < MT_N; i++) {
+            const double sp = S[2 * i], sb = S[2 * i + 1], si = sp + sb;
+            if (si <= 0.0) continue;
+            double mp = sp > 0 ? C[2 * i] / sp : 0.0, mb = sb > 0 ? C[2 * i + 1] / sb : 0.0;
+            if (sp <= 0) mp = mb;
+            if (sb <= 0) mb = mp;
+            for (uint32_t j = 0; j < MT_N; j++) cost[q * MT_N + j] += si * (i >= j ? mb : mp);
+        }
+    }
+    return cost;
+}
+
+// k_pick's margin-trial argument: the candidates while a trial batch runs,
+// else none.
+MarginTrial margin_trial(mn_graph *g)
+{
+    MarginTrial mt;
+    memset(&mt, 0, sizeof(mt));
+    if (!g->qcyc_on) return mt;
+    for (uint32_t k = 0; k < MT_N; k++) mt.m[k] = MT_CANDS[k];     // ascending, from 0
+    mt.n = MT_N;
+    mt.round = g->mt_idx + 1;
+    mt.q_seeds = g->d_qseeds;
+    return mt;
+}
+
 // Before enumerating `phase`: pick each seed's matching order by policy.
 mn_status choose_orders(mn_graph *g, int phase)
 {
@@ -732,8 +770,7 @@ mn_status choose_orders(mn_graph *g, int phase)
         g->stats.model_launches++;
         CK(cudaMemsetAsync(g->d_pick_hist, 0, 2 * PICK_BUCKETS * sizeof(uint32_t), g->stream));
         k_pick<<<grid, 256, 0, g->stream>>>(g->d_seeds[phase], &g->d_ctrl->nseeds[phase], cap, g->d_y,
-                                            std::max(g->trial_margin, 0.f),
-                                            g->trial_margin >= 0.f ? nullptr : g->d_qmargin,
+                                            g->d_qmargin, margin_trial(g),
                                             g->presplit_log2, g->d_picked, g->d_bucket,
                                             g->d_pick_hist);
         CKL();
@@ -1216,6 +1253,8 @@ mn_status grow_outputs(mn_graph *g, int phase, unsigned long long *rerun, bool *
 // Before a launch: lists of queries whose recent batches produced more
 // records per edge than this batch's lists hold are grown now, so that the
 // batch is not enumerated twice.
+constexpr uint64_t PRESIZE_MAX_BYTES = 1ull << 30;   // per result list
+
 mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
 {
     bool any = false, over = false;
@@ -1225,8 +1264,12 @@ mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
         for (size_t q = 0; q < g->queries.size() && q < g->rec_rate[s].size(); q++) {
             // three times the decayed maximum: a batch that brings a hub
             // into play multiplies one query's output, and a second launch
-            // costs more than the memory (lists are grown within the budget)
-            const double est = 3.0 * g->rec_rate[s][q] * (double)edges;
+            // costs more than the memory (lists are grown within the budget);
+            // but no list is presized past PRESIZE_MAX_BYTES, so that one
+            // heavy batch's rate times a large batch cannot claim the device
+            // (a list that overflows is grown to its exact count)
+            const double est = std::min(3.0 * g->rec_rate[s][q] * (double)edges,
+                                        (double)(PRESIZE_MAX_BYTES / g->queries[q].rec_bytes));
             if (est <= (double)g->queries[q].out_cap[s]) continue;
             bool grown = false;
             TRY(ensure_out_cap(g, q, s, (uint64_t)est, &grown, &over));
@@ -1373,35 +1416,40 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
             }
         }
     }
-    g->trial_margin = -1.f;
     g->qcyc_on = false;
     if (margin_now && est == MN_OK) {
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
-        const size_t nq = g->queries.size();
-        std::vector<unsigned long long> qc(nq);
-        CK(cudaMemcpyAsync(qc.data(), g->d_qcyc, nq * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+        const size_t nq = g->queries.size(), ns = nq * MARGIN_SLOTS;
+        std::vector<unsigned long long> qc(ns);
+        std::vector<uint32_t> qs(ns);
+        CK(cudaMemcpyAsync(qc.data(), g->d_qcyc, ns * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                            g->stream));
+        CK(cudaMemcpyAsync(qs.data(), g->d_qseeds, ns * sizeof(uint32_t), cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
-        g->mt_ms[pd.mt_k] += ms;
-        g->mt_edges[pd.mt_k] += (double)n;
-        for (size_t q = 0; q < nq; q++) g->mt_qcyc[pd.mt_k * g->max_queries + q] += (double)qc[q];
-        if (++g->mt_idx >= MT_N * MT_ROUNDS) {
-            // each query keeps the margin under which its units took the
-            // fewest SM cycles per inserted edge; queries registered later
-            // take the margin of the least time per inserted edge
+        for (size_t i = 0; i < ns; i++) {
+            g->mt_qcyc[i] += (double)qc[i];
+            g->mt_qseeds[i] += (double)qs[i];
+        }
+        if (++g->mt_idx >= MT_BATCHES) {
+            // each query keeps the margin of the least estimated cycles
+            // (margin_costs); queries registered later take the margin of the
+            // least cycles summed over all queries
+            const std::vector<double> cost = margin_costs(g);
+            double tot[MT_N] = {};
+            for (size_t q = 0; q < nq; q++)
+                for (uint32_t j = 0; j < MT_N; j++) tot[j] += cost[q * MT_N + j];
             uint32_t best = 0;
-            for (uint32_t k = 1; k < MT_N; k++)
-                if (g->mt_ms[k] / g->mt_edges[k] < g->mt_ms[best] / g->mt_edges[best]) best = k;
+            for (uint32_t j = 1; j < MT_N; j++)
+                if (tot[j] < tot[best]) best = j;
             g->pick_margin = MT_CANDS[best];
             g->mt_choice = (int)best;
             for (size_t q = 0; q < g->max_queries; q++) g->q_margin[q] = g->pick_margin;
             for (size_t q = 0; q < nq; q++) {
                 uint32_t bq = 0;
-                for (uint32_t k = 1; k < MT_N; k++)
-                    if (g->mt_qcyc[k * g->max_queries + q] / g->mt_edges[k] <
-                        g->mt_qcyc[bq * g->max_queries + q] / g->mt_edges[bq])
-                        bq = k;
+                double any = 0.0;
+                for (uint32_t j = 0; j < MT_N; j++) any += cost[q * MT_N + j];
+                if (any <= 0.0) continue;                  // no seed of q depended on the margin
+                for (uint32_t j = 1; j < MT_N; j++)
+                    if (cost[q * MT_N + j] < cost[q * MT_N + bq]) bq = j;
                 g->q_margin[q] = MT_CANDS[bq];
             }
             TRY(upload_margins(g));
@@ -1604,7 +1652,8 @@ mn_status mn_create_graph(const mn_graph_config *cfg, mn_graph **out)
     A(dalloc(g, &g->d_ctrl, 1));
     A(dalloc(g, &g->d_temporal, g->max_queries));
     A(dalloc(g, &g->d_qmargin, g->max_queries, false));
-    A(dalloc(g, &g->d_qcyc, g->max_queries));
+    A(dalloc(g, &g->d_qcyc, (uint64_t)g->max_queries * MARGIN_SLOTS));
+    A(dalloc(g, &g->d_qseeds, (uint64_t)g->max_queries * MARGIN_SLOTS));
 #undef A
     {
         int nsm = 0, per_sm = 0;
@@ -1860,11 +1909,12 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
         g->tuning = true;
     }
     const bool margin_now = g->mtrial && !g->queries.empty() && n;
-    const uint32_t mt_k = g->mt_idx % MT_N;
-    g->trial_margin = margin_now ? MT_CANDS[mt_k] : -1.f;
     g->qcyc_on = margin_now;
-    if (margin_now)
-        CK(cudaMemsetAsync(g->d_qcyc, 0, g->queries.size() * sizeof(unsigned long long), g->stream));
+    if (margin_now) {
+        const size_t ns = g->queries.size() * MARGIN_SLOTS;
+        CK(cudaMemsetAsync(g->d_qcyc, 0, ns * sizeof(unsigned long long), g->stream));
+        CK(cudaMemsetAsync(g->d_qseeds, 0, ns * sizeof(uint32_t), g->stream));
+    }
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
     const bool trial_now = !tune_now && g->ftrial && !g->queries.empty() && n;
     if (tune_now) {
@@ -1937,7 +1987,6 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     pd.tune_now = tune_now;
     pd.trial_now = trial_now;
     pd.margin_now = margin_now;
-    pd.mt_k = mt_k;
     pd.nph = nph;
     for (int k = 0; k < nph; k++) pd.ph[k] = ph[k];
     if (flags & MN_ASYNC) {
@@ -2633,8 +2682,8 @@ mn_status mn_autotune(mn_graph *g, uint32_t batches_per_config)
     // under learned orders the margin trial comes first, then the launch
     g->mtrial = g->policy == MN_ORDER_LEARNED ? 1 : 0;
     g->mt_idx = 0;
-    for (uint32_t k = 0; k < MT_N; k++) g->mt_ms[k] = g->mt_edges[k] = 0.0;
-    g->mt_qcyc.assign((size_t)MT_N * g->max_queries, 0.0);
+    g->mt_qcyc.assign((size_t)MARGIN_SLOTS * g->max_queries, 0.0);
+    g->mt_qseeds.assign((size_t)MARGIN_SLOTS * g->max_queries, 0.0);
     g->mt_choice = -1;
     g->tuning = !g->mtrial;
     return MN_OK;
@@ -2706,7 +2755,7 @@ mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batche
     if (batches_left) {
         uint64_t left = 0;
         if (g->mtrial)
-            left = (uint64_t)(MT_N * MT_ROUNDS - g->mt_idx) + (uint64_t)g->tune_cfgs.size() * g->tune_per +
+            left = (uint64_t)(MT_BATCHES - g->mt_idx) + (uint64_t)g->tune_cfgs.size() * g->tune_per +
                    2ull * g->ft_per;
         else if (g->tuning)
             left = (uint64_t)(g->tune_cfgs.size() - g->tune_idx) * g->tune_per - g->tune_in + 2ull * g->ft_per;
@@ -2763,20 +2812,31 @@ mn_status mn_get_order_margin(const mn_graph *g, uint32_t query_id, float *log2_
     return MN_OK;
 }
 
-mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *ms_per_kedge,
-                                    double *query_cycles_per_edge, uint32_t *n, float *kept)
+mn_status mn_autotune_margin_result(const mn_graph *g, uint32_t cap, float *margins, double *cycles_per_seed,
+                                    double *query_cycles_per_seed, uint32_t *n, float *kept)
 {
     if (!g || !n) return MN_ERR_INVALID_ARG;
     *n = MT_N;
     if (g->mt_choice < 0) return MN_ERR_STATE;
-    if ((margins || ms_per_kedge || query_cycles_per_edge) && cap < MT_N) return MN_ERR_INVALID_ARG;
-    for (uint32_t k = 0; k < MT_N; k++) {
-        if (margins) margins[k] = MT_CANDS[k];
-        if (ms_per_kedge) ms_per_kedge[k] = g->mt_edges[k] > 0 ? 1e3 * g->mt_ms[k] / g->mt_edges[k] : 0.0;
-        if (query_cycles_per_edge)
-            for (size_t q = 0; q < g->queries.size(); q++)
-                query_cycles_per_edge[q * cap + k] =
-                    g->mt_edges[k] > 0 ? g->mt_qcyc[k * g->max_queries + q] / g->mt_edges[k] : 0.0;
+    if ((margins || cycles_per_seed || query_cycles_per_seed) && cap < MT_N) return MN_ERR_INVALID_ARG;
+    const size_t nq = g->queries.size();
+    const std::vector<double> cost = margin_costs(g);
+    double all = 0.0;
+    std::vector<double> seeds(nq, 0.0);
+    for (size_t q = 0; q < nq; q++) {
+        for (uint32_t s = 0; s < 2 * (MT_N - 1); s++)     // the intervals' two arms
+            seeds[q] += g->mt_qseeds[q * MARGIN_SLOTS + s];
+        all += seeds[q];
+    }
+    for (uint32_t j = 0; j < MT_N; j++) {
+        if (margins) margins[j] = MT_CANDS[j];
+        double c = 0.0;
+        for (size_t q = 0; q < nq; q++) {
+            c += cost[q * MT_N + j];
+            if (query_cycles_per_seed)
+                query_cycles_per_seed[q * cap + j] = seeds[q] > 0 ? cost[q * MT_N + j] / seeds[q] : 0.0;
+        }
+        if (cycles_per_seed) cycles_per_seed[j] = all > 0 ? c / all : 0.0;
     }
     if (kept) *kept = MT_CANDS[g->mt_choice];
     return MN_OK;

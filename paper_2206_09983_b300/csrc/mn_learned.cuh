@@ -710,16 +710,30 @@ __device__ __forceinline__ uint32_t cost_bucket(float log2_cycles)
     return PICK_BUCKETS - 1 - (uint32_t)h;
 }
 
+// The autotuner's margin trial.  A margin matters only for a seed whose
+// model pick beats the paper's order by a predicted gain g = y0 - y_best in
+// (0, m_max), m_max the largest candidate margin: outside it every candidate
+// makes the same choice.  The candidate margins m_0 = 0 < m_1 < ... cut
+// [0, m_max) into intervals [m_i, m_i+1); a seed whose gain falls in
+// interval i takes the paper's order or the model's pick with equal odds
+// (splitmix64 of seed index and round), slot 2 i + arm in its seed word and
+// in mt.q_seeds, so each interval compares the two arms on a random half of
+// the same batches' seeds.  Other seeds take the paper's order (g = 0) or
+// the pick (g >= m_max) and slot MARGIN_SLOTS - 1.
+struct MarginTrial {
+    float m[MARGIN_SLOTS / 2];          // candidate margins, ascending, m[0] = 0
+    uint32_t n;                         // candidates; 0: no trial
+    uint32_t round;
+    uint32_t *q_seeds;                  // [q][MARGIN_SLOTS]
+};
+
 // Per seed: the candidate order with the smallest predicted cost, but the
 // paper's order (candidate 0) unless the best prediction beats it by at least
-// the margin (log2 units; q_margin[q] for the seed's query q, or `margin` for
-// every query if q_margin is NULL): the paper's order is the fallback.  A seed whose
-// predicted cost under the chosen order is at least `split_log2` is flagged
-// for pre-splitting (SEED_PRESPLIT; split_log2 = +inf: never).  The picked
-// seed words go to `picked`, their cost buckets to `bucket`, and `hist`
-// (PICK_BUCKETS counters, zeroed by the caller) counts each bucket.
+// the margin (log2 units; q_margin[q] for the seed's query q): the paper's
+// order is the fallback.  During a margin trial (mt.n > 0) the seeds whose
+// choice depends on the margin are split at random instead (MarginTrial).
 __global__ void k_pick(const unsigned long long *seeds, const uint32_t *nseeds, uint32_t seed_cap,
-                       const float *y, float margin, const float *q_margin, float split_log2,
+                       const float *y, const float *q_margin, MarginTrial mt, float split_log2,
                        unsigned long long *picked, uint8_t *bucket, uint32_t *hist)
 {
     __shared__ uint32_t sh[PICK_BUCKETS];
@@ -735,9 +749,30 @@ __global__ void k_pick(const unsigned long long *seeds, const uint32_t *nseeds, 
             if (v < bv) { bv = v; best = k; }
         }
         const unsigned long long sd = seeds[s];
-        const float m = q_margin ? q_margin[(sd >> 8) & 0xffffu] : margin;
-        if (bv > y0 - m) { best = 0; bv = y0; }
-        unsigned long long w = (sd & ~(0xffull << 24)) | ((unsigned long long)best << 24);
+        const uint32_t q = (uint32_t)(sd >> 8) & 0xffffu;
+        uint32_t slot = MARGIN_SLOTS - 1;
+        if (mt.n) {
+            const float gain = y0 - bv;                  // >= 0; 0 when the paper's order is best
+            uint32_t iv = mt.n;                          // interval of the gain
+            if (best != 0)
+                for (uint32_t i = 0; i + 1 < mt.n; i++)
+                    if (gain >= mt.m[i] && gain < mt.m[i + 1]) iv = i;
+            if (iv + 1 < mt.n) {
+                unsigned long long z = ((unsigned long long)mt.round << 32) + s + 0x9E3779B97F4A7C15ull;
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                z ^= z >> 31;
+                const uint32_t arm = (uint32_t)(z & 1u);   // 0: the paper's order, 1: the pick
+                if (!arm) { best = 0; bv = y0; }
+                slot = 2 * iv + arm;
+                atomicAdd(&mt.q_seeds[q * MARGIN_SLOTS + slot], 1u);
+            }
+        } else if (bv > y0 - q_margin[q]) {
+            best = 0;
+            bv = y0;
+        }
+        unsigned long long w = (sd & ~(0xffull << 24)) | ((unsigned long long)best << 24) |
+                               ((unsigned long long)slot << SEED_MARGIN_SHIFT);
         if (bv >= split_log2) w |= SEED_PRESPLIT;
         picked[s] = w;
         const uint32_t b = cost_bucket(bv);

@@ -577,21 +577,23 @@ class Graph:
 
     def autotune_margin_result(self):
         """The autotuner's margin trial of the learned order: the candidate
-        margins (log2 units), their ms per 1,000 inserted edges, per registered
-        query the SM cycles per inserted edge under each, and the default
-        margin kept; None before a trial."""
+        margins (log2 units), the SM cycles per seed under each (all queries),
+        per registered query the SM cycles per seed under each (0: no seed of
+        it drew that margin), and the default margin kept; None before a
+        trial."""
         cap = 16
         n, kept = C.c_uint32(), C.c_float()
         m = (C.c_float * cap)()
-        ms = (C.c_double * cap)()
-        qc = np.zeros((max(1, len(self.layouts)), cap), dtype=np.float64)
-        st = self._lib.mn_autotune_margin_result(self._h, cap, m, ms, qc.ctypes.data, C.byref(n), C.byref(kept))
+        cs = (C.c_double * cap)()
+        nq = len(self.layouts)
+        qc = np.zeros((max(1, nq), cap), dtype=np.float64)
+        st = self._lib.mn_autotune_margin_result(self._h, cap, m, cs, qc.ctypes.data, C.byref(n), C.byref(kept))
         if st == MN_ERR_STATE:
             return None
         self._check(st)
         k = n.value
-        return {"margins": list(m[:k]), "ms_per_kedge": list(ms[:k]),
-                "query_cycles_per_edge": qc[:len(self.layouts), :k].tolist(), "kept": kept.value}
+        return {"margins": list(m[:k]), "cycles_per_seed": list(cs[:k]),
+                "query_cycles_per_seed": qc[:nq, :k].tolist(), "kept": kept.value}
 
     def set_order_margin(self, log2_margin: float):
         """Every query's margin (log2 units of predicted cost) by which a

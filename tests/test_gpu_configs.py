@@ -128,12 +128,14 @@ def test_learned_presplit_is_exact_and_splits():
 
 
 def test_online_autotuner_batches_are_exact():
-    """Under learned orders the margin trial runs first (two rounds over the
-    five candidate margins), then each batch of the tuning walk runs under
-    another launch candidate, then the filtering trial runs batches with the
-    DEBI filtering off and on; every one of them (and the batches after the
-    choices) equals the oracle, the margin kept is the fastest per inserted
-    edge, and the filtering is kept only when it is at least 3% faster."""
+    """Under learned orders the margin trial runs first (6 batches; each seed
+    whose choice depends on the margin takes the paper's order or the model's
+    pick at random), then each batch of the tuning walk runs under another
+    launch candidate, then the filtering trial runs batches with the DEBI
+    filtering off and on; every one of them (and the batches after the
+    choices) equals the oracle, each query keeps the margin of its fewest
+    estimated SM cycles, and the filtering is kept only when it is at least
+    3% faster."""
     s, qs = split_stream(56), split_queries()
     with fresh(s, qs) as g:
         g.set_order_policy("explore")
@@ -146,8 +148,8 @@ def test_online_autotuner_batches_are_exact():
         assert g.autotune_filter_result() is None and g.autotune_margin_result() is None
         g.autotune(1)
         active, left = g.autotune_state()
-        # 2 x 5 margin-trial batches, the candidates, then 3 + 3 filtering-trial batches
-        assert active and left == 10 + n + 6
+        # 6 margin-trial batches, the candidates, then 3 + 3 filtering-trial batches
+        assert active and left == 6 + n + 6
         g.reset_stats()
         k = 3
         while k < 3 + left + 2:
@@ -162,12 +164,14 @@ def test_online_autotuner_batches_are_exact():
         assert ft["filtering_kept"] == (ft["ms_per_kedge_on"] < 0.97 * ft["ms_per_kedge_off"])
         mt = g.autotune_margin_result()
         assert mt is not None and mt["margins"] == [0.0, 0.5, 1.0, 2.0, 3.0]
-        assert all(v > 0 for v in mt["ms_per_kedge"])
-        assert mt["kept"] == mt["margins"][int(np.argmin(mt["ms_per_kedge"]))] == g.get_order_margin()
-        for qi in range(len(qs)):                      # each query: the fewest SM cycles per edge
-            cyc = mt["query_cycles_per_edge"][qi]
-            assert all(v > 0 for v in cyc)
-            assert g.get_order_margin(qi) == mt["margins"][int(np.argmin(cyc))]
+        assert all(v > 0 for v in mt["cycles_per_seed"])
+        assert mt["kept"] == mt["margins"][int(np.argmin(mt["cycles_per_seed"]))] == g.get_order_margin()
+        for qi in range(len(qs)):                      # each query: the fewest estimated SM cycles
+            cyc = np.array(mt["query_cycles_per_seed"][qi])
+            if cyc.sum() > 0:
+                assert g.get_order_margin(qi) == mt["margins"][int(np.argmin(cyc))]
+            else:                                      # no seed of it depended on the margin
+                assert g.get_order_margin(qi) == mt["kept"]
         assert g.stats()["seeds_filtered"] > 0         # the trial's filtered batches pruned seeds
 
 
