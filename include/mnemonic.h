@@ -380,8 +380,8 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
  * How far the model's ranking can be trusted depends on the query, so when
  * mn_autotune starts under MN_ORDER_LEARNED it first runs a margin trial on 6
  * live inserting batches.  Only a seed whose model pick beats the paper's
- * order by a predicted gain in (0, 3) log2 units can be decided differently
- * by the candidate margins {0, 0.5, 1, 2, 3}; such a seed takes the paper's
+ * order by a predicted gain in (0, 6) log2 units can be decided differently
+ * by the candidate margins {0, 0.5, 1, 2, 3, 6}; such a seed takes the paper's
  * order or the pick with equal odds (drawn pseudo-randomly per seed), and
  * the enumerator logs the SM cycles of its work units per (query, gain
  * interval between two candidates, arm).  Since a margin picks the model's
@@ -392,7 +392,7 @@ mn_status mn_autotune_filter_result(const mn_graph *g, double *ms_per_kedge_off,
  * margin of the fewest cycles over all queries becomes the default for later
  * queries; the launch candidates and the filtering trial follow.  (Switching
  * the policy away from learned before the trial ends skips it.)
- * mn_autotune_margin_result gives, for candidate k < *n (= 5): margins[k],
+ * mn_autotune_margin_result gives, for candidate k < *n (= 6): margins[k],
  * cycles_per_seed[k] (the estimated SM cycles per trial seed under margin k,
  * over all queries) and, for registered query q, query_cycles_per_seed[q *
  * cap + k] (0 for a query none of whose seeds depended on the margin: it

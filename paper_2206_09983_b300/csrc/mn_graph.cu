@@ -92,8 +92,8 @@ struct Phase {
 
 // A batch queued by mn_insert_batch with MN_ASYNC: what its completion needs.
 // the autotuner's candidate margins of the learned order (log2 units)
-constexpr uint32_t MT_N = 5, MT_BATCHES = 6;
-constexpr float MT_CANDS[MT_N] = {0.f, 0.5f, 1.f, 2.f, 3.f};
+constexpr uint32_t MT_N = 6, MT_BATCHES = 6;
+constexpr float MT_CANDS[MT_N] = {0.f, 0.5f, 1.f, 2.f, 3.f, 6.f};
 static_assert(MT_N <= MARGIN_SLOTS / 2, "two trial slots per margin interval");
 
 struct PendingBatch {

@@ -163,7 +163,7 @@ def test_online_autotuner_batches_are_exact():
         assert ft is not None and ft["ms_per_kedge_off"] > 0 and ft["ms_per_kedge_on"] > 0
         assert ft["filtering_kept"] == (ft["ms_per_kedge_on"] < 0.97 * ft["ms_per_kedge_off"])
         mt = g.autotune_margin_result()
-        assert mt is not None and mt["margins"] == [0.0, 0.5, 1.0, 2.0, 3.0]
+        assert mt is not None and mt["margins"] == [0.0, 0.5, 1.0, 2.0, 3.0, 6.0]
         assert all(v > 0 for v in mt["cycles_per_seed"])
         assert mt["kept"] == mt["margins"][int(np.argmin(mt["cycles_per_seed"]))] == g.get_order_margin()
         for qi in range(len(qs)):                      # each query: the fewest estimated SM cycles
