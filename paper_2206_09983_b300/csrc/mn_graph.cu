@@ -66,6 +66,7 @@ struct QueryHost {
     uint32_t *debi = nullptr;
     uint8_t *out[2] = {nullptr, nullptr};
     unsigned long long out_cap[2] = {0, 0};
+    unsigned long long max_seen[2] = {0, 0};     // the most records one batch put in each list
     uint64_t sorted_batch[2] = {0, 0};   // batch whose list is sorted in place (MN_FETCH_SORTED)
 };
 
@@ -1253,7 +1254,7 @@ mn_status grow_outputs(mn_graph *g, int phase, unsigned long long *rerun, bool *
 // Before a launch: lists of queries whose recent batches produced more
 // records per edge than this batch's lists hold are grown now, so that the
 // batch is not enumerated twice.
-constexpr uint64_t PRESIZE_MAX_BYTES = 1ull << 30;   // per result list
+constexpr uint64_t PRESIZE_MAX_BYTES = 16ull << 30;  // per result list
 
 mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
 {
@@ -1265,11 +1266,13 @@ mn_status presize_outputs(mn_graph *g, uint64_t n_new, uint64_t n_expired)
             // three times the decayed maximum: a batch that brings a hub
             // into play multiplies one query's output, and a second launch
             // costs more than the memory (lists are grown within the budget);
-            // but no list is presized past PRESIZE_MAX_BYTES, so that one
-            // heavy batch's rate times a large batch cannot claim the device
-            // (a list that overflows is grown to its exact count)
-            const double est = std::min(3.0 * g->rec_rate[s][q] * (double)edges,
-                                        (double)(PRESIZE_MAX_BYTES / g->queries[q].rec_bytes));
+            // but at most four times the most records one batch has put in
+            // the list, and never past PRESIZE_MAX_BYTES, so that one small
+            // batch's rate times a large batch cannot claim the device (a
+            // list that overflows is grown to its exact count)
+            const double est = std::min({3.0 * g->rec_rate[s][q] * (double)edges,
+                                         4.0 * (double)g->queries[q].max_seen[s] + 65536.0,
+                                         (double)(PRESIZE_MAX_BYTES / g->queries[q].rec_bytes)});
             if (est <= (double)g->queries[q].out_cap[s]) continue;
             bool grown = false;
             TRY(ensure_out_cap(g, q, s, (uint64_t)est, &grown, &over));
@@ -1290,6 +1293,7 @@ void note_rates(mn_graph *g, uint64_t n_new, uint64_t n_expired)
         for (size_t q = 0; q < g->queries.size(); q++) {
             const double r = (double)g->h_ctrl->counts[q * 3 + s] / (double)edges;
             g->rec_rate[s][q] = std::max(0.9 * g->rec_rate[s][q], r);
+            g->queries[q].max_seen[s] = std::max(g->queries[q].max_seen[s], g->h_ctrl->counts[q * 3 + s]);
         }
     }
 }
