@@ -95,7 +95,7 @@ class ClockSampler:
 # launch, the mean of the learned arm's first two timed launches (one per batch) in
 # one ncu capture (profiles/k_enumerate_rmat20_window.md).  It holds only for the
 # enumerator code it was taken on (enum_source_sha1): null once that changed.
-ENUM_TRAFFIC = {"source_sha1": "9f06f603ebe0fd83b6d7536fca7e54931b253b10", "bytes_per_launch": 946.3e6}
+ENUM_TRAFFIC = {"source_sha1": "fea350eeb68150b8a130d732c83384fdbb4f1c7e", "bytes_per_launch": 883.8e6}
 
 
 def enum_source_sha1() -> str:
