@@ -5,9 +5,11 @@ four calibrated queries (rmat20_window) and the 36 batched uneven queries
 launch configurations bench.py times (device-resident batches, count-only
 preload, queries registered on the full window): the plain path (paper
 order, default launch), and the learned arm (orders picked by the work
-model trained on three explore batches, with the order margin, the launch
-parameters and the pre-splitting the autotuner keeps on these workloads, and
-on the uneven workload the DEBI filtering it keeps there).
+model trained on three explore batches, then tuned online on live batches as
+the benchmark does: the per-query margin trial of the learned order, the walk
+over launch parameters, pre-splitting and slice staging, and the trial of the
+DEBI filtering; the two checked batches run in whatever configuration the
+autotuner kept).
 
 The oracle cannot list a whole batch quickly, so per batch and query:
 * sampled exactness: for a seeded sample of the batch's edges, the GPU records
@@ -30,10 +32,10 @@ pytestmark = pytest.mark.gpu
 _STREAM = {}
 
 
-# the autotuner's choices on these workloads (blocks per SM at the limit,
-# split threshold, split depth; pre-split threshold, 0 = off; filtering;
-# margin of the learned order)
-LEARNED = {"rmat20_window": ((0, 40, 3), 22.0, False, 2.0), "rmat20_uneven": ((0, 64, 16), 0.0, True, 0.0)}
+# batches the learned arm may spend before its checked ones: 3 explore
+# batches, then the autotuner (6 margin-trial batches, one per launch
+# candidate, 6 for the filtering trial)
+LEARNED_SPAN = 48
 
 
 @pytest.fixture(scope="module", params=[("rmat20_window", "plain"), ("rmat20_uneven", "plain"),
@@ -49,8 +51,8 @@ def run(request):
     if "s" not in _STREAM:
         _STREAM["s"] = workloads.rmat20_stream()
     s = _STREAM["s"]
-    skip = 3 if mode == "learned" else 0
-    packed = M.edges_from_stream(s, 0, W + (skip + 2) * B)
+    span = LEARNED_SPAN if mode == "learned" else 0
+    packed = M.edges_from_stream(s, 0, W + (span + 2) * B)
     d = torch.from_numpy(packed.view(np.uint8)).cuda()
     qs = wl["queries"]()
     g = M.Graph(s["num_vertices"], s["num_edge_labels"], vmask=s["vmask"], window=W, max_batch=B,
@@ -59,23 +61,27 @@ def run(request):
     for lo in range(0, W, B):
         g.insert(None, device_ptr=d.data_ptr() + 24 * lo, n=B, count_only=True)
     qids = [g.register_query(q) for q in qs]
+    pos = W
     if mode == "learned":
         g.set_order_policy("explore")
-        for k in range(skip):
-            g.insert(None, device_ptr=d.data_ptr() + 24 * (W + k * B), n=B)
+        for _ in range(3):
+            g.insert(None, device_ptr=d.data_ptr() + 24 * pos, n=B)
+            pos += B
         g.train_order_model(epochs=300, lr=2e-3)
         g.set_order_policy("learned")
-        tuning, presplit, filtering, margin = LEARNED[name]
-        g.set_tuning(*tuning)
-        g.set_presplit(presplit)
-        g.set_filtering(filtering)
-        g.set_order_margin(margin)
+        g.autotune(1)
+        while g.autotune_state()[0]:
+            assert pos < W + span * B, "autotuner needs more batches than the fixture packed"
+            g.insert(None, device_ptr=d.data_ptr() + 24 * pos, n=B)
+            pos += B
+        print(f"{name}: kept {g.get_tuning()}, filtering trial {g.autotune_filter_result()}")
     out = []
-    for k in range(skip, skip + 2):
-        hi = W + k * B
+    for _ in range(2):
+        hi = pos
         r = g.insert(None, device_ptr=d.data_ptr() + 24 * hi, n=B)
         rows = {(qi, sg): g.fetch_rows(qi, sg) for qi in qids for sg in (+1, -1)}
         out.append((hi - W, hi, hi + B, r, rows))
+        pos += B
     g.close()
     return s, qs, out
 
