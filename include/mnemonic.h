@@ -351,11 +351,15 @@ mn_status mn_get_slice_staging(const mn_graph *g, uint32_t *min_entries);
  * threshold {off, 2^20, 2^22 cycles}, all without slice staging, plus split
  * threshold 40 at any depth with staging of ranges of at least {256, 1024}
  * entries (mn_set_slice_staging).  Then the DEBI filtering (mn_set_filtering)
- * is tried the same way on live inserting batches: 3 with it off, then 3 with
- * it on (its full pass to turn on is not timed), each timed from the filter
- * pass to the end of the enumeration, and the filtering is kept when it is
- * at least 3% faster per inserted edge (it removes seeds and candidates but
- * costs a pass per batch, so which wins depends on the queries).  mn_autotune_state reports whether tuning is
+ * is tried on 8 live inserting batches: it is turned on (its full pass to
+ * build the sets is not timed) and kept up to date on all of them, while the
+ * batches alternate between enumerating without it (timed over the
+ * enumeration; their filter pass runs afterwards, untimed) and with it (timed
+ * from the filter pass to the end of the enumeration), so that differences
+ * between stretches of the stream fall on both arms alike; the filtering is
+ * kept when it is at least 3% faster per inserted edge (it removes seeds and
+ * candidates but costs a pass per batch, so which wins depends on the
+ * queries).  mn_autotune_state reports whether tuning is
  * still running and how many of its batches are left; mn_autotune_filter_result
  * gives the trial's times (ms per 1,000 inserted edges) and choice
  * (MN_ERR_STATE before a trial has finished). */

@@ -101,6 +101,7 @@ struct PendingBatch {
     bool active = false;
     uint64_t id = 0, n = 0, x = 0, hi_new = 0;
     bool count_only = false, tune_now = false, trial_now = false, margin_now = false;
+    bool trial_off = false;             // a filtering-trial batch enumerated without the filter
     int nph = 0;
     Phase ph[2] = {};
 };
@@ -189,10 +190,13 @@ struct mn_graph {
     std::vector<double> tune_ms, tune_work;
     uint32_t tune_per = 1, tune_idx = 0, tune_in = 0;
     cudaEvent_t tune_e0 = nullptr, tune_e1 = nullptr;
-    // the autotuner's filtering trial: batches with the DEBI filtering off
-    // (ftrial 1), then on (2); the faster per inserted edge is kept
+    // the autotuner's filtering trial: the filtering is kept up to date over
+    // 2 x ft_per live inserting batches that alternate between enumerating
+    // without it (off, even ft_idx) and with it (on, odd); the faster per
+    // inserted edge is kept
     int ftrial = 0;
-    uint32_t ft_left = 0, ft_per = 3;
+    uint32_t ft_idx = 0, ft_per = 4;
+    bool ft_off_now = false;            // the pending batch enumerates without the filter
     double ft_ms[2] = {0.0, 0.0}, ft_edges[2] = {0.0, 0.0};
     int ft_choice = -1;                 // -1: no trial has finished
     // the learned order's margins (log2 units of predicted cost by which the
@@ -1060,7 +1064,7 @@ mn_status launch_enumerate(mn_graph *g, const Phase *ph, int nph, bool count_onl
     p.qrun[1] = qrun ? qrun[1] : ~0ull;
     p.wait_polls = g->wait_polls;
     p.wait_hold = g->wait_hold;
-    p.bu = g->filter ? g->d_bu_ptrs : nullptr;
+    p.bu = g->filter && !g->ft_off_now ? g->d_bu_ptrs : nullptr;
     p.W32 = g->W32;
     if (nph > 1) {
         const Phase &b = ph[1];
@@ -1394,6 +1398,8 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
     const Phase *ph = pd.ph;
     bool over_budget = false;
     const mn_status est = enumerate_phases(g, ph, nph, count_only, &over_budget);
+    g->ft_off_now = false;                   // every launch of the batch has run
+    int ft_switch = 0;                       // after the commit: 1 turn the filtering on, -1 off
     if (tune_now && est == MN_OK) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
@@ -1412,11 +1418,12 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
                 g->presplit_log2 = c.presplit_log2;
                 g->slice_min = c.slice_min;
                 g->tuning = false;
-                // then the filtering trial: first with the filtering off
+                // then the filtering trial, with the filtering turned on (and
+                // its sets built, untimed) after this batch's commit
                 g->ftrial = 1;
-                g->ft_left = g->ft_per;
+                g->ft_idx = 0;
                 g->ft_ms[0] = g->ft_ms[1] = g->ft_edges[0] = g->ft_edges[1] = 0.0;
-                g->filter = false;
+                ft_switch = 1;
             }
         }
     }
@@ -1461,25 +1468,19 @@ static mn_status insert_finish(mn_graph *g, mn_batch_result *out)
             g->tuning = true;                      // then the launch parameters
         }
     }
-    int ft_switch = 0;                       // after the commit: 1 turn the filtering on, -1 off
     if (trial_now && est == MN_OK) {
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, g->tune_e0, g->tune_e1));
-        g->ft_ms[g->ftrial - 1] += ms;
-        g->ft_edges[g->ftrial - 1] += (double)n;
-        if (--g->ft_left == 0) {
-            if (g->ftrial == 1) {
-                g->ftrial = 2;
-                g->ft_left = g->ft_per;
-                ft_switch = 1;
-            } else {
-                // kept only when clearly faster: the dirty-vertex marking at
-                // insertion and expiry is outside the timed span
-                const bool on = g->ft_ms[1] / g->ft_edges[1] < 0.97 * (g->ft_ms[0] / g->ft_edges[0]);
-                g->ft_choice = on ? 1 : 0;
-                g->ftrial = 0;
-                if (!on) ft_switch = -1;
-            }
+        const int arm = pd.trial_off ? 0 : 1;
+        g->ft_ms[arm] += ms;
+        g->ft_edges[arm] += (double)n;
+        if (++g->ft_idx >= 2 * g->ft_per) {
+            // kept only when clearly faster: the dirty-vertex marking at
+            // insertion and expiry is outside the timed span
+            const bool on = g->ft_ms[1] / g->ft_edges[1] < 0.97 * (g->ft_ms[0] / g->ft_edges[0]);
+            g->ft_choice = on ? 1 : 0;
+            g->ftrial = 0;
+            if (!on) ft_switch = -1;
         }
     }
     if (est != MN_OK && est != MN_ERR_TIMEOUT) return est;   // validation: nothing applied
@@ -1848,11 +1849,15 @@ static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint
             x = g->h_ctrl->time_cut;
         }
     }
-    // the filtering trial times the filter pass with the enumeration
-    if (trial_now) CK(cudaEventRecord(g->tune_e0, g->stream));
+    // the filtering trial times an on batch from its filter pass to the end of
+    // the enumeration; an off batch (g->ft_off_now) enumerates without the
+    // filter, and its pass runs after the enumeration, untimed, only to keep
+    // the sets up to date
+    const bool ft_off = trial_now && g->ft_off_now;
+    if (trial_now && !ft_off) CK(cudaEventRecord(g->tune_e0, g->stream));
     // DEBI filtering on G1 (the new adjacency, the expiring edges still visible)
-    if (n) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
-    if (tune_now) CK(cudaEventRecord(g->tune_e0, g->stream));
+    if (n && !ft_off) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
+    if (tune_now || ft_off) CK(cudaEventRecord(g->tune_e0, g->stream));
     // the adjacency enumerated holds seqs from `base` on: the new buffer was
     // merged at lo; without new edges the current one was merged at merged_lo
     const int nbuf = n ? 1 - g->cur : g->cur;
@@ -1876,6 +1881,7 @@ static mn_status queue_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint
     if (nph) TRY(launch_enumerate(g, ph, nph, count_only));
     for (int k = 0; k < nph; k++) TRY(log_samples(g, ph[k].phase));
     if (tune_now || trial_now) CK(cudaEventRecord(g->tune_e1, g->stream));
+    if (n && ft_off) TRY(filter_pass(g, 1 - g->cur, g->lo, hi_new, false));
     *x_io = x;
     *nph_out = nph;
     return MN_OK;
@@ -1921,6 +1927,9 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     }
     const bool tune_now = g->tuning && !g->queries.empty() && (n || x);
     const bool trial_now = !tune_now && g->ftrial && !g->queries.empty() && n;
+    // a filtering-trial batch with an even index enumerates without the filter
+    const bool trial_off = trial_now && (g->ft_idx & 1u) == 0;
+    g->ft_off_now = trial_off;
     if (tune_now) {
         const auto &c = g->tune_cfgs[g->tune_idx];
         g->enum_grid = g->nsm * (int)c.bps;
@@ -1990,6 +1999,7 @@ mn_status mn_insert_batch(mn_graph *g, const mn_edge *edges, uint64_t n, uint32_
     pd.count_only = count_only;
     pd.tune_now = tune_now;
     pd.trial_now = trial_now;
+    pd.trial_off = trial_off;
     pd.margin_now = margin_now;
     pd.nph = nph;
     for (int k = 0; k < nph; k++) pd.ph[k] = ph[k];
@@ -2763,10 +2773,8 @@ mn_status mn_autotune_state(const mn_graph *g, int32_t *active, uint32_t *batche
                    2ull * g->ft_per;
         else if (g->tuning)
             left = (uint64_t)(g->tune_cfgs.size() - g->tune_idx) * g->tune_per - g->tune_in + 2ull * g->ft_per;
-        else if (g->ftrial == 1)
-            left = g->ft_left + g->ft_per;
-        else if (g->ftrial == 2)
-            left = g->ft_left;
+        else if (g->ftrial)
+            left = 2ull * g->ft_per - g->ft_idx;
         *batches_left = (uint32_t)left;
     }
     return MN_OK;

@@ -131,8 +131,9 @@ def test_online_autotuner_batches_are_exact():
     """Under learned orders the margin trial runs first (6 batches; each seed
     whose choice depends on the margin takes the paper's order or the model's
     pick at random), then each batch of the tuning walk runs under another
-    launch candidate, then the filtering trial runs batches with the DEBI
-    filtering off and on; every one of them (and the batches after the
+    launch candidate, then the filtering trial keeps the DEBI filtering up to
+    date over 8 batches that alternate between enumerating without it and
+    with it; every one of them (and the batches after the
     choices) equals the oracle, each query keeps the margin of its fewest
     estimated SM cycles, and the filtering is kept only when it is at least
     3% faster."""
@@ -148,8 +149,9 @@ def test_online_autotuner_batches_are_exact():
         assert g.autotune_filter_result() is None and g.autotune_margin_result() is None
         g.autotune(1)
         active, left = g.autotune_state()
-        # 6 margin-trial batches, the candidates, then 3 + 3 filtering-trial batches
-        assert active and left == 6 + n + 6
+        # 6 margin-trial batches, the candidates, then 4 + 4 filtering-trial
+        # batches (off and on alternating)
+        assert active and left == 6 + n + 8
         g.reset_stats()
         k = 3
         while k < 3 + left + 2:
