@@ -146,7 +146,8 @@ WORKLOADS = {
 
 # NetFlow-like serving stream (BASELINE config 5): 10M hosts (10% servers),
 # client -> server flows by Zipf(1.1) client activity and server popularity,
-# 10% uniform background flows, ~8 timestamped parallel edges per host pair,
+# 10% uniform background flows, geometric repeats (mean 8) of each drawn host
+# pair (8.1 timestamped parallel edges per distinct pair in the first 2^22),
 # 6 protocol labels Zipf(1.1), one vertex label, 200M edges; count window
 # 2^24 edges, Poisson arrivals of log-uniform batches in [2^10, 2^18].
 FLOW = dict(name="flow10m_serve", hosts=10_000_000, num_edges=200_000_000, elabels=6, zipf=1.1,
