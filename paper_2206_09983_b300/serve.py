@@ -69,6 +69,7 @@ class Server:
         self.budget = int(mem_budget_bytes)
         self.in_use = 0
         self.peak_in_use = 0
+        self.inflight = 0               # device batches admitted and not yet completed
         self.merge = merge
         self.max_batch = max_batch
         self.safety = safety
@@ -120,6 +121,7 @@ class Server:
             need += extra
         self.in_use += need
         self.peak_in_use = max(self.peak_in_use, self.in_use)
+        self.inflight += 1
         return reqs, need
 
     def _worker(self, t: _Tenant):
@@ -169,13 +171,16 @@ class Server:
                               for i in range(len(res.count_pos)))
                     t.bytes_per_edge = 0.8 * t.bytes_per_edge + 0.2 * out / len(edges)
                 self.in_use -= need
+                self.inflight -= 1
                 self.cv.notify_all()
 
     def drain(self, timeout: float = 600.0):
         """Wait until every submitted request has completed."""
         deadline = time.perf_counter() + timeout
         with self.cv:
-            while any(t.queue for t in self.tenants.values()) or self.in_use > 0:
+            # an admitted batch counts until it completes, also one that
+            # reserved no bytes (a request without edges)
+            while any(t.queue for t in self.tenants.values()) or self.inflight > 0:
                 left = deadline - time.perf_counter()
                 if left <= 0:
                     raise TimeoutError("requests still pending")

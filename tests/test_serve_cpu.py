@@ -86,3 +86,16 @@ def test_poisson_schedule_covers_stream():
     assert all(1 <= n <= 262144 for _, n in sch)
     ts = [t for t, _ in sch]
     assert ts == sorted(ts)
+
+
+def test_drain_waits_for_empty_requests():
+    """A request with no edges reserves no result bytes, yet drain() must
+    still wait until it has completed (its insert call takes time too)."""
+    log = []
+    s = Server(mem_budget_bytes=1 << 20, merge=False)
+    s.add_tenant("a", FakeGraph(log, "a", per_edge=0.0))
+    reqs = [s.submit("a", edges(0)) for _ in range(5)]
+    s.drain()
+    done = [r.t_done > 0 for r in reqs]
+    s.close()
+    assert all(done) and len(log) == 5
