@@ -142,17 +142,24 @@ class Server:
             edges = reqs[0].edges if len(reqs) == 1 else np.concatenate([r.edges for r in reqs])
             err = ""
             res = None
+            rows = ([], [])
             t_ins = time.perf_counter()
+            # any failure is reported on the batch's requests, and the worker
+            # goes on: its reservation is released below either way
             try:
                 res = t.graph.insert(edges, count_only=t.count_only)
-            except M.MnError as e:                     # reported per request
+            except M.MnError as e:
                 err = str(e)
+            except Exception as e:                     # noqa: BLE001 -- reported per request
+                err = f"{type(e).__name__}: {e}"
             t.batches.append((len(edges), len(reqs), time.perf_counter() - t_ins))
-            rows = ([], [])
             if res is not None and t.keep_rows and not t.count_only:
-                for qi in range(len(res.count_pos)):
-                    rows[0].append(t.graph.fetch_rows(qi, +1))
-                    rows[1].append(t.graph.fetch_rows(qi, -1))
+                try:
+                    for qi in range(len(res.count_pos)):
+                        rows[0].append(t.graph.fetch_rows(qi, +1))
+                        rows[1].append(t.graph.fetch_rows(qi, -1))
+                except Exception as e:                 # noqa: BLE001 -- reported per request
+                    err = f"{type(e).__name__}: {e}"
             done = time.perf_counter()
             with self.cv:
                 for r in reqs:

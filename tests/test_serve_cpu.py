@@ -99,3 +99,25 @@ def test_drain_waits_for_empty_requests():
     done = [r.t_done > 0 for r in reqs]
     s.close()
     assert all(done) and len(log) == 5
+
+
+class FailingGraph(FakeGraph):
+    """Raises on its second insert call."""
+
+    def insert(self, edges, count_only=False):
+        if self.batch == 1:
+            self.batch += 1
+            raise ValueError("device gone")
+        return super().insert(edges, count_only)
+
+
+def test_failed_insert_is_reported_and_the_worker_goes_on():
+    log = []
+    s = Server(mem_budget_bytes=1 << 20, merge=False)
+    s.add_tenant("a", FailingGraph(log, "a"))
+    reqs = [s.submit("a", edges(100)) for _ in range(4)]
+    s.drain(timeout=30)
+    s.close()
+    assert [bool(r.error) for r in reqs] == [False, True, False, False]
+    assert "ValueError" in reqs[1].error
+    assert s.in_use == 0 and s.inflight == 0
